@@ -1,0 +1,187 @@
+"""Seeded synthetic workloads (inputs only).
+
+This module describes the problems that both the CUDA library and the test
+oracle are run on: the model, its parameters, the grid, the initial Gaussian,
+the time horizon and the measurement schedule. It holds none of the grid
+method's arithmetic; the only computation here is the generation of synthetic
+measurements from a seeded "truth" trajectory of the model ODE (classic RK4)
+plus seeded Gaussian noise.
+
+Workloads (the Lorenz systems are the paper's use cases, Sec. 5.1):
+  lorenz63_h0.5   -- Lorenz '63 (sigma, rho, beta) = (10, 28, 8/3), mean
+                     (-11.5, -10, 9.5), covariance I, h = 0.5, threshold 1e-7,
+                     CFL 0.9, t_end = 0.5, no measurement (about 1e4 cells).
+  lorenz63_h0.25  -- the same with h = 0.25, t_end = 2.0 and a full-state
+                     Gaussian measurement (R = 0.25 I) every 0.25 time units
+                     (10^5 - 10^6 cells).
+  lorenz96_6d     -- Lorenz '96, n = 6, F = 4, mean (4.01, 4, 4, 4, 4, 4),
+                     covariance 0.25 I, h = 0.25, threshold 1e-6, t_end = 1.0,
+                     no measurement (10^6 - 10^7 cells).
+  lorenz96_6d_h0.5 -- the same with h = 0.5 (a size the oracle can finish).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field, replace
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+
+# model identifiers shared by name (each side defines its own numeric enum with these values)
+DYN_CONSTANT, DYN_LINEAR, DYN_LORENZ63, DYN_LORENZ63_SHIFTED, DYN_LORENZ96 = range(5)
+LIM_MC, LIM_NONE, LIM_LW = range(3)
+
+L63_PARAMS = (10.0, 28.0, 8.0 / 3.0)
+
+
+@dataclass
+class Measurement:
+    t: float
+    y: np.ndarray          # measured values of the components H_idx
+    R: np.ndarray          # measurement covariance (m x m)
+    H_idx: np.ndarray      # measured state components
+
+
+@dataclass
+class Workload:
+    name: str
+    n: int
+    dynamics: int
+    params: Tuple[float, ...]
+    h: Tuple[float, ...]
+    mean: Tuple[float, ...]
+    cov: np.ndarray
+    thr_rel: float
+    cfl: float
+    t_end: float
+    prune_interval: int = 20
+    limiter: int = LIM_MC
+    measurements: List[Measurement] = field(default_factory=list)
+
+    @property
+    def x0(self) -> Tuple[float, ...]:
+        """Grid origin: the centre of cell 0 sits on the initial mean."""
+        return tuple(self.mean)
+
+    def segments(self) -> List[Tuple[float, Optional[Measurement]]]:
+        """(t_target, measurement at t_target or None) in time order."""
+        out: List[Tuple[float, Optional[Measurement]]] = []
+        for m in self.measurements:
+            if m.t <= self.t_end:
+                out.append((m.t, m))
+        if not out or out[-1][0] < self.t_end:
+            out.append((self.t_end, None))
+        return out
+
+    def with_(self, **kw) -> "Workload":
+        return replace(self, **kw)
+
+
+def _l63_rhs(x, p):
+    s, r, b = p
+    return np.array([s * (x[1] - x[0]), x[0] * (r - x[2]) - x[1], x[0] * x[1] - b * x[2]])
+
+
+def _l96_rhs(x, F):
+    n = x.size
+    return np.array([(x[(j + 1) % n] - x[(j - 2) % n]) * x[(j - 1) % n] - x[j] + F for j in range(n)])
+
+
+def truth_trajectory(rhs, x0: np.ndarray, times: Sequence[float], dt: float = 1e-4) -> List[np.ndarray]:
+    """Classic RK4 of dx/dt = rhs(x) sampled at the given increasing times."""
+    x = np.array(x0, dtype=np.float64)
+    t = 0.0
+    out = []
+    for tt in times:
+        while t < tt - 1e-15:
+            step = min(dt, tt - t)
+            k1 = rhs(x)
+            k2 = rhs(x + 0.5 * step * k1)
+            k3 = rhs(x + 0.5 * step * k2)
+            k4 = rhs(x + step * k3)
+            x = x + step / 6.0 * (k1 + 2 * k2 + 2 * k3 + k4)
+            t += step
+        out.append(x.copy())
+    return out
+
+
+def gaussian_measurements(rhs, mean, cov0, times, R, seed: int) -> List[Measurement]:
+    """Full-state measurements y_k = x(t_k) + nu_k of a truth started at mean + xi,
+    xi ~ N(0, cov0), nu_k ~ N(0, R); NumPy PCG64 with the given seed."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n = len(mean)
+    L0 = np.linalg.cholesky(np.asarray(cov0, dtype=np.float64))
+    x0 = np.asarray(mean, dtype=np.float64) + L0 @ rng.standard_normal(n)
+    xs = truth_trajectory(rhs, x0, times)
+    LR = np.linalg.cholesky(np.asarray(R, dtype=np.float64))
+    out = []
+    for t, x in zip(times, xs):
+        y = x + LR @ rng.standard_normal(n)
+        out.append(Measurement(float(t), y, np.array(R, dtype=np.float64), np.arange(n, dtype=np.int32)))
+    return out
+
+
+def lorenz63(h: float = 0.5, t_end: float = 0.5, thr_rel: float = 1e-7, cfl: float = 0.9,
+             measure_every: Optional[float] = None, R_diag: float = 0.25, seed: int = 2508,
+             prune_interval: int = 20, limiter: int = LIM_MC) -> Workload:
+    mean = (-11.5, -10.0, 9.5)
+    cov = np.eye(3)
+    meas: List[Measurement] = []
+    if measure_every:
+        k = int(round(t_end / measure_every))
+        times = [measure_every * (q + 1) for q in range(k)]
+        meas = gaussian_measurements(lambda x: _l63_rhs(x, L63_PARAMS), mean, cov, times,
+                                     R_diag * np.eye(3), seed)
+    return Workload(name=f"lorenz63_h{h}", n=3, dynamics=DYN_LORENZ63, params=L63_PARAMS,
+                    h=(h, h, h), mean=mean, cov=cov, thr_rel=thr_rel, cfl=cfl, t_end=t_end,
+                    prune_interval=prune_interval, limiter=limiter, measurements=meas)
+
+
+def lorenz96(h: float = 0.25, t_end: float = 1.0, thr_rel: float = 1e-6, cfl: float = 0.9,
+             F: float = 4.0, n: int = 6, sigma2: float = 0.25, prune_interval: int = 20,
+             limiter: int = LIM_MC) -> Workload:
+    mean = tuple([F + 0.01] + [F] * (n - 1))
+    return Workload(name=f"lorenz96_{n}d_h{h}", n=n, dynamics=DYN_LORENZ96, params=(F,),
+                    h=tuple([h] * n), mean=mean, cov=sigma2 * np.eye(n), thr_rel=thr_rel, cfl=cfl,
+                    t_end=t_end, prune_interval=prune_interval, limiter=limiter)
+
+
+def config(name: str) -> Workload:
+    """The named workloads of the benchmark and the parity tests."""
+    if name == "lorenz63_h0.5":
+        return lorenz63(h=0.5, t_end=0.5)
+    if name == "lorenz63_h0.25":
+        return lorenz63(h=0.25, t_end=2.0, measure_every=0.25)
+    if name == "lorenz96_6d":
+        return lorenz96(h=0.25, t_end=1.0)
+    if name == "lorenz96_6d_h0.5":
+        return lorenz96(h=0.5, t_end=1.0)
+    raise KeyError(name)
+
+
+def random_cells(n: int, count: int, radius: int, seed: int, p_scale: float = 1.0):
+    """A seeded random set of distinct cells inside a box of the given radius
+    with positive random values (for hashtable and step tests)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    side = 2 * radius + 1
+    total = side ** n
+    count = min(count, total)
+    lin = rng.choice(total, size=count, replace=False)
+    idx = np.zeros((count, n), dtype=np.int32)
+    rem = lin.copy()
+    for k in range(n - 1, -1, -1):
+        idx[:, k] = (rem % side) - radius
+        rem //= side
+    p = p_scale * rng.random(count)
+    return idx, p
+
+
+def gaussian_blob_cells(n: int, radius: int, sigma_cells: float, shift=None):
+    """All cells of a box with a Gaussian bump sampled at their centres; a dense
+    stand-in for a smooth pdf on a fixed set (values are inputs, not results)."""
+    side = 2 * radius + 1
+    grids = np.meshgrid(*[np.arange(-radius, radius + 1)] * n, indexing="ij")
+    idx = np.stack([g.reshape(-1) for g in grids], axis=1).astype(np.int32)
+    s = np.zeros(n) if shift is None else np.asarray(shift, dtype=np.float64)
+    d2 = (((idx - s) / sigma_cells) ** 2).sum(axis=1)
+    return idx, np.exp(-0.5 * d2)
