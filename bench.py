@@ -1,0 +1,425 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the GBEES propagation on one GB300 (cell-updates/s).
+
+One timed "step" is one whole run of the workload through the hot path: the
+initial Gaussian, then every propagate segment (grow, flux update, prune) and
+measurement update up to t_end. The default workload is Lorenz '63 with
+h = 0.25, t_end = 2 and a full-state measurement every 0.25 (the 10^5-10^6
+cell case). `value` is device time (CUDA events on the library's stream) with
+the inputs resident; `e2e` runs the same through the C ABI with host buffers
+and reads the final density back to the host.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision f64|f32]
+  python bench.py --impl reference ...   # the CPU oracle as the reference arm
+
+With N > 1 (torchrun) every rank runs its own replica: the path has no data
+exchange between grids, so scaling is weak and no collective is used except
+the barrier and the max/sum of the timings.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s"
+DEFAULT_WORKLOAD = "lorenz63_h0.25"
+
+# DRAM traffic of one update-kernel launch per cell, from an ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum divided by the cells the launch
+# updated); valid only while the kernel source has the recorded hash.
+TRAFFIC_BYTES_PER_CELL = {}
+CTU_SOURCE = os.path.join(ROOT, "paper_2508_13986_gb300", "csrc", "gbees_ctu.cuh")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--precision", choices=["f64", "f32"], default="f64")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the other precision's line")
+    ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
+    ap.add_argument("--max-cells", type=int, default=1 << 22)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        out_dir = os.path.join(ROOT, "gpurun_out")
+        if os.path.isdir(out_dir):
+            with open(os.path.join(out_dir, "clocks.csv"), "a") as f:
+                f.write("\n".join(self.lines) + "\n")
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ runs
+
+def run_workload(grid, w, with_readout=False):
+    """One whole run through the public API. Returns (cell updates, steps, bytes in, bytes out, peak cells)."""
+    import numpy as np
+
+    grid.init_gaussian(w.mean, w.cov)
+    h2d = 8 * w.n + 8 * w.n * w.n
+    updates = steps = 0
+    peak = grid.count() if with_readout else 0
+    for t_target, meas in w.segments():
+        st = grid.propagate(t_target)
+        updates += st.cell_updates
+        steps += st.steps
+        peak = max(peak, st.n_cells)
+        if meas is not None:
+            grid.correct_gaussian(meas.y, meas.R, meas.H_idx)
+            h2d += 8 * meas.y.size + 8 * meas.R.size + 4 * meas.H_idx.size
+    d2h = 0
+    if with_readout:
+        idx, p = grid.read_cells(sorted_=False)
+        mean, cov = grid.moments()
+        d2h = idx.nbytes + p.nbytes + mean.nbytes + cov.nbytes
+    return updates, steps, h2d, d2h, peak
+
+
+def bytes_per_update(n: int, precision: str) -> int:
+    """Algorithmic HBM bytes of the update kernel per cell: the packed key (8),
+    the cell's own value read and the new value written (2 S) and its 2n
+    neighbour links (8 n); neighbour values are L2 hits in key order."""
+    S = 8 if precision == "f64" else 4
+    return 8 + 2 * S + 8 * n
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def ctu_source_hash() -> str:
+    with open(CTU_SOURCE, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def time_precision(args, w, precision, dev, rank, world):
+    import torch
+
+    from paper_2508_13986_gb300 import gbees
+
+    prec = gbees.GBEES_FP64 if precision == "f64" else gbees.GBEES_FP32
+    grid = gbees.grid_for_workload(w, precision=prec, max_cells=args.max_cells, device=f"cuda:{dev}")
+    stream = grid.stream
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=f"cuda:{dev}")
+    for _ in range(args.warmup):
+        run_workload(grid, w)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    grid.profile(enable=True, reset=True)
+    clocks = ClockSampler(dev)
+    clocks.start()
+    total_ms, total_updates, total_steps, peak = 0.0, 0, 0, 0
+    for _ in range(args.steps):
+        flush.zero_()  # L2 flush between timed runs (outside the events)
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        u, s, _, _, pk = run_workload(grid, w)
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        total_updates += u
+        total_steps += s
+        peak = max(peak, pk)
+    clk = clocks.stop()
+    prof = grid.profile(enable=False)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+
+    # end to end through the C ABI with host buffers: inputs from host memory,
+    # final density and moments read back to host memory, wall clock
+    e2e_ms, e2e_updates, h2d, d2h = 0.0, 0, 0, 0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        u, _, bi, bo, _ = run_workload(grid, w, with_readout=True)
+        torch.cuda.synchronize(dev)
+        e2e_ms += (time.perf_counter() - t0) * 1e3
+        e2e_updates += u
+        h2d, d2h = bi, bo
+    grid.close()
+
+    ms_max = reduce_max(total_ms, world)
+    upd_sum = reduce_sum(total_updates, world)
+    e2e_max = reduce_max(e2e_ms, world)
+    e2e_sum = reduce_sum(e2e_updates, world)
+
+    peak_gbs, peak_src = load_peaks()
+    bpc = bytes_per_update(w.n, precision)
+    upd_ms = prof["ms"]["update"]
+    achieved = bpc * total_updates / (upd_ms / 1e3) / 1e9 if upd_ms > 0 else None
+    launches_upd = max(prof["timed"]["update"], 1)
+    traffic = None
+    key = f"{w.name}/{precision}"
+    rec = TRAFFIC_BYTES_PER_CELL.get(key)
+    if rec and rec.get("src") == ctu_source_hash():
+        traffic = rec["bytes_per_cell"] * total_updates / launches_upd
+    phase_share = {k: (v / sum(prof["ms"].values()) if sum(prof["ms"].values()) > 0 else 0.0)
+                   for k, v in prof["ms"].items()}
+    return {
+        "value": upd_sum / (ms_max / 1e3),
+        "ms_per_step": ms_max / args.steps,
+        "updates_per_step": total_updates / args.steps,
+        "time_steps_per_run": total_steps / args.steps,
+        "peak_cells": peak,
+        "e2e": {"value": e2e_sum / (e2e_max / 1e3), "unit": METRIC, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_max / args.steps},
+        "roofline": {
+            "bound": "hbm",
+            "kernel": "k_ctu (DCU + CTU + high-resolution update)",
+            "achieved": achieved,
+            "peak": peak_gbs,
+            "peak_source": peak_src,
+            "unit": "GB/s",
+            "frac": (achieved / peak_gbs) if achieved else None,
+            "traffic": traffic,
+            "algorithmic_bytes_per_cell": bpc,
+            "cells_per_launch": total_updates / launches_upd,
+            "avg_launch_us": upd_ms * 1e3 / launches_upd,
+        },
+        "phase_share": phase_share,
+        "gpu_launches": prof["total_launches"],
+        "fallback_lookups": prof["fallback_lookups"],
+        "clocks": clk,
+    }
+
+
+def cpu_baseline(w, budget_s):
+    """The oracle as it stands, single-threaded, on the first part of the same
+    workload until about budget_s seconds of work."""
+    from oracle.oracle import Oracle
+
+    o = Oracle(w.n, w.dynamics, w.params, w.h, w.x0, w.thr_rel, w.cfl, w.prune_interval, w.limiter)
+    t0 = time.perf_counter()
+    o.init_gaussian(w.mean, w.cov)
+    updates, steps, t = 0, 0, 0.0
+    dt_probe = 1e-3
+    while time.perf_counter() - t0 < budget_s and t < w.t_end:
+        t = min(w.t_end, t + dt_probe)
+        st = o.propagate(t)
+        updates += st.cell_updates
+        steps += st.steps
+    el = time.perf_counter() - t0
+    return {"value": updates / el, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": f"{w.name}: init + first {steps} time steps (t <= {t:.3f}), {updates} cell updates, {el:.1f} s"}
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def reduce_max(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def main_ours(args):
+    import torch
+
+    from paper_2508_13986_gb300 import workloads
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    w = workloads.config(args.workload)
+    main = time_precision(args, w, args.precision, local, rank, world)
+    other = None
+    if not args.no_secondary:
+        other_prec = "f32" if args.precision == "f64" else "f64"
+        other = time_precision(args, w, other_prec, local, rank, world)
+    if rank == 0:
+        cpu = cpu_baseline(w, args.cpu_budget) if world == 1 else None
+        line = {
+            "metric": METRIC,
+            "value": main["value"],
+            "unit": METRIC,
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": main["ms_per_step"],
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": args.precision,
+            "data": "synthetic",
+            "config": {"workload": args.workload, "parallelism": f"replicas{world}",
+                       "step": "one whole run: init + propagate/correct to t_end",
+                       "l2": "flushed between timed runs (256 MiB write)",
+                       "cell_updates_per_step": main["updates_per_step"],
+                       "time_steps_per_run": main["time_steps_per_run"],
+                       "peak_cells": main["peak_cells"]},
+            "e2e": main["e2e"],
+            "roofline": main["roofline"],
+            "cpu_baseline": cpu,
+            "gpu_launches": main["gpu_launches"],
+            "clocks": main["clocks"],
+            "phase_share": main["phase_share"],
+            "fallback_lookups": main["fallback_lookups"],
+        }
+        if other is not None:
+            line["other_precision"] = {
+                "dtype": "f32" if args.precision == "f64" else "f64",
+                "value": other["value"], "ms_per_step": other["ms_per_step"], "e2e": other["e2e"],
+                "roofline": other["roofline"], "gpu_launches": other["gpu_launches"], "clocks": other["clocks"],
+                "phase_share": other["phase_share"]}
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+def main_reference(args):
+    """The reference arm: the CPU oracle (plain FP64 GBEES) on a bounded sample of
+    the same workload per step."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle.oracle import Oracle
+    from paper_2508_13986_gb300 import workloads
+
+    w = workloads.config(args.workload)
+    t_sample = 0.004
+
+    def one():
+        o = Oracle(w.n, w.dynamics, w.params, w.h, w.x0, w.thr_rel, w.cfl, w.prune_interval, w.limiter)
+        o.init_gaussian(w.mean, w.cov)
+        st = o.propagate(t_sample)
+        return st.cell_updates, st.steps
+
+    for _ in range(args.warmup):
+        one()
+    t0 = time.perf_counter()
+    upd = steps = 0
+    for _ in range(args.steps):
+        u, s = one()
+        upd += u
+        steps += s
+    el = time.perf_counter() - t0
+    val = upd / el
+    sample = (f"{w.name}: init + propagate to t = {t_sample} ({steps // max(args.steps, 1)} time steps, "
+              f"{upd // max(args.steps, 1)} cell updates) per step")
+    print(json.dumps({
+        "metric": METRIC, "value": val, "unit": METRIC, "impl": "reference", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / max(args.steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "parallelism": "cpu oracle, 1 thread", "sample_t_end": t_sample},
+        "cpu_baseline": {"value": val, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": val, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        main_reference(a)
+    else:
+        main_ours(a)

@@ -1,0 +1,209 @@
+/*
+ * gbees.h -- C ABI of the GB300 (sm_103a) GBEES propagation library.
+ *
+ * GBEES (Grid-based Bayesian Estimation Exploiting Sparsity; Hanson, Rubio,
+ * Garcia-Gutierrez, Bewley, "GBEES-GPU", arXiv 2508.13986) propagates a
+ * probability density p(x, t) of a state x in R^n by a finite-volume solution
+ * of the advection form of the Fokker-Planck equation (Eq. 3), on a sparse
+ * Cartesian grid that holds only the cells where p is non-negligible, and
+ * folds in measurements by Bayes' rule (Eq. 4).
+ *
+ * One call sequence (the paper's flowchart, Fig. 1):
+ *   gbees_workspace_bytes -> caller allocates device memory and a stream
+ *   gbees_create -> gbees_init_gaussian | gbees_init_cells
+ *   { gbees_propagate(t_m) -> gbees_correct_gaussian(y_m) }* -> gbees_propagate(t_end)
+ *   gbees_read_cells / gbees_moments -> gbees_destroy
+ *
+ * Conventions for every entry point:
+ *   - Return value: a gbees_status (0 = success, negative = error). No entry
+ *     point throws or aborts; gbees_last_error() returns a message.
+ *   - After GBEES_ECAPACITY, GBEES_EKEYRANGE, GBEES_ETABLE or GBEES_EDEGENERATE
+ *     the context is poisoned: every later call except gbees_last_error /
+ *     gbees_status / gbees_destroy returns the same status until
+ *     gbees_init_gaussian or gbees_init_cells starts a new grid. GBEES_ECUDA
+ *     poisons the context for good (destroy it).
+ *   - Device memory: the caller owns the workspace (one allocation of
+ *     gbees_workspace_bytes bytes, 256-byte aligned) and the CUDA stream; the
+ *     library owns only its small host-side context. All work is issued on the
+ *     caller's stream. Every call returns after its work has completed on that
+ *     stream (the host buffers it writes are valid on return).
+ *   - Host pointers (mean, cov, idx, p, y, R, ...) belong to the caller and are
+ *     read or written only during the call.
+ *   - Cell indices are signed integers; cell i has centre x0 + i * h (Eq. 5).
+ *     Keys pack the indices with floor(63 / n) bits per dimension (32 for n = 1),
+ *     so |i_j| must stay below 2^(bits-1); a cell outside that range is
+ *     GBEES_EKEYRANGE.
+ */
+#ifndef GBEES_H
+#define GBEES_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GBEES_OK = 0,
+    GBEES_EINVAL = -1,      /* bad argument or configuration */
+    GBEES_ECAPACITY = -2,   /* more active cells than max_cells (fixed capacity, Sec. 4.1) */
+    GBEES_EKEYRANGE = -3,   /* a cell index does not fit the packed key */
+    GBEES_EDEGENERATE = -4, /* total probability is zero or not finite (e.g. C = 0 in Eq. 4) */
+    GBEES_ECUDA = -5,       /* a CUDA runtime call failed */
+    GBEES_ETIMEOUT = -6,    /* a bounded device wait gave up */
+    GBEES_ETABLE = -7       /* the hashtable probe sequence found no free slot (Algorithm 2) */
+} gbees_status;
+
+/* Drift models f(x) (Sec. 5.1). Parameter layout in gbees_config.params:
+ *   GBEES_DYN_CONSTANT          f = (c_1..c_n)                        params[0..n)
+ *   GBEES_DYN_LINEAR            f = A x + b, A row-major n x n, then b params[0..n*n+n)
+ *   GBEES_DYN_LORENZ63          n = 3, (sigma (y-x), x (rho - z) - y, x y - beta z)
+ *                               params = sigma, rho, beta
+ *   GBEES_DYN_LORENZ63_SHIFTED  n = 3, the form printed in Sec. 5.1.1:
+ *                               (sigma (x2-x1), -x2 - x1 x3, -b x3 + x1 x2 - b r)
+ *                               params = sigma, b, r
+ *   GBEES_DYN_LORENZ96          n >= 4, f_j = (x_{j+1} - x_{j-2}) x_{j-1} - x_j + F
+ *                               (cyclic, Sec. 5.1.2), params = F */
+enum {
+    GBEES_DYN_CONSTANT = 0,
+    GBEES_DYN_LINEAR = 1,
+    GBEES_DYN_LORENZ63 = 2,
+    GBEES_DYN_LORENZ63_SHIFTED = 3,
+    GBEES_DYN_LORENZ96 = 4
+};
+
+/* Limiter of the high-resolution correction term (Sec. 2.1). MC is the
+ * default; NONE (first order: DCU + CTU only) and LW (phi = 1, Lax-Wendroff)
+ * exist for testing. */
+enum { GBEES_LIM_MC = 0, GBEES_LIM_NONE = 1, GBEES_LIM_LW = 2 };
+
+/* Storage and flux precision. FP64: everything in double. FP32: probabilities
+ * stored and fluxes computed in float; the normalisation sum, the maximum, the
+ * CFL reduction, the grow/prune decisions and the likelihood stay in double. */
+enum { GBEES_FP64 = 0, GBEES_FP32 = 1 };
+
+typedef struct {
+    int32_t n;              /* state dimension, 1..6 */
+    int32_t dynamics;       /* GBEES_DYN_* */
+    double params[64];      /* model parameters, see above */
+    double h[6];            /* cell width per dimension, > 0 */
+    double x0[6];           /* centre of cell 0 (grid origin) */
+    double thr_rel;         /* a cell is significant when p > thr_rel * max p */
+    double cfl;             /* CFL number (dt = cfl / max rate, Eq. 8) */
+    int32_t prune_interval; /* prune every K steps (and after every measurement); 0 = only after measurements */
+    int32_t precision;      /* GBEES_FP64 | GBEES_FP32 */
+    int32_t limiter;        /* GBEES_LIM_* */
+    int32_t probe_width;    /* lanes that probe the hashtable together: 1, 2, 4, 8, 16 or 32 (0 = 1) */
+    int64_t max_cells;      /* fixed cell capacity (Sec. 4.1) */
+    double table_factor;    /* hashtable slots per cell of capacity, >= 1.25 (0 = 2.0, Sec. 4.2) */
+} gbees_config;
+
+typedef struct {
+    int64_t steps;        /* time steps taken by the call */
+    int64_t cell_updates; /* sum over those steps of the active cells advanced */
+    double t;             /* time reached */
+    double last_dt;       /* size of the last step */
+    int64_t total_steps;  /* steps since the last init */
+    int64_t n_cells;      /* active cells on return */
+    double norm;          /* (prod h) * sum of the stored values before the last normalisation */
+} gbees_stats;
+
+typedef struct gbees_ctx gbees_ctx;
+
+/* Bytes of device workspace that gbees_create needs for this configuration
+ * (cell pools, double buffers, hashtable and scalars). Returns 0 for an
+ * invalid configuration. */
+size_t gbees_workspace_bytes(const gbees_config* cfg);
+
+/* Create a context on the current CUDA device. d_workspace: device pointer to
+ * at least gbees_workspace_bytes(cfg) bytes, 256-byte aligned, owned by the
+ * caller and not touched by anyone else until gbees_destroy. cuda_stream: a
+ * cudaStream_t (NULL = legacy default stream). On success *out receives the
+ * context. The configuration is copied. */
+int gbees_create(const gbees_config* cfg, void* d_workspace, size_t workspace_bytes, void* cuda_stream,
+                 gbees_ctx** out);
+
+/* Start a new grid from a Gaussian N(mean, cov) sampled at cell centres
+ * (the initial PDFs of Sec. 5.1): every cell with p > thr_rel * max p is
+ * active, and p is normalised so that (prod h) sum p = 1. mean: n doubles;
+ * cov: n x n row-major, symmetric positive definite. t0: initial time. */
+int gbees_init_gaussian(gbees_ctx* ctx, const double* mean, const double* cov, double t0);
+
+/* Start a new grid from explicit cells (a checkpoint, or any test set).
+ * idx: N x n int32 row-major cell indices, all distinct; p: N densities,
+ * taken as given (not renormalised); t0: time; step0: steps already taken
+ * (the prune schedule counts from it; 0 for a new run). N may be 0. */
+int gbees_init_cells(gbees_ctx* ctx, const int32_t* idx, const double* p, int64_t N, double t0, int64_t step0);
+
+/* Propagate until t == t_end (the grow / step / prune loop of Fig. 1): each
+ * step grows the downwind neighbours of the significant cells (Sec. 3.3),
+ * takes dt = min(cfl / max_i sum_j |f_j(x_{i-e_j/2})| / h_j, t_end - t) over
+ * the active cells (Eq. 8), applies the DCU flux (Eq. 7), the corner-transport
+ * corrections (Algorithm 1) and the limited high-resolution correction,
+ * prunes every prune_interval steps (Algorithm 3) and normalises. stats may be
+ * NULL. t_end <= t takes no step. */
+int gbees_propagate(gbees_ctx* ctx, double t_end, gbees_stats* stats);
+
+/* Bayesian measurement update (Eq. 4) with the Gaussian likelihood
+ * exp(-1/2 (y - x_H)^T R^{-1} (y - x_H)) of m measured components
+ * x_H = (x[H_idx[0]], ..., x[H_idx[m-1]]) at the cell centres, followed by a
+ * prune and the normalisation (C of Eq. 4). y: m doubles; R: m x m row-major
+ * symmetric positive definite; 1 <= m <= n. */
+int gbees_correct_gaussian(gbees_ctx* ctx, const double* y, const double* R, const int32_t* H_idx, int32_t m);
+
+/* Number of active cells. */
+int gbees_count(gbees_ctx* ctx, int64_t* n_cells);
+
+/* Copy the active cells to host memory: idx (cap x n int32) and p (cap
+ * doubles, normalised densities). *n_cells receives the count; when it
+ * exceeds cap only cap cells are written and GBEES_EINVAL is returned.
+ * sorted != 0 returns the cells in lexicographic index order (dimension 0
+ * slowest); otherwise in storage order. */
+int gbees_read_cells(gbees_ctx* ctx, int32_t* idx, double* p, int64_t cap, int64_t* n_cells, int32_t sorted);
+
+/* Mean (n doubles) and covariance (n x n row-major) of the grid density:
+ * mean = (prod h) sum_i x_i p_i, cov = (prod h) sum_i (x_i - mean)(x_i - mean)^T p_i,
+ * both summed exactly. */
+int gbees_moments(gbees_ctx* ctx, double* mean, double* cov);
+
+/* Time, step count, cell count and last normaliser without a propagation. */
+int gbees_get_stats(gbees_ctx* ctx, gbees_stats* stats);
+
+/* Per-phase timing of the library's own kernels (diagnostics). While enabled,
+ * every launch of a phase is bracketed by CUDA events on the context's stream
+ * and its duration is added up; launches counts every kernel the library
+ * issues, enabled or not. Phases: */
+enum {
+    GBEES_PHASE_GROW = 0,    /* directional grow (Sec. 3.3) */
+    GBEES_PHASE_LINK = 1,    /* neighbour links of the new cells (Sec. 4.1) */
+    GBEES_PHASE_UPDATE = 2,  /* DCU + CTU + high-resolution update (Eq. 7, Algorithm 1) */
+    GBEES_PHASE_PRUNE = 3,   /* mark, scan, compaction, relink and rehash (Algorithm 3) */
+    GBEES_PHASE_CORRECT = 4, /* Bayesian update (Eq. 4) */
+    GBEES_PHASE_OTHER = 5,   /* init, read-out, moments */
+    GBEES_NPHASES = 6
+};
+typedef struct {
+    int64_t launches[GBEES_NPHASES]; /* kernel launches per phase since the last reset */
+    double ms[GBEES_NPHASES];        /* summed event time per phase (while enabled) */
+    int64_t timed[GBEES_NPHASES];    /* launches that were timed */
+    int64_t total_launches;          /* all kernel launches since the last reset */
+    int64_t fallback_lookups;        /* edge and second-neighbour lookups that needed the hashtable */
+} gbees_profile;
+
+/* enable != 0 turns event timing on; reset != 0 zeroes the counters. */
+int gbees_profile_control(gbees_ctx* ctx, int32_t enable, int32_t reset);
+int gbees_profile_read(gbees_ctx* ctx, gbees_profile* out);
+
+/* Last error status and message of the context (never NULL). */
+int gbees_get_status(gbees_ctx* ctx);
+const char* gbees_last_error(gbees_ctx* ctx);
+
+/* Free the host context. The workspace stays the caller's. */
+void gbees_destroy(gbees_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBEES_H */

@@ -524,8 +524,9 @@ int orc_init_gaussian(void* h, const double* mean, const double* cov, double t0)
     return normalise(o);
 }
 
-/* Load an explicit cell set; p is taken as given (not renormalised). */
-int orc_init_cells(void* h, const int32_t* idx, const double* p, int64_t N, double t0) {
+/* Load an explicit cell set; p is taken as given (not renormalised); step0
+ * steps are counted as already taken (the prune schedule continues from it). */
+int orc_init_cells(void* h, const int32_t* idx, const double* p, int64_t N, double t0, int64_t step0) {
     Oracle& o = *(Oracle*)h;
     o.P.clear();
     for (int64_t c = 0; c < N; ++c) {
@@ -534,7 +535,7 @@ int orc_init_cells(void* h, const int32_t* idx, const double* p, int64_t N, doub
         o.P[i] = p[c];
     }
     o.t = t0;
-    o.step = 0;
+    o.step = step0;
     return ORC_OK;
 }
 

@@ -82,7 +82,7 @@ def _lib():
             "orc_destroy": (None, [vp]),
             "orc_last_error": (ctypes.c_char_p, [vp]),
             "orc_init_gaussian": (ctypes.c_int, [vp, P(d), P(d), d]),
-            "orc_init_cells": (ctypes.c_int, [vp, P(i32), P(d), i64, d]),
+            "orc_init_cells": (ctypes.c_int, [vp, P(i32), P(d), i64, d, i64]),
             "orc_propagate": (ctypes.c_int, [vp, d, P(_Stats)]),
             "orc_correct_gaussian": (ctypes.c_int, [vp, P(d), P(d), P(i32), i32]),
             "orc_count": (i64, [vp]),
@@ -171,10 +171,10 @@ class Oracle:
         C = np.ascontiguousarray(cov, dtype=np.float64)
         self._check(_lib().orc_init_gaussian(self._h, _dp(m), _dp(C), float(t0)))
 
-    def init_cells(self, idx, p, t0: float = 0.0):
+    def init_cells(self, idx, p, t0: float = 0.0, step0: int = 0):
         I = np.ascontiguousarray(idx, dtype=np.int32).reshape(-1, self.n)
         P = np.ascontiguousarray(p, dtype=np.float64)
-        self._check(_lib().orc_init_cells(self._h, _ip(I), _dp(P), I.shape[0], float(t0)))
+        self._check(_lib().orc_init_cells(self._h, _ip(I), _dp(P), I.shape[0], float(t0), int(step0)))
 
     def propagate(self, t_end: float) -> OracleStats:
         st = _Stats()

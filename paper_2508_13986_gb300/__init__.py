@@ -1,0 +1,6 @@
+"""GB300-native GBEES: sparse-grid propagation of a probability density
+(arXiv 2508.13986) in hand-written sm_103a CUDA behind a C ABI.
+
+Submodules: `gbees` (the binding of include/gbees.h), `workloads` (seeded
+synthetic inputs), `build` (compiles the CUDA library in-tree).
+"""

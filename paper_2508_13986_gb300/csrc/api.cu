@@ -1,0 +1,749 @@
+// Host side of the GBEES C ABI (include/gbees.h): configuration checks,
+// workspace layout, the per-step launch sequence and the host<->device
+// transfers of the public calls. All arithmetic of the method runs in the
+// kernels of gbees_kernels.cuh and gbees_ctu.cuh.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "../../include/gbees.h"
+#include "gbees_kernels.cuh"
+
+namespace gbees {
+cudaError_t launch_ctu_f64(const Model& m, const Bufs& b, int grid, cudaStream_t s);
+cudaError_t launch_ctu_f32(const Model& m, const Bufs& b, int grid, cudaStream_t s);
+}  // namespace gbees
+
+using namespace gbees;
+
+struct gbees_ctx {
+    gbees_config cfg;
+    Model m;
+    Bufs b;
+    cudaStream_t stream;
+    int grid;          // blocks of the fixed launch grid
+    int status;        // sticky status
+    bool has_grid;     // an init succeeded
+    std::string err;
+    DevScalars hs;     // host copy of the device scalars
+    // diagnostics: per-phase launch counts and event timings
+    bool prof_on = false;
+    gbees_profile prof{};
+    std::vector<cudaEvent_t> ev_pool;
+    struct Pending {
+        int phase;
+        cudaEvent_t a, b;
+    };
+    std::vector<Pending> pending;
+    ~gbees_ctx() {
+        for (auto& p : pending) {
+            cudaEventDestroy(p.a);
+            cudaEventDestroy(p.b);
+        }
+        for (auto e : ev_pool) cudaEventDestroy(e);
+    }
+};
+
+namespace {
+
+constexpr size_t ALIGN = 256;
+
+size_t align_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
+
+struct Layout {
+    size_t sc, blk, key[2], q[2], link[2], keep, map, table, total;
+    unsigned long long slots;
+};
+
+int key_bits_for(int n) { return n == 1 ? 32 : 63 / n; }
+
+bool config_ok(const gbees_config* c, std::string* why) {
+    auto fail = [&](const char* s) {
+        if (why) *why = s;
+        return false;
+    };
+    if (!c) return fail("null configuration");
+    if (c->n < 1 || c->n > 6) return fail("n must be 1..6");
+    for (int j = 0; j < c->n; ++j) {
+        if (!(c->h[j] > 0.0) || !std::isfinite(c->h[j])) return fail("cell widths must be positive");
+        if (!std::isfinite(c->x0[j])) return fail("grid origin must be finite");
+    }
+    switch (c->dynamics) {
+        case GBEES_DYN_CONSTANT:
+        case GBEES_DYN_LINEAR:
+            break;
+        case GBEES_DYN_LORENZ63:
+        case GBEES_DYN_LORENZ63_SHIFTED:
+            if (c->n != 3) return fail("Lorenz '63 needs n = 3");
+            break;
+        case GBEES_DYN_LORENZ96:
+            if (c->n < 4) return fail("Lorenz '96 needs n >= 4");
+            break;
+        default:
+            return fail("unknown dynamics");
+    }
+    if (!(c->cfl > 0.0) || !std::isfinite(c->cfl)) return fail("cfl must be positive");
+    if (!(c->thr_rel >= 0.0) || !(c->thr_rel < 1.0)) return fail("thr_rel must be in [0, 1)");
+    if (c->prune_interval < 0) return fail("prune_interval must be >= 0");
+    if (c->precision != GBEES_FP64 && c->precision != GBEES_FP32) return fail("unknown precision");
+    if (c->limiter < 0 || c->limiter > 2) return fail("unknown limiter");
+    int pw = c->probe_width;
+    if (!(pw == 0 || pw == 1 || pw == 2 || pw == 4 || pw == 8 || pw == 16 || pw == 32))
+        return fail("probe_width must be 1, 2, 4, 8, 16 or 32");
+    if (c->max_cells < 1 || c->max_cells > 0x7fffffffll) return fail("max_cells must be in 1..2^31-1");
+    if (!(c->table_factor == 0.0 || c->table_factor >= 1.25)) return fail("table_factor must be 0 or >= 1.25");
+    return true;
+}
+
+bool make_layout(const gbees_config* c, Layout* L) {
+    if (!config_ok(c, nullptr)) return false;
+    const size_t cap = (size_t)c->max_cells;
+    const size_t S = c->precision == GBEES_FP32 ? 4 : 8;
+    const double tf = c->table_factor > 0.0 ? c->table_factor : 2.0;
+    unsigned long long want = (unsigned long long)std::ceil(tf * (double)cap);
+    unsigned long long slots = 64;
+    while (slots < want) slots <<= 1;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = off;
+        off = align_up(off + bytes);
+        return at;
+    };
+    L->sc = take(sizeof(DevScalars));
+    L->blk = take(sizeof(long long) * (GRID_MAX + 1));
+    for (int g = 0; g < 2; ++g) L->key[g] = take(8 * cap);
+    for (int g = 0; g < 2; ++g) L->q[g] = take(S * cap);
+    for (int g = 0; g < 2; ++g) L->link[g] = take((size_t)4 * 2 * c->n * cap);
+    L->keep = take(cap);
+    L->map = take(4 * cap);
+    L->table = take(sizeof(Slot) * slots);
+    L->total = off;
+    L->slots = slots;
+    return true;
+}
+
+void set_err(gbees_ctx* ctx, int st, const std::string& msg) {
+    if (ctx->status == GBEES_OK || st == GBEES_OK) ctx->status = st;
+    ctx->err = msg;
+}
+
+const char* status_text(int st) {
+    switch (st) {
+        case GBEES_OK: return "ok";
+        case GBEES_EINVAL: return "invalid argument";
+        case GBEES_ECAPACITY: return "cell capacity exceeded (max_cells)";
+        case GBEES_EKEYRANGE: return "cell index outside the packed-key range";
+        case GBEES_EDEGENERATE: return "total probability is zero or not finite";
+        case GBEES_ECUDA: return "CUDA error";
+        case GBEES_ETIMEOUT: return "device wait timed out";
+        case GBEES_ETABLE: return "hashtable full";
+    }
+    return "unknown status";
+}
+
+bool cuda_ok(gbees_ctx* ctx, cudaError_t e, const char* where) {
+    if (e == cudaSuccess) return true;
+    set_err(ctx, GBEES_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+    return false;
+}
+
+cudaEvent_t take_event(gbees_ctx* ctx) {
+    if (!ctx->ev_pool.empty()) {
+        cudaEvent_t e = ctx->ev_pool.back();
+        ctx->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Brackets the kernels of one phase: counts them and, when profiling is on,
+// times them with a pair of events on the context's stream.
+struct Phase {
+    gbees_ctx* ctx;
+    int phase;
+    int kernels;
+    cudaEvent_t a = nullptr;
+    Phase(gbees_ctx* c, int ph, int nk) : ctx(c), phase(ph), kernels(nk) {
+        if (ctx->prof_on && (a = take_event(ctx))) cudaEventRecord(a, ctx->stream);
+    }
+    ~Phase() {
+        ctx->prof.launches[phase] += kernels;
+        ctx->prof.total_launches += kernels;
+        if (a) {
+            cudaEvent_t b = take_event(ctx);
+            if (b) {
+                cudaEventRecord(b, ctx->stream);
+                ctx->pending.push_back({phase, a, b});
+            } else {
+                ctx->ev_pool.push_back(a);
+            }
+        }
+    }
+};
+
+// Add up the timed phases whose events have completed (after a stream sync).
+void drain_events(gbees_ctx* ctx) {
+    for (auto& p : ctx->pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            ctx->prof.ms[p.phase] += ms;
+            ctx->prof.timed[p.phase] += 1;
+        }
+        ctx->ev_pool.push_back(p.a);
+        ctx->ev_pool.push_back(p.b);
+    }
+    ctx->pending.clear();
+}
+
+// Copy the device scalars back and fold a device error into the status.
+bool sync_scalars(gbees_ctx* ctx, const char* where) {
+    if (!cuda_ok(ctx, cudaGetLastError(), where)) return false;
+    if (!cuda_ok(ctx, cudaMemcpyAsync(&ctx->hs, ctx->b.sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, ctx->stream),
+                 where))
+        return false;
+    if (!cuda_ok(ctx, cudaStreamSynchronize(ctx->stream), where)) return false;
+    drain_events(ctx);
+    ctx->prof.fallback_lookups = ctx->hs.lookups_fallback;
+    if (ctx->hs.error) {
+        set_err(ctx, ctx->hs.error, std::string(where) + ": " + status_text(ctx->hs.error));
+        return false;
+    }
+    return true;
+}
+
+int guard(gbees_ctx* ctx, bool need_grid) {
+    if (!ctx) return GBEES_EINVAL;
+    if (ctx->status != GBEES_OK) return ctx->status;
+    if (need_grid && !ctx->has_grid) {
+        ctx->err = "no grid: call gbees_init_gaussian or gbees_init_cells first";
+        return GBEES_EINVAL;
+    }
+    return GBEES_OK;
+}
+
+// Run f(N, T) for the configured dimension and precision.
+template <typename F>
+void with_nt(const gbees_ctx* ctx, F&& f) {
+    const bool f32 = ctx->cfg.precision == GBEES_FP32;
+    switch (ctx->cfg.n) {
+#define GBEES_CASE(NN)                                                  \
+    case NN:                                                            \
+        if (f32) f(std::integral_constant<int, NN>{}, float{});        \
+        else f(std::integral_constant<int, NN>{}, double{});           \
+        break;
+        GBEES_CASE(1)
+        GBEES_CASE(2)
+        GBEES_CASE(3)
+        GBEES_CASE(4)
+        GBEES_CASE(5)
+        GBEES_CASE(6)
+#undef GBEES_CASE
+    }
+}
+
+template <int N>
+void launch_link(gbees_ctx* ctx) {
+    const int G = ctx->grid;
+    cudaStream_t s = ctx->stream;
+    switch (ctx->m.probe_width) {
+        case 2: k_link<N, 2><<<G, THREADS, 0, s>>>(ctx->m, ctx->b); break;
+        case 4: k_link<N, 4><<<G, THREADS, 0, s>>>(ctx->m, ctx->b); break;
+        case 8: k_link<N, 8><<<G, THREADS, 0, s>>>(ctx->m, ctx->b); break;
+        case 16: k_link<N, 16><<<G, THREADS, 0, s>>>(ctx->m, ctx->b); break;
+        case 32: k_link<N, 32><<<G, THREADS, 0, s>>>(ctx->m, ctx->b); break;
+        default: k_link<N, 1><<<G, THREADS, 0, s>>>(ctx->m, ctx->b); break;
+    }
+}
+
+cudaError_t launch_ctu(gbees_ctx* ctx) {
+    if (ctx->cfg.precision == GBEES_FP32) return launch_ctu_f32(ctx->m, ctx->b, ctx->grid, ctx->stream);
+    return launch_ctu_f64(ctx->m, ctx->b, ctx->grid, ctx->stream);
+}
+
+// The prune of Algorithm 3 (directional marking, scan, compaction, relink,
+// rehash). It runs only when the device flag prune_now is set.
+void launch_prune(gbees_ctx* ctx) {
+    const int G = ctx->grid;
+    cudaStream_t s = ctx->stream;
+    Phase ph(ctx, GBEES_PHASE_PRUNE, 6);
+    with_nt(ctx, [&](auto NN, auto TT) {
+        constexpr int N = decltype(NN)::value;
+        using T = decltype(TT);
+        k_prune_mark<T><<<G, THREADS, 0, s>>>(ctx->m, ctx->b);
+        k_prune_scatter<N, T><<<G, THREADS, 0, s>>>(ctx->m, ctx->b);
+        k_prune_count<<<G, THREADS, 0, s>>>(ctx->m, ctx->b);
+        k_scan_prune<<<1, THREADS, 0, s>>>(ctx->b, G, ctx->m.cap);
+        k_prune_compact<N, T><<<G, THREADS, 0, s>>>(ctx->m, ctx->b);
+        k_prune_relink<N><<<G, THREADS, 0, s>>>(ctx->m, ctx->b);
+    });
+}
+
+// One time step: grow, link the new cells, flux update (the last block of the
+// update advances t and decides whether a prune is due).
+void launch_step(gbees_ctx* ctx) {
+    const int G = ctx->grid;
+    cudaStream_t s = ctx->stream;
+    with_nt(ctx, [&](auto NN, auto TT) {
+        constexpr int N = decltype(NN)::value;
+        using T = decltype(TT);
+        {
+            Phase ph(ctx, GBEES_PHASE_GROW, 1);
+            k_grow<N, T><<<G, THREADS, 0, s>>>(ctx->m, ctx->b);
+        }
+        Phase ph(ctx, GBEES_PHASE_LINK, 1);
+        launch_link<N>(ctx);
+    });
+    Phase ph(ctx, GBEES_PHASE_UPDATE, 1);
+    launch_ctu(ctx);
+}
+
+// Inverse of a small symmetric positive definite matrix (Cholesky factor,
+// then the inverse of the factor). Returns false if not positive definite.
+bool spd_inverse(int m, const double* A, double* Ainv) {
+    double L[36] = {0}, Li[36] = {0};
+    for (int i = 0; i < m; ++i) {
+        for (int j = 0; j <= i; ++j) {
+            double s = A[i * m + j];
+            for (int k = 0; k < j; ++k) s -= L[i * m + k] * L[j * m + k];
+            if (i == j) {
+                if (!(s > 0.0)) return false;
+                L[i * m + i] = std::sqrt(s);
+            } else {
+                L[i * m + j] = s / L[j * m + j];
+            }
+        }
+    }
+    for (int i = 0; i < m; ++i) {
+        Li[i * m + i] = 1.0 / L[i * m + i];
+        for (int j = 0; j < i; ++j) {
+            double s = 0.0;
+            for (int k = j; k < i; ++k) s -= L[i * m + k] * Li[k * m + j];
+            Li[i * m + j] = s / L[i * m + i];
+        }
+    }
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) {
+            double s = 0.0;
+            for (int k = std::max(i, j); k < m; ++k) s += Li[k * m + i] * Li[k * m + j];
+            Ainv[i * m + j] = s;
+        }
+    return true;
+}
+
+bool box_for(const gbees_ctx* ctx, const double* mean, const double* cov, double r2, InitBox* bx) {
+    const int n = ctx->cfg.n;
+    long long total = 1;
+    for (int k = 0; k < n; ++k) {
+        double ctr = std::round((mean[k] - ctx->cfg.x0[k]) / ctx->cfg.h[k]);
+        double hw = std::ceil(std::sqrt(r2 * cov[k * n + k]) / ctx->cfg.h[k]) + 1.0;
+        if (!std::isfinite(ctr) || !std::isfinite(hw) || std::fabs(ctr) + hw > 2.0e9) return false;
+        bx->lo[k] = (int)(ctr - hw);
+        bx->dims[k] = (long long)(2.0 * hw + 1.0);
+        if (total > (1ll << 42) / bx->dims[k]) return false;
+        total *= bx->dims[k];
+    }
+    bx->total = total;
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t gbees_workspace_bytes(const gbees_config* cfg) {
+    Layout L;
+    if (!make_layout(cfg, &L)) return 0;
+    return L.total;
+}
+
+int gbees_create(const gbees_config* cfg, void* d_workspace, size_t workspace_bytes, void* cuda_stream,
+                 gbees_ctx** out) {
+    if (!out) return GBEES_EINVAL;
+    *out = nullptr;
+    std::string why;
+    if (!config_ok(cfg, &why)) return GBEES_EINVAL;
+    Layout L;
+    make_layout(cfg, &L);
+    if (!d_workspace || workspace_bytes < L.total || ((uintptr_t)d_workspace % ALIGN) != 0) return GBEES_EINVAL;
+    gbees_ctx* ctx = new gbees_ctx();
+    ctx->cfg = *cfg;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    ctx->status = GBEES_OK;
+    ctx->has_grid = false;
+    Model& m = ctx->m;
+    std::memset(&m, 0, sizeof m);
+    m.n = cfg->n;
+    m.dyn = cfg->dynamics;
+    m.limiter = cfg->limiter;
+    m.key_bits = key_bits_for(cfg->n);
+    m.prune_interval = cfg->prune_interval;
+    m.probe_width = cfg->probe_width ? cfg->probe_width : 1;
+    m.cap = cfg->max_cells;
+    m.tmask = L.slots - 1;
+    std::memcpy(m.a, cfg->params, sizeof m.a);
+    m.prod_h = 1.0;
+    for (int j = 0; j < cfg->n; ++j) {
+        m.h[j] = cfg->h[j];
+        m.x0[j] = cfg->x0[j];
+        m.prod_h *= cfg->h[j];
+    }
+    m.thr_rel = cfg->thr_rel;
+    m.cfl = cfg->cfl;
+    char* base = (char*)d_workspace;
+    Bufs& b = ctx->b;
+    b.sc = (DevScalars*)(base + L.sc);
+    b.blk = (long long*)(base + L.blk);
+    for (int g = 0; g < 2; ++g) {
+        b.key[g] = (unsigned long long*)(base + L.key[g]);
+        b.q[g] = (void*)(base + L.q[g]);
+        b.link[g] = (int*)(base + L.link[g]);
+    }
+    b.keep = (unsigned char*)(base + L.keep);
+    b.map = (int*)(base + L.map);
+    b.table = (Slot*)(base + L.table);
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        delete ctx;
+        return GBEES_ECUDA;
+    }
+    ctx->grid = std::min(GRID_MAX, std::max(1, sms * 4));
+    k_reset<<<1, 1, 0, ctx->stream>>>(b.sc, 0.0);
+    if (!sync_scalars(ctx, "create")) {
+        int st = ctx->status;
+        delete ctx;
+        return st;
+    }
+    *out = ctx;
+    return GBEES_OK;
+}
+
+void gbees_destroy(gbees_ctx* ctx) { delete ctx; }
+
+int gbees_profile_control(gbees_ctx* ctx, int32_t enable, int32_t reset) {
+    if (!ctx) return GBEES_EINVAL;
+    if (ctx->prof_on && !enable) {
+        cudaStreamSynchronize(ctx->stream);
+        drain_events(ctx);
+    }
+    ctx->prof_on = enable != 0;
+    if (reset) {
+        cudaStreamSynchronize(ctx->stream);
+        drain_events(ctx);
+        ctx->prof = gbees_profile{};
+    }
+    return GBEES_OK;
+}
+
+int gbees_profile_read(gbees_ctx* ctx, gbees_profile* out) {
+    if (!ctx || !out) return GBEES_EINVAL;
+    cudaStreamSynchronize(ctx->stream);
+    drain_events(ctx);
+    *out = ctx->prof;
+    return GBEES_OK;
+}
+
+int gbees_get_status(gbees_ctx* ctx) { return ctx ? ctx->status : GBEES_EINVAL; }
+
+const char* gbees_last_error(gbees_ctx* ctx) {
+    if (!ctx) return "null context";
+    return ctx->err.c_str();
+}
+
+int gbees_init_gaussian(gbees_ctx* ctx, const double* mean, const double* cov, double t0) {
+    if (!ctx) return GBEES_EINVAL;
+    if (ctx->status != GBEES_OK && ctx->status != GBEES_ECUDA) {  // a new grid clears a poisoned state
+        ctx->status = GBEES_OK;
+        ctx->err.clear();
+    }
+    if (ctx->status != GBEES_OK) return ctx->status;
+    ctx->has_grid = false;
+    const int n = ctx->cfg.n;
+    if (!mean || !cov || !std::isfinite(t0)) {
+        ctx->err = "null mean or covariance";
+        return GBEES_EINVAL;
+    }
+    InitBox bx;
+    std::memset(&bx, 0, sizeof bx);
+    for (int k = 0; k < n; ++k) bx.mean[k] = mean[k];
+    if (!spd_inverse(n, cov, bx.icov)) {
+        ctx->err = "covariance is not symmetric positive definite";
+        return GBEES_EINVAL;
+    }
+    const double thr = ctx->cfg.thr_rel > 0.0 ? ctx->cfg.thr_rel : 1e-300;
+    if (!box_for(ctx, mean, cov, -2.0 * std::log(thr), &bx)) {
+        ctx->err = "initial box too large";
+        return GBEES_EINVAL;
+    }
+    const int G = ctx->grid;
+    cudaStream_t s = ctx->stream;
+    {
+        Phase ph(ctx, GBEES_PHASE_OTHER, 3);
+        k_reset<<<1, 1, 0, s>>>(ctx->b.sc, t0);
+        k_table_clear<<<G, THREADS, 0, s>>>(ctx->m, ctx->b);
+        with_nt(ctx, [&](auto NN, auto) {
+            constexpr int N = decltype(NN)::value;
+            k_init_max<N><<<G, THREADS, 0, s>>>(ctx->m, ctx->b, bx);
+        });
+    }
+    if (!sync_scalars(ctx, "init_gaussian")) return ctx->status;
+    unsigned long long ordk = ctx->hs.tmp_ord;
+    double gmax = 0.0;
+    if (ordk) {
+        unsigned long long bits = (ordk >> 63) ? (ordk & 0x7FFFFFFFFFFFFFFFull) : ~ordk;
+        std::memcpy(&gmax, &bits, 8);
+    }
+    if (!(gmax > 0.0)) {
+        set_err(ctx, GBEES_EDEGENERATE, "initial density underflows on the grid");
+        return ctx->status;
+    }
+    bx.pstar = ctx->cfg.thr_rel * gmax;
+    if (!box_for(ctx, mean, cov, -2.0 * std::log(thr * gmax), &bx)) {
+        ctx->err = "initial box too large";
+        return GBEES_EINVAL;
+    }
+    {
+        Phase ph(ctx, GBEES_PHASE_OTHER, 6);
+        with_nt(ctx, [&](auto NN, auto TT) {
+            constexpr int N = decltype(NN)::value;
+            using T = decltype(TT);
+            k_init_count<N><<<G, THREADS, 0, s>>>(ctx->m, ctx->b, bx);
+            k_scan_blocks<<<1, THREADS, 0, s>>>(ctx->b, G, ctx->m.cap);
+            k_init_write<N, T><<<G, THREADS, 0, s>>>(ctx->m, ctx->b, bx);
+        });
+        k_set_count_from_new<<<1, 1, 0, s>>>(ctx->b.sc);
+        with_nt(ctx, [&](auto NN, auto) {
+            constexpr int N = decltype(NN)::value;
+            launch_link<N>(ctx);
+        });
+        k_finalise<<<1, 1, 0, s>>>(ctx->m, ctx->b.sc, 0);
+    }
+    if (!sync_scalars(ctx, "init_gaussian")) return ctx->status;
+    ctx->has_grid = true;
+    return GBEES_OK;
+}
+
+int gbees_init_cells(gbees_ctx* ctx, const int32_t* idx, const double* p, int64_t N, double t0, int64_t step0) {
+    if (!ctx) return GBEES_EINVAL;
+    if (ctx->status != GBEES_OK && ctx->status != GBEES_ECUDA) {
+        ctx->status = GBEES_OK;
+        ctx->err.clear();
+    }
+    if (ctx->status != GBEES_OK) return ctx->status;
+    ctx->has_grid = false;
+    const int n = ctx->cfg.n;
+    if (N < 0 || N > ctx->m.cap || (N > 0 && (!idx || !p)) || !std::isfinite(t0) || step0 < 0) {
+        ctx->err = "bad cell list (count above max_cells or null pointers)";
+        return GBEES_EINVAL;
+    }
+    cudaStream_t s = ctx->stream;
+    const int G = ctx->grid;
+    Phase ph(ctx, GBEES_PHASE_OTHER, N > 0 ? 6 : 5);
+    k_reset<<<1, 1, 0, s>>>(ctx->b.sc, t0);
+    k_table_clear<<<G, THREADS, 0, s>>>(ctx->m, ctx->b);
+    // stage the inputs in the second buffer set (unused outside a prune)
+    int* d_idx = ctx->b.link[1];
+    double* d_p = reinterpret_cast<double*>(ctx->b.key[1]);
+    if (N > 0) {
+        if (!cuda_ok(ctx, cudaMemcpyAsync(d_idx, idx, sizeof(int32_t) * n * N, cudaMemcpyHostToDevice, s), "init_cells"))
+            return ctx->status;
+        if (!cuda_ok(ctx, cudaMemcpyAsync(d_p, p, sizeof(double) * N, cudaMemcpyHostToDevice, s), "init_cells"))
+            return ctx->status;
+    }
+    with_nt(ctx, [&](auto NN, auto TT) {
+        constexpr int NC = decltype(NN)::value;
+        using T = decltype(TT);
+        if (N > 0) k_init_cells<NC, T><<<G, THREADS, 0, s>>>(ctx->m, ctx->b, d_idx, d_p, N);
+    });
+    k_set_count<<<1, 1, 0, s>>>(ctx->b.sc, N, step0);
+    with_nt(ctx, [&](auto NN, auto) {
+        constexpr int NC = decltype(NN)::value;
+        launch_link<NC>(ctx);
+    });
+    k_finalise<<<1, 1, 0, s>>>(ctx->m, ctx->b.sc, 2);
+    if (!sync_scalars(ctx, "init_cells")) return ctx->status;
+    ctx->has_grid = true;
+    return GBEES_OK;
+}
+
+static void fill_stats(const gbees_ctx* ctx, gbees_stats* st) {
+    if (!st) return;
+    st->steps = ctx->hs.steps_call;
+    st->cell_updates = ctx->hs.updates_call;
+    st->t = ctx->hs.t;
+    st->last_dt = ctx->hs.dt;
+    st->total_steps = ctx->hs.step;
+    st->n_cells = ctx->hs.N;
+    st->norm = ctx->hs.w;
+}
+
+int gbees_propagate(gbees_ctx* ctx, double t_end, gbees_stats* stats) {
+    int st = guard(ctx, true);
+    if (st) return st;
+    if (!std::isfinite(t_end)) {
+        ctx->err = "t_end must be finite";
+        return GBEES_EINVAL;
+    }
+    cudaStream_t s = ctx->stream;
+    {
+        Phase ph(ctx, GBEES_PHASE_OTHER, 1);
+        k_begin<<<1, 1, 0, s>>>(ctx->b.sc, t_end);
+    }
+    if (!sync_scalars(ctx, "propagate")) return ctx->status;
+    const int K = ctx->cfg.prune_interval;
+    long long host_step = ctx->hs.step;
+    long long batch = 4;
+    while (!ctx->hs.done) {
+        for (long long i = 0; i < batch; ++i) {
+            ++host_step;
+            launch_step(ctx);
+            if (K > 0 && host_step % K == 0) launch_prune(ctx);
+        }
+        if (!sync_scalars(ctx, "propagate")) return ctx->status;
+        host_step = ctx->hs.step;
+        if (ctx->hs.done) break;
+        const double rem = ctx->hs.t_target - ctx->hs.t;
+        const double est = ctx->hs.dt > 0.0 ? rem / ctx->hs.dt : 1.0;
+        batch = (long long)std::min(256.0, std::max(1.0, std::ceil(est * 1.02) + 1.0));
+    }
+    fill_stats(ctx, stats);
+    return GBEES_OK;
+}
+
+int gbees_correct_gaussian(gbees_ctx* ctx, const double* y, const double* R, const int32_t* H_idx, int32_t m) {
+    int st = guard(ctx, true);
+    if (st) return st;
+    const int n = ctx->cfg.n;
+    if (!y || !R || !H_idx || m < 1 || m > n) {
+        ctx->err = "bad measurement";
+        return GBEES_EINVAL;
+    }
+    Meas ms;
+    std::memset(&ms, 0, sizeof ms);
+    ms.m = m;
+    for (int a = 0; a < m; ++a) {
+        if (H_idx[a] < 0 || H_idx[a] >= n || !std::isfinite(y[a])) {
+            ctx->err = "bad measurement index or value";
+            return GBEES_EINVAL;
+        }
+        ms.H[a] = H_idx[a];
+        ms.y[a] = y[a];
+    }
+    if (!spd_inverse(m, R, ms.Rinv)) {
+        ctx->err = "measurement covariance is not symmetric positive definite";
+        return GBEES_EINVAL;
+    }
+    const int G = ctx->grid;
+    cudaStream_t s = ctx->stream;
+    {
+        Phase ph(ctx, GBEES_PHASE_CORRECT, 1);
+        with_nt(ctx, [&](auto NN, auto TT) {
+            constexpr int N = decltype(NN)::value;
+            using T = decltype(TT);
+            k_correct<N, T><<<G, THREADS, 0, s>>>(ctx->m, ctx->b, ms);
+        });
+    }
+    launch_prune(ctx);
+    if (!sync_scalars(ctx, "correct")) return ctx->status;
+    return GBEES_OK;
+}
+
+int gbees_count(gbees_ctx* ctx, int64_t* n_cells) {
+    int st = guard(ctx, true);
+    if (st) return st;
+    if (!n_cells) return GBEES_EINVAL;
+    if (!sync_scalars(ctx, "count")) return ctx->status;
+    *n_cells = ctx->hs.N;
+    return GBEES_OK;
+}
+
+int gbees_get_stats(gbees_ctx* ctx, gbees_stats* stats) {
+    int st = guard(ctx, true);
+    if (st) return st;
+    if (!sync_scalars(ctx, "get_stats")) return ctx->status;
+    fill_stats(ctx, stats);
+    return GBEES_OK;
+}
+
+int gbees_read_cells(gbees_ctx* ctx, int32_t* idx, double* p, int64_t cap, int64_t* n_cells, int32_t sorted) {
+    int st = guard(ctx, true);
+    if (st) return st;
+    if (!sync_scalars(ctx, "read_cells")) return ctx->status;
+    const long long N = ctx->hs.N;
+    if (n_cells) *n_cells = N;
+    if (N == 0) return GBEES_OK;
+    if ((!idx || !p) && cap > 0) return GBEES_EINVAL;
+    const int n = ctx->cfg.n;
+    const int g = ctx->hs.gen;
+    int* d_idx = ctx->b.link[g ^ 1];
+    double* d_p = reinterpret_cast<double*>(ctx->b.key[g ^ 1]);
+    const int G = ctx->grid;
+    cudaStream_t s = ctx->stream;
+    {
+        Phase ph(ctx, GBEES_PHASE_OTHER, 1);
+        with_nt(ctx, [&](auto NN, auto TT) {
+            constexpr int NC = decltype(NN)::value;
+            using T = decltype(TT);
+            k_readout<NC, T><<<G, THREADS, 0, s>>>(ctx->m, ctx->b, d_idx, d_p);
+        });
+    }
+    std::vector<int32_t> hidx((size_t)N * n);
+    std::vector<double> hp((size_t)N);
+    if (!cuda_ok(ctx, cudaMemcpyAsync(hidx.data(), d_idx, sizeof(int32_t) * n * N, cudaMemcpyDeviceToHost, s), "read_cells"))
+        return ctx->status;
+    if (!cuda_ok(ctx, cudaMemcpyAsync(hp.data(), d_p, sizeof(double) * N, cudaMemcpyDeviceToHost, s), "read_cells"))
+        return ctx->status;
+    if (!cuda_ok(ctx, cudaStreamSynchronize(s), "read_cells")) return ctx->status;
+    std::vector<long long> order((size_t)N);
+    std::iota(order.begin(), order.end(), 0ll);
+    if (sorted) {
+        std::sort(order.begin(), order.end(), [&](long long a, long long c) {
+            return std::lexicographical_compare(&hidx[a * n], &hidx[a * n] + n, &hidx[c * n], &hidx[c * n] + n);
+        });
+    }
+    const long long w = std::min<long long>(N, cap);
+    for (long long r = 0; r < w; ++r) {
+        std::memcpy(idx + r * n, &hidx[order[r] * n], sizeof(int32_t) * n);
+        p[r] = hp[order[r]];
+    }
+    return N > cap ? GBEES_EINVAL : GBEES_OK;
+}
+
+int gbees_moments(gbees_ctx* ctx, double* mean, double* cov) {
+    int st = guard(ctx, true);
+    if (st) return st;
+    if (!mean || !cov) return GBEES_EINVAL;
+    const int n = ctx->cfg.n;
+    const int G = ctx->grid;
+    cudaStream_t s = ctx->stream;
+    DevScalars* sc = ctx->b.sc;
+    Phase ph(ctx, GBEES_PHASE_OTHER, 6);
+    k_moments_clear<<<1, THREADS, 0, s>>>(sc);
+    with_nt(ctx, [&](auto NN, auto TT) {
+        constexpr int NC = decltype(NN)::value;
+        using T = decltype(TT);
+        k_moments<NC, T><<<G, THREADS, 0, s>>>(ctx->m, ctx->b, 0, sc->mom_mean);
+    });
+    k_moments_final<<<1, 32, 0, s>>>(ctx->m, sc, sc->mom_mean, n);
+    k_moments_clear<<<1, THREADS, 0, s>>>(sc);
+    with_nt(ctx, [&](auto NN, auto TT) {
+        constexpr int NC = decltype(NN)::value;
+        using T = decltype(TT);
+        k_moments<NC, T><<<G, THREADS, 0, s>>>(ctx->m, ctx->b, 1, sc->mom_mean);
+    });
+    k_moments_final<<<1, 32, 0, s>>>(ctx->m, sc, sc->mom_out, n * (n + 1) / 2);
+    if (!sync_scalars(ctx, "moments")) return ctx->status;
+    for (int a = 0; a < n; ++a) mean[a] = ctx->hs.mom_mean[a];
+    int slot = 0;
+    for (int a = 0; a < n; ++a)
+        for (int e = a; e < n; ++e, ++slot) cov[a * n + e] = cov[e * n + a] = ctx->hs.mom_out[slot];
+    return GBEES_OK;
+}
+
+}  // extern "C"

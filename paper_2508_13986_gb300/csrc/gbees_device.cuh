@@ -1,0 +1,523 @@
+// Device-side building blocks of the GBEES library: layout of the workspace,
+// packed cell keys, the open-addressing hashtable, the drift models, the exact
+// fixed-point accumulator and block reductions.
+#pragma once
+
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gbees {
+
+namespace cg = cooperative_groups;
+
+constexpr int MAXN = 6;
+constexpr int THREADS = 256;
+constexpr int WARPS = THREADS / 32;
+constexpr int GRID_MAX = 8192;                       // blocks of the fixed launch grid (upper bound)
+constexpr unsigned long long EMPTY_KEY = ~0ull;      // free hashtable slot
+
+// Exact accumulator: NDIG signed 64-bit cells, each collecting 32-bit digits of a
+// fixed-point number whose lowest bit weighs 2^ACC_LSB. The window
+// [2^-128, 2^64) holds every density sum and moment of the workloads; terms
+// below 2^-128 are truncated (deterministically), terms of 2^64 or more raise
+// an error. Up to 2^31 terms per reduction need no carry.
+constexpr int NDIG = 6;
+constexpr int ACC_LSB = -128;
+
+enum { DYN_CONSTANT = 0, DYN_LINEAR = 1, DYN_LORENZ63 = 2, DYN_LORENZ63_SHIFTED = 3, DYN_LORENZ96 = 4 };
+enum { LIM_MC = 0, LIM_NONE = 1, LIM_LW = 2 };
+enum {
+    ST_OK = 0,
+    ST_EINVAL = -1,
+    ST_ECAPACITY = -2,
+    ST_EKEYRANGE = -3,
+    ST_EDEGENERATE = -4,
+    ST_ECUDA = -5,
+    ST_ETIMEOUT = -6,
+    ST_ETABLE = -7
+};
+
+struct alignas(16) Slot {
+    unsigned long long key;
+    long long val;  // cell index (low 32 bits used)
+};
+
+// Scalars that live on the device so that a whole step needs no host round trip.
+struct alignas(256) DevScalars {
+    long long N;          // active cells (grows during grow)
+    long long N_prev;     // cells before the current grow
+    long long N_new;      // cells surviving the current prune
+    double t;             // time
+    double t_target;      // end of the current propagate call
+    double dt;            // last step
+    unsigned long long maxrate_bits;      // max CFL rate over the cells (non-negative double bits)
+    unsigned long long maxrate_new_bits;  // max rate over the survivors of a prune
+    unsigned long long maxq_ord;          // order key of the running max of Q
+    double maxq;          // max of Q after the last finalisation
+    double w;             // (prod h) * sum Q at the last finalisation
+    double scale;         // 1 / w, applied by the next step
+    long long acc[NDIG];  // exact sum of Q
+    long long step;       // steps since init
+    long long steps_call; // steps of the current propagate call
+    long long updates_call;  // cell updates of the current propagate call
+    long long lookups_fallback;  // edge/second-neighbour lookups that needed the hashtable
+    int pbuf;             // current Q buffer
+    int gen;              // current key/link buffer
+    int done;             // t reached t_target
+    int error;            // first error status (0 = none)
+    int prune_now;        // the step just taken is a prune step
+    unsigned int ticket;  // last-block election
+    unsigned long long tmp_ord;  // scratch maximum (init)
+    long long mom[28][NDIG];     // exact sums for moments
+    double mom_mean[MAXN];       // mean, input of the covariance pass
+    double mom_out[28];          // moments times prod h
+};
+
+// Everything a kernel needs to know about the model and the grid (by value).
+struct Model {
+    int n;
+    int dyn;
+    int limiter;
+    int key_bits;
+    int prune_interval;
+    int probe_width;
+    long long cap;               // cell capacity
+    unsigned long long tmask;    // hashtable slots - 1
+    double a[64];                // model parameters
+    double h[MAXN];
+    double x0[MAXN];
+    double thr_rel;
+    double cfl;
+    double prod_h;
+};
+
+// Device buffers (by value). link[g] holds 2n arrays of cap int32: entry
+// (2j + s) * cap + c is the index of the neighbour of cell c one step down
+// (s = 0) or up (s = 1) in dimension j, or -1.
+struct Bufs {
+    unsigned long long* key[2];
+    void* q[2];
+    int* link[2];
+    unsigned char* keep;
+    int* map;
+    Slot* table;
+    DevScalars* sc;
+    long long* blk;
+};
+
+// ------------------------------------------------------------------ keys
+
+template <int N>
+__device__ __forceinline__ bool pack_key(const Model& m, const int* I, unsigned long long& k) {
+    const int b = m.key_bits;
+    const long long bias = 1ll << (b - 1);
+    const long long lim = 1ll << b;
+    k = 0;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        long long v = (long long)I[j] + bias;
+        if (v < 0 || v >= lim) return false;
+        k = (k << b) | (unsigned long long)v;
+    }
+    return true;
+}
+
+template <int N>
+__device__ __forceinline__ void unpack_key(const Model& m, unsigned long long k, int* I) {
+    const int b = m.key_bits;
+    const long long bias = 1ll << (b - 1);
+    const unsigned long long mask = (b >= 64) ? ~0ull : ((1ull << b) - 1);
+#pragma unroll
+    for (int j = N - 1; j >= 0; --j) {
+        I[j] = (int)((long long)(k & mask) - bias);
+        k >>= b;
+    }
+}
+
+// murmur3 64-bit finaliser
+__device__ __forceinline__ unsigned long long mix64(unsigned long long x) {
+    x ^= x >> 33;
+    x *= 0xff51afd7ed558ccdull;
+    x ^= x >> 33;
+    x *= 0xc4ceb9fe1a85ec53ull;
+    x ^= x >> 33;
+    return x;
+}
+
+// ------------------------------------------------------------------ hashtable
+// Open addressing with linear probing (Sec. 4.2); keys are claimed with
+// atomicCAS (the concurrent insertion of Algorithm 2 without staging).
+
+__device__ __forceinline__ int table_find(const Model& m, const Slot* __restrict__ T, unsigned long long key) {
+    unsigned long long h = mix64(key) & m.tmask;
+    for (unsigned long long probe = 0; probe <= m.tmask; ++probe) {
+        ulonglong2 s = __ldcg(reinterpret_cast<const ulonglong2*>(T + h));
+        if (s.x == key) return (int)(long long)s.y;
+        if (s.x == EMPTY_KEY) return -1;
+        h = (h + 1) & m.tmask;
+    }
+    return -1;
+}
+
+// Cooperative lookup: a tile of W lanes probes W consecutive slots per round
+// (one coalesced load) and the lowest lane that sees the key or an empty slot
+// decides. All lanes of the tile must call it with the same key.
+template <int W>
+__device__ __forceinline__ int table_find_tile(const Model& m, const Slot* __restrict__ T, unsigned long long key,
+                                               cg::thread_block_tile<W> tile) {
+    unsigned long long base = mix64(key) & m.tmask;
+    const int lane = tile.thread_rank();
+    for (unsigned long long probe = 0; probe <= m.tmask; probe += W) {
+        unsigned long long h = (base + probe + lane) & m.tmask;
+        ulonglong2 s = __ldcg(reinterpret_cast<const ulonglong2*>(T + h));
+        unsigned hit = tile.ballot(s.x == key);
+        unsigned emp = tile.ballot(s.x == EMPTY_KEY);
+        if (hit | emp) {
+            int first_hit = hit ? __ffs(hit) - 1 : W;
+            int first_emp = emp ? __ffs(emp) - 1 : W;
+            if (first_hit < first_emp) {
+                long long v = tile.shfl((long long)s.y, first_hit);
+                return (int)v;
+            }
+            return -1;
+        }
+    }
+    return -1;
+}
+
+// Insert key if absent. Returns 1 and the slot when this thread claimed a new
+// slot, 0 when the key is present, -1 when the table is full.
+__device__ __forceinline__ int table_claim(const Model& m, Slot* T, unsigned long long key, unsigned long long* slot) {
+    unsigned long long h = mix64(key) & m.tmask;
+    for (unsigned long long probe = 0; probe <= m.tmask; ++probe) {
+        unsigned long long k = *reinterpret_cast<volatile unsigned long long*>(&T[h].key);
+        if (k == key) return 0;
+        if (k == EMPTY_KEY) {
+            unsigned long long old = atomicCAS(&T[h].key, EMPTY_KEY, key);
+            if (old == EMPTY_KEY) {
+                *slot = h;
+                return 1;
+            }
+            if (old == key) return 0;
+        }
+        h = (h + 1) & m.tmask;
+    }
+    return -1;
+}
+
+// ------------------------------------------------------------------ errors
+
+__device__ __forceinline__ void set_error(DevScalars* sc, int code) { atomicCAS(&sc->error, 0, code); }
+
+__device__ __forceinline__ long long warp_aggregated_add(long long* counter, int count = 1) {
+    cg::coalesced_group g = cg::coalesced_threads();
+    long long base = 0;
+    int total = g.size() * count;
+    if (g.thread_rank() == 0) base = (long long)atomicAdd((unsigned long long*)counter, (unsigned long long)total);
+    base = g.shfl(base, 0);
+    return base + (long long)g.thread_rank() * count;
+}
+
+// ------------------------------------------------------------------ drift models
+
+template <typename R>
+struct Ar;  // IEEE operations without contraction into fused multiply-add
+
+template <>
+struct Ar<double> {
+    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+    static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+};
+template <>
+struct Ar<float> {
+    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+};
+
+// f_j(y) with the evaluation order written out (no fused multiply-add), so that
+// the FP64 velocities that take the grow / prune / CFL decisions are the IEEE
+// values of the textbook expressions.
+template <typename R, int N>
+__device__ __forceinline__ R drift(const Model& m, int dyn, const R* y, int j) {
+    using A = Ar<R>;
+    switch (dyn) {
+        case DYN_CONSTANT:
+            return (R)m.a[j];
+        case DYN_LINEAR: {
+            R s = 0;
+#pragma unroll
+            for (int k = 0; k < N; ++k) s = A::add(s, A::mul((R)m.a[j * N + k], y[k]));
+            return A::add(s, (R)m.a[N * N + j]);
+        }
+        case DYN_LORENZ63:
+            if (N != 3) return 0;
+            if (j == 0) return A::mul((R)m.a[0], A::sub(y[1], y[0]));
+            if (j == 1) return A::sub(A::mul(y[0], A::sub((R)m.a[1], y[2 % N])), y[1]);
+            return A::sub(A::mul(y[0], y[1]), A::mul((R)m.a[2], y[2 % N]));
+        case DYN_LORENZ63_SHIFTED:
+            if (N != 3) return 0;
+            if (j == 0) return A::mul((R)m.a[0], A::sub(y[1], y[0]));
+            if (j == 1) return A::sub(-y[1], A::mul(y[0], y[2 % N]));
+            return A::sub(A::add(A::mul(-(R)m.a[1], y[2 % N]), A::mul(y[0], y[1])), A::mul((R)m.a[1], (R)m.a[2]));
+        case DYN_LORENZ96: {
+            const int jp = (j + 1) % N, jm2 = (j + N - 2) % N, jm1 = (j + N - 1) % N;
+            return A::add(A::sub(A::mul(A::sub(y[jp], y[jm2]), y[jm1]), y[j]), (R)m.a[0]);
+        }
+    }
+    return 0;
+}
+
+// Centre coordinate x0_k + i_k h_k and lower-face coordinate x0_k + (i_k - 1/2) h_k,
+// evaluated exactly as written (one rounded product, one rounded sum).
+__device__ __forceinline__ double centre64(const Model& m, int k, int i) {
+    return __dadd_rn(m.x0[k], __dmul_rn((double)i, m.h[k]));
+}
+__device__ __forceinline__ double lowface64(const Model& m, int k, int i) {
+    return __dadd_rn(m.x0[k], __dmul_rn((double)i - 0.5, m.h[k]));
+}
+
+// FP64 face velocity f_j at the lower face of cell I in dimension j (Eq. 7).
+template <int N>
+__device__ __forceinline__ double face_velocity64(const Model& m, const int* I, int j) {
+    double y[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) y[k] = (k == j) ? lowface64(m, k, I[k]) : centre64(m, k, I[k]);
+    return drift<double, N>(m, m.dyn, y, j);
+}
+
+// FP64 CFL rate sum_j |f_j(x_{i-e_j/2})| / h_j (Eq. 8 with |f|).
+template <int N>
+__device__ __forceinline__ double cfl_rate64(const Model& m, const int* I) {
+    double r = 0.0;
+#pragma unroll
+    for (int j = 0; j < N; ++j) r = __dadd_rn(r, __ddiv_rn(fabs(face_velocity64<N>(m, I, j)), m.h[j]));
+    return r;
+}
+
+// ------------------------------------------------------------------ exact accumulator
+
+// Add x (a finite double) to the digits. Sets err on a non-finite or too
+// large term.
+__device__ __forceinline__ void acc_add(long long (&d)[NDIG], double x, int& err) {
+    unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    int ex = (int)((bits >> 52) & 0x7ff);
+    unsigned long long mt = bits & 0xFFFFFFFFFFFFFull;
+    if (ex == 0x7ff) { err = 1; return; }
+    if (ex == 0) {
+        if (mt == 0) return;
+        ex = 1;
+    } else {
+        mt |= 1ull << 52;
+    }
+    int pos = ex - 1075 - ACC_LSB;  // x = mt * 2^(pos + ACC_LSB)
+    if (pos < 0) {
+        if (pos <= -64) return;
+        mt >>= -pos;
+        pos = 0;
+        if (mt == 0) return;
+    }
+    if (pos > 32 * NDIG - 53 - 1) { err = 1; return; }
+    const bool neg = (bits >> 63) != 0;
+    const int k = pos >> 5, r = pos & 31;
+    const unsigned long long lo = mt << r;
+    const unsigned long long hi = r ? (mt >> (64 - r)) : 0ull;
+    const long long d0 = (long long)(lo & 0xffffffffull), d1 = (long long)(lo >> 32), d2 = (long long)(hi & 0xffffffffull);
+#pragma unroll
+    for (int q = 0; q < NDIG; ++q) {
+        long long v = (q == k) ? d0 : (q == k + 1) ? d1 : (q == k + 2) ? d2 : 0;
+        d[q] += neg ? -v : v;
+    }
+}
+
+// Round the exact value sum_q D[q] 2^(32 q + ACC_LSB) once to the nearest double.
+__device__ inline double acc_to_double(const long long* D) {
+    long long c[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) c[q] = q < NDIG ? D[q] : 0;
+    for (int q = 0; q < 7; ++q) {
+        long long carry = c[q] >> 32;  // floor division by 2^32
+        c[q] -= carry * 4294967296ll;
+        c[q + 1] += carry;
+    }
+    const bool neg = c[7] < 0;
+    unsigned long long W[4];
+    {
+        unsigned int mag[8];
+        unsigned long long carry = 1;
+        for (int q = 0; q < 8; ++q) {
+            unsigned int v = (unsigned int)(unsigned long long)c[q];
+            if (neg) {
+                unsigned long long s = (unsigned long long)(~v) + carry;
+                mag[q] = (unsigned int)s;
+                carry = s >> 32;
+            } else {
+                mag[q] = v;
+            }
+        }
+        for (int q = 0; q < 4; ++q) W[q] = (unsigned long long)mag[2 * q] | ((unsigned long long)mag[2 * q + 1] << 32);
+    }
+    int top = -1;
+    for (int q = 3; q >= 0; --q)
+        if (W[q]) { top = q; break; }
+    if (top < 0) return 0.0;
+    const int msb = 64 * top + 63 - __clzll((long long)W[top]);
+    auto extract = [&](int shift) -> unsigned long long {  // bits [shift, shift + 64)
+        if (shift < 0) return W[0] << (-shift);
+        int wq = shift >> 6, r = shift & 63;
+        unsigned long long lo = wq < 4 ? W[wq] >> r : 0ull;
+        unsigned long long hi = (r && wq + 1 < 4) ? W[wq + 1] << (64 - r) : 0ull;
+        return lo | hi;
+    };
+    double result;
+    if (msb < 53) {
+        result = ldexp((double)W[0], ACC_LSB);
+    } else {
+        const int sh = msb - 53;  // the 54 bits [sh, msb] hold mantissa + round bit
+        unsigned long long v54 = extract(sh) & ((1ull << 54) - 1);
+        unsigned long long v = v54 >> 1;
+        const unsigned long long round = v54 & 1ull;
+        bool sticky = false;
+        for (int q = 0; q < 4 && !sticky; ++q) {
+            int lo_bit = 64 * q;
+            if (lo_bit >= sh) break;
+            int nb = sh - lo_bit;
+            unsigned long long mask = nb >= 64 ? ~0ull : ((1ull << nb) - 1);
+            sticky = (W[q] & mask) != 0;
+        }
+        if (round && (sticky || (v & 1ull))) v += 1;
+        result = ldexp((double)v, msb - 52 + ACC_LSB);
+    }
+    return neg ? -result : result;
+}
+
+// Order-preserving map of doubles onto unsigned 64-bit keys (for atomicMax).
+__device__ __forceinline__ unsigned long long ord_key(double x) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double ord_val(unsigned long long k) {
+    unsigned long long b = (k >> 63) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k;
+    return __longlong_as_double((long long)b);
+}
+
+// Block-wide reduction of the digits and of a maximum, then one atomic per
+// digit into global memory. All threads of the block must call it.
+__device__ __forceinline__ void block_reduce_acc_max(long long (&d)[NDIG], double mx, long long* g_acc,
+                                                     unsigned long long* g_ord) {
+    __shared__ long long s_acc[WARPS][NDIG];
+    __shared__ double s_mx[WARPS];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NDIG; ++q) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) d[q] += __shfl_down_sync(0xffffffffu, d[q], off);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, off));
+    if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < NDIG; ++q) s_acc[wid][q] = d[q];
+        s_mx[wid] = mx;
+    }
+    __syncthreads();
+    if (threadIdx.x < NDIG) {
+        long long v = 0;
+        for (int w = 0; w < WARPS; ++w) v += s_acc[w][threadIdx.x];
+        if (v) atomicAdd((unsigned long long*)&g_acc[threadIdx.x], (unsigned long long)v);
+    }
+    if (threadIdx.x == 32 && g_ord) {
+        double m = -INFINITY;
+        for (int w = 0; w < WARPS; ++w) m = fmax(m, s_mx[w]);
+        if (m > -INFINITY) atomicMax(g_ord, ord_key(m));
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ double block_max(double mx) {
+    __shared__ double s_m[WARPS];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, off));
+    if ((threadIdx.x & 31) == 0) s_m[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    double m = -INFINITY;
+    for (int w = 0; w < WARPS; ++w) m = fmax(m, s_m[w]);
+    __syncthreads();
+    return m;
+}
+
+// True in every thread of exactly one block: the last one to arrive.
+__device__ __forceinline__ bool last_block(DevScalars* sc) {
+    __shared__ bool s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned int t = atomicAdd(&sc->ticket, 1u);
+        s_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (s_last) __threadfence();
+    return s_last;
+}
+
+// Normalisation scalars from the exact sum and the running maximum; also the
+// end of a prune (swap buffers, new count, new CFL maximum).
+// mode bit 1: a prune just completed; mode bit 2: keep w = 1 (cells loaded as given).
+__device__ __forceinline__ void finalise_norm(const Model& m, DevScalars* sc, int mode) {
+    if (mode & 1) {
+        sc->N = sc->N_new;
+        sc->gen ^= 1;
+        sc->pbuf ^= 1;
+        sc->maxrate_bits = sc->maxrate_new_bits;
+        sc->maxrate_new_bits = 0;
+        sc->prune_now = 0;
+    }
+    sc->N_prev = sc->N;
+    sc->maxq = sc->maxq_ord ? ord_val(sc->maxq_ord) : 0.0;
+    if (mode & 2) {
+        sc->w = 1.0;
+        sc->scale = 1.0;
+    } else {
+        long long D[NDIG];
+        for (int q = 0; q < NDIG; ++q) D[q] = *(volatile long long*)&sc->acc[q];
+        double s = acc_to_double(D);
+        double w = m.prod_h * s;
+        sc->w = w;
+        if (!(w > 0.0) || !isfinite(w)) {
+            set_error(sc, ST_EDEGENERATE);
+            sc->scale = 0.0;
+        } else {
+            sc->scale = 1.0 / w;
+        }
+    }
+    for (int q = 0; q < NDIG; ++q) sc->acc[q] = 0;
+    sc->maxq_ord = 0;
+    sc->ticket = 0;
+    if (sc->N == 0 && !(mode & 2)) set_error(sc, ST_EDEGENERATE);
+}
+
+// Exclusive prefix of a 0/1 flag over the block (in thread order) and the total.
+__device__ __forceinline__ int block_exclusive_scan(int flag, int& total) {
+    __shared__ int s_w[WARPS];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned bal = __ballot_sync(0xffffffffu, flag);
+    int in_warp = __popc(bal & ((1u << lane) - 1u));
+    if (lane == 0) s_w[wid] = __popc(bal);
+    __syncthreads();
+    int before = 0, tot = 0;
+    for (int w = 0; w < WARPS; ++w) {
+        int v = s_w[w];
+        if (w < wid) before += v;
+        tot += v;
+    }
+    __syncthreads();
+    total = tot;
+    return before + in_warp;
+}
+
+template <typename T>
+__device__ __forceinline__ T ldq(const T* p) { return __ldg(p); }
+
+}  // namespace gbees

@@ -1,0 +1,342 @@
+"""Thin Python binding of the GBEES C ABI (include/gbees.h).
+
+The module-level functions carry the C names and only marshal arguments
+(ctypes); every step of the method runs in the CUDA library
+`_lib/libgbees_gb300.so`. PyTorch provides the device workspace and the CUDA
+stream. Loading fails with an error when the library has not been built: there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional, Sequence, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libgbees_gb300.so")
+
+GBEES_OK, GBEES_EINVAL, GBEES_ECAPACITY, GBEES_EKEYRANGE = 0, -1, -2, -3
+GBEES_EDEGENERATE, GBEES_ECUDA, GBEES_ETIMEOUT, GBEES_ETABLE = -4, -5, -6, -7
+STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ECAPACITY", -3: "EKEYRANGE", -4: "EDEGENERATE", -5: "ECUDA",
+                -6: "ETIMEOUT", -7: "ETABLE"}
+GBEES_DYN_CONSTANT, GBEES_DYN_LINEAR, GBEES_DYN_LORENZ63, GBEES_DYN_LORENZ63_SHIFTED, GBEES_DYN_LORENZ96 = range(5)
+GBEES_LIM_MC, GBEES_LIM_NONE, GBEES_LIM_LW = range(3)
+GBEES_FP64, GBEES_FP32 = 0, 1
+
+
+class gbees_config(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int32),
+        ("dynamics", ctypes.c_int32),
+        ("params", ctypes.c_double * 64),
+        ("h", ctypes.c_double * 6),
+        ("x0", ctypes.c_double * 6),
+        ("thr_rel", ctypes.c_double),
+        ("cfl", ctypes.c_double),
+        ("prune_interval", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("limiter", ctypes.c_int32),
+        ("probe_width", ctypes.c_int32),
+        ("max_cells", ctypes.c_int64),
+        ("table_factor", ctypes.c_double),
+    ]
+
+
+class gbees_stats(ctypes.Structure):
+    _fields_ = [
+        ("steps", ctypes.c_int64),
+        ("cell_updates", ctypes.c_int64),
+        ("t", ctypes.c_double),
+        ("last_dt", ctypes.c_double),
+        ("total_steps", ctypes.c_int64),
+        ("n_cells", ctypes.c_int64),
+        ("norm", ctypes.c_double),
+    ]
+
+
+GBEES_NPHASES = 6
+PHASE_NAMES = ("grow", "link", "update", "prune", "correct", "other")
+
+
+class gbees_profile(ctypes.Structure):
+    _fields_ = [
+        ("launches", ctypes.c_int64 * GBEES_NPHASES),
+        ("ms", ctypes.c_double * GBEES_NPHASES),
+        ("timed", ctypes.c_int64 * GBEES_NPHASES),
+        ("total_launches", ctypes.c_int64),
+        ("fallback_lookups", ctypes.c_int64),
+    ]
+
+
+_P = ctypes.POINTER
+_vp, _d, _i32, _i64 = ctypes.c_void_p, ctypes.c_double, ctypes.c_int32, ctypes.c_int64
+_SIGNATURES = {
+    "gbees_workspace_bytes": (ctypes.c_size_t, [_P(gbees_config)]),
+    "gbees_create": (ctypes.c_int, [_P(gbees_config), _vp, ctypes.c_size_t, _vp, _P(_vp)]),
+    "gbees_init_gaussian": (ctypes.c_int, [_vp, _P(_d), _P(_d), _d]),
+    "gbees_init_cells": (ctypes.c_int, [_vp, _P(_i32), _P(_d), _i64, _d, _i64]),
+    "gbees_propagate": (ctypes.c_int, [_vp, _d, _P(gbees_stats)]),
+    "gbees_correct_gaussian": (ctypes.c_int, [_vp, _P(_d), _P(_d), _P(_i32), _i32]),
+    "gbees_count": (ctypes.c_int, [_vp, _P(_i64)]),
+    "gbees_read_cells": (ctypes.c_int, [_vp, _P(_i32), _P(_d), _i64, _P(_i64), _i32]),
+    "gbees_moments": (ctypes.c_int, [_vp, _P(_d), _P(_d)]),
+    "gbees_get_stats": (ctypes.c_int, [_vp, _P(gbees_stats)]),
+    "gbees_get_status": (ctypes.c_int, [_vp]),
+    "gbees_profile_control": (ctypes.c_int, [_vp, _i32, _i32]),
+    "gbees_profile_read": (ctypes.c_int, [_vp, _P(gbees_profile)]),
+    "gbees_last_error": (ctypes.c_char_p, [_vp]),
+    "gbees_destroy": (None, [_vp]),
+}
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load the CUDA library; raise if it is missing (no fallback path exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"GBEES CUDA library not built: {path} is missing "
+                               "(run python -c 'import __graft_entry__ as g; g.build()')")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _f(name):
+    return getattr(load_library(), name)
+
+
+# ---- the C entry points under their own names (argument marshalling only) ----
+
+def gbees_workspace_bytes(cfg: gbees_config) -> int:
+    return int(_f("gbees_workspace_bytes")(ctypes.byref(cfg)))
+
+
+def gbees_create(cfg: gbees_config, d_workspace: int, nbytes: int, stream: int) -> Tuple[int, int]:
+    out = _vp()
+    rc = _f("gbees_create")(ctypes.byref(cfg), _vp(d_workspace), nbytes, _vp(stream), ctypes.byref(out))
+    return rc, (out.value or 0)
+
+
+def gbees_init_gaussian(ctx: int, mean: np.ndarray, cov: np.ndarray, t0: float) -> int:
+    return _f("gbees_init_gaussian")(_vp(ctx), _dp(mean), _dp(cov), float(t0))
+
+
+def gbees_init_cells(ctx: int, idx: np.ndarray, p: np.ndarray, t0: float, step0: int = 0) -> int:
+    return _f("gbees_init_cells")(_vp(ctx), _ip(idx), _dp(p), int(p.shape[0]), float(t0), int(step0))
+
+
+def gbees_propagate(ctx: int, t_end: float, stats: gbees_stats) -> int:
+    return _f("gbees_propagate")(_vp(ctx), float(t_end), ctypes.byref(stats))
+
+
+def gbees_correct_gaussian(ctx: int, y: np.ndarray, R: np.ndarray, H_idx: np.ndarray) -> int:
+    return _f("gbees_correct_gaussian")(_vp(ctx), _dp(y), _dp(R), _ip(H_idx), int(H_idx.size))
+
+
+def gbees_count(ctx: int) -> Tuple[int, int]:
+    n = _i64()
+    rc = _f("gbees_count")(_vp(ctx), ctypes.byref(n))
+    return rc, int(n.value)
+
+
+def gbees_read_cells(ctx: int, idx: np.ndarray, p: np.ndarray, sorted_: bool) -> Tuple[int, int]:
+    n = _i64()
+    rc = _f("gbees_read_cells")(_vp(ctx), _ip(idx), _dp(p), int(p.shape[0]), ctypes.byref(n), int(bool(sorted_)))
+    return rc, int(n.value)
+
+
+def gbees_moments(ctx: int, mean: np.ndarray, cov: np.ndarray) -> int:
+    return _f("gbees_moments")(_vp(ctx), _dp(mean), _dp(cov))
+
+
+def gbees_get_stats(ctx: int, stats: gbees_stats) -> int:
+    return _f("gbees_get_stats")(_vp(ctx), ctypes.byref(stats))
+
+
+def gbees_get_status(ctx: int) -> int:
+    return _f("gbees_get_status")(_vp(ctx))
+
+
+def gbees_profile_control(ctx: int, enable: bool, reset: bool) -> int:
+    return _f("gbees_profile_control")(_vp(ctx), int(bool(enable)), int(bool(reset)))
+
+
+def gbees_profile_read(ctx: int, prof: gbees_profile) -> int:
+    return _f("gbees_profile_read")(_vp(ctx), ctypes.byref(prof))
+
+
+def gbees_last_error(ctx: int) -> str:
+    s = _f("gbees_last_error")(_vp(ctx))
+    return s.decode() if s else ""
+
+
+def gbees_destroy(ctx: int) -> None:
+    _f("gbees_destroy")(_vp(ctx))
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(_P(_d))
+
+
+def _ip(a: np.ndarray):
+    return a.ctypes.data_as(_P(_i32))
+
+
+# ---- a convenience wrapper that owns the workspace through PyTorch ----
+
+class GbeesError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+@dataclass
+class Stats:
+    steps: int
+    cell_updates: int
+    t: float
+    last_dt: float
+    total_steps: int
+    n_cells: int
+    norm: float
+
+    @classmethod
+    def of(cls, s: gbees_stats) -> "Stats":
+        return cls(s.steps, s.cell_updates, s.t, s.last_dt, s.total_steps, s.n_cells, s.norm)
+
+
+def make_config(n: int, dynamics: int, params: Sequence[float], h: Sequence[float], x0: Sequence[float],
+                thr_rel: float = 1e-7, cfl: float = 0.9, prune_interval: int = 20, precision: int = GBEES_FP64,
+                limiter: int = GBEES_LIM_MC, max_cells: int = 1 << 20, table_factor: float = 2.0,
+                probe_width: int = 1) -> gbees_config:
+    c = gbees_config()
+    c.n, c.dynamics = int(n), int(dynamics)
+    for k, v in enumerate(params):
+        c.params[k] = float(v)
+    for k in range(min(n, 6, len(h), len(x0))):
+        c.h[k] = float(h[k])
+        c.x0[k] = float(x0[k])
+    c.thr_rel, c.cfl = float(thr_rel), float(cfl)
+    c.prune_interval, c.precision, c.limiter = int(prune_interval), int(precision), int(limiter)
+    c.probe_width, c.max_cells, c.table_factor = int(probe_width), int(max_cells), float(table_factor)
+    return c
+
+
+class Grid:
+    """One GBEES grid on a CUDA device; the workspace is a torch uint8 tensor."""
+
+    def __init__(self, cfg: gbees_config, device: str = "cuda:0", stream=None):
+        import torch
+
+        self.cfg = cfg
+        self.n = cfg.n
+        self.device = torch.device(device)
+        nbytes = gbees_workspace_bytes(cfg)
+        if nbytes == 0:
+            raise GbeesError(GBEES_EINVAL, "invalid configuration")
+        with torch.cuda.device(self.device):
+            self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            rc, ctx = gbees_create(cfg, self.workspace.data_ptr(), nbytes, self.stream.cuda_stream)
+        if rc != 0:
+            raise GbeesError(rc, "gbees_create failed")
+        self.ctx = ctx
+
+    def close(self):
+        if getattr(self, "ctx", 0):
+            gbees_destroy(self.ctx)
+            self.ctx = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc: int):
+        if rc != 0:
+            raise GbeesError(rc, gbees_last_error(self.ctx))
+
+    def init_gaussian(self, mean, cov, t0: float = 0.0):
+        m = np.ascontiguousarray(mean, dtype=np.float64)
+        C = np.ascontiguousarray(cov, dtype=np.float64)
+        self._check(gbees_init_gaussian(self.ctx, m, C, t0))
+
+    def init_cells(self, idx, p, t0: float = 0.0, step0: int = 0):
+        I = np.ascontiguousarray(idx, dtype=np.int32).reshape(-1, self.n)
+        P = np.ascontiguousarray(p, dtype=np.float64)
+        self._check(gbees_init_cells(self.ctx, I, P, t0, step0))
+
+    def propagate(self, t_end: float) -> Stats:
+        st = gbees_stats()
+        self._check(gbees_propagate(self.ctx, t_end, st))
+        return Stats.of(st)
+
+    def correct_gaussian(self, y, R, H_idx=None):
+        yy = np.ascontiguousarray(y, dtype=np.float64).reshape(-1)
+        RR = np.ascontiguousarray(R, dtype=np.float64)
+        HH = np.ascontiguousarray(np.arange(yy.size) if H_idx is None else H_idx, dtype=np.int32)
+        self._check(gbees_correct_gaussian(self.ctx, yy, RR, HH))
+
+    def count(self) -> int:
+        rc, n = gbees_count(self.ctx)
+        self._check(rc)
+        return n
+
+    def read_cells(self, sorted_: bool = True):
+        n = self.count()
+        idx = np.zeros((max(n, 1), self.n), dtype=np.int32)
+        p = np.zeros(max(n, 1), dtype=np.float64)
+        rc, n2 = gbees_read_cells(self.ctx, idx, p, sorted_)
+        self._check(rc)
+        return idx[:n2], p[:n2]
+
+    def moments(self):
+        mean = np.zeros(self.n)
+        cov = np.zeros((self.n, self.n))
+        self._check(gbees_moments(self.ctx, mean, cov))
+        return mean, cov
+
+    def stats(self) -> Stats:
+        st = gbees_stats()
+        self._check(gbees_get_stats(self.ctx, st))
+        return Stats.of(st)
+
+    @property
+    def status(self) -> int:
+        return gbees_get_status(self.ctx)
+
+    def profile(self, enable: Optional[bool] = None, reset: bool = False) -> dict:
+        """Switch per-phase event timing on or off and return the counters as a dict."""
+        if enable is not None or reset:
+            cur = self._prof_on if enable is None else enable
+            self._check(gbees_profile_control(self.ctx, cur, reset))
+            self._prof_on = cur
+        pr = gbees_profile()
+        self._check(gbees_profile_read(self.ctx, pr))
+        return {
+            "launches": {k: int(pr.launches[i]) for i, k in enumerate(PHASE_NAMES)},
+            "ms": {k: float(pr.ms[i]) for i, k in enumerate(PHASE_NAMES)},
+            "timed": {k: int(pr.timed[i]) for i, k in enumerate(PHASE_NAMES)},
+            "total_launches": int(pr.total_launches),
+            "fallback_lookups": int(pr.fallback_lookups),
+        }
+
+    _prof_on = False
+
+
+def grid_for_workload(w, precision: int = GBEES_FP64, max_cells: int = 1 << 20, device: str = "cuda:0",
+                      probe_width: int = 1, table_factor: float = 2.0) -> Grid:
+    """A Grid configured for a paper_2508_13986_gb300.workloads.Workload."""
+    cfg = make_config(w.n, w.dynamics, w.params, w.h, w.x0, w.thr_rel, w.cfl, w.prune_interval, precision,
+                      w.limiter, max_cells, table_factor, probe_width)
+    return Grid(cfg, device)

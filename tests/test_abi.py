@@ -1,0 +1,83 @@
+"""The C-ABI library builds, loads and exports every entry point that
+include/gbees.h declares; host-only calls work without a GPU."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2508_13986_gb300 import gbees
+from paper_2508_13986_gb300.build import LIB, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gbees.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^[A-Za-z_][\w\s\*]*?\b(gbees_\w+)\s*\(", text, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build()
+    return ctypes.CDLL(LIB)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for want in ("gbees_workspace_bytes", "gbees_create", "gbees_init_gaussian", "gbees_init_cells",
+                 "gbees_propagate", "gbees_correct_gaussian", "gbees_count", "gbees_read_cells",
+                 "gbees_moments", "gbees_get_stats", "gbees_get_status", "gbees_last_error", "gbees_destroy"):
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", LIB], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (gbees_\w+)", out))
+    for name in declared_functions():
+        assert name in exported, name
+        getattr(lib, name)
+
+
+def test_binding_wraps_every_declared_symbol():
+    for name in declared_functions():
+        assert name in gbees._SIGNATURES, name
+        assert callable(getattr(gbees, name))
+
+
+def test_workspace_bytes_is_host_only_and_validates(lib):
+    gbees.load_library()
+    cfg = gbees.make_config(3, gbees.GBEES_DYN_LORENZ63, (10, 28, 8 / 3), [0.5] * 3, [0, 0, 0], max_cells=1000)
+    nb = gbees.gbees_workspace_bytes(cfg)
+    # 2 keys + 2 p + 2 x 6 links + keep + map per cell, 2048 table slots of 16 B, scalars
+    assert nb >= 1000 * (16 + 16 + 48 + 1 + 4) + 2048 * 16
+    cfg32 = gbees.make_config(3, gbees.GBEES_DYN_LORENZ63, (10, 28, 8 / 3), [0.5] * 3, [0, 0, 0],
+                              max_cells=1000, precision=gbees.GBEES_FP32)
+    assert gbees.gbees_workspace_bytes(cfg32) < nb
+    bad = [
+        gbees.make_config(3, gbees.GBEES_DYN_LORENZ96, (4,), [0.5] * 3, [0, 0, 0]),   # L96 needs n >= 4
+        gbees.make_config(2, gbees.GBEES_DYN_LORENZ63, (10, 28, 8 / 3), [0.5] * 2, [0, 0]),
+        gbees.make_config(7, gbees.GBEES_DYN_CONSTANT, (1,) * 7, [0.5] * 6, [0] * 6),
+        gbees.make_config(3, gbees.GBEES_DYN_CONSTANT, (1, 1, 1), [0.5, 0.0, 0.5], [0, 0, 0]),
+        gbees.make_config(3, gbees.GBEES_DYN_CONSTANT, (1, 1, 1), [0.5] * 3, [0, 0, 0], cfl=0.0),
+        gbees.make_config(3, gbees.GBEES_DYN_CONSTANT, (1, 1, 1), [0.5] * 3, [0, 0, 0], probe_width=3),
+        gbees.make_config(3, gbees.GBEES_DYN_CONSTANT, (1, 1, 1), [0.5] * 3, [0, 0, 0], max_cells=0),
+        gbees.make_config(3, gbees.GBEES_DYN_CONSTANT, (1, 1, 1), [0.5] * 3, [0, 0, 0], table_factor=1.1),
+        gbees.make_config(3, gbees.GBEES_DYN_CONSTANT, (1, 1, 1), [0.5] * 3, [0, 0, 0], thr_rel=1.5),
+    ]
+    for c in bad:
+        assert gbees.gbees_workspace_bytes(c) == 0
+
+
+def test_create_rejects_a_short_or_misaligned_workspace(lib):
+    cfg = gbees.make_config(3, gbees.GBEES_DYN_CONSTANT, (1, 1, 1), [0.5] * 3, [0, 0, 0], max_cells=100)
+    nb = gbees.gbees_workspace_bytes(cfg)
+    rc, ctx = gbees.gbees_create(cfg, 0, nb, 0)
+    assert rc == gbees.GBEES_EINVAL and ctx == 0
+    rc, ctx = gbees.gbees_create(cfg, 256 * 1000, nb - 1, 0)
+    assert rc == gbees.GBEES_EINVAL and ctx == 0
+    rc, ctx = gbees.gbees_create(cfg, 256 * 1000 + 8, nb, 0)
+    assert rc == gbees.GBEES_EINVAL and ctx == 0
