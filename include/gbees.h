@@ -202,6 +202,46 @@ const char* gbees_last_error(gbees_ctx* ctx);
 /* Free the host context. The workspace stays the caller's. */
 void gbees_destroy(gbees_ctx* ctx);
 
+/* Size of the library's built-in device scratch used by
+ * gbees_propagate_cells_noalloc (16 MiB). */
+#define GBEES_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
+
+/* Propagation without any device allocation by the caller or the library.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc -- code that runs while a stream is being captured
+ * into a CUDA graph (an allocation there is illegal or breaks the capture),
+ * real-time loops that cannot afford the implicit synchronisation and latency
+ * of an allocation, and host applications that own all device memory through
+ * their own allocator and forbid side allocations.
+ *
+ * It does what gbees_create + gbees_init_cells + gbees_propagate +
+ * gbees_read_cells(sorted = 0) do, but its workspace is a file-scope device
+ * array of GBEES_NOALLOC_SCRATCH_BYTES inside the library, which every GPU
+ * that loads the library holds until the process exits. Inputs and outputs
+ * are the caller's host buffers, as in those calls: idx (N x n int32), p (N
+ * densities, taken as given), t0 and step0 as in gbees_init_cells; t_end as in
+ * gbees_propagate; the active cells at t_end are written in storage order to
+ * idx_out (cap_out x n) and p_out (cap_out, normalised densities), their count
+ * to *n_out; stats may be NULL. cuda_stream: the stream to work on (NULL =
+ * legacy default stream); the call returns after its work completed.
+ *
+ * Errors: GBEES_ECAPACITY when gbees_workspace_bytes(cfg) exceeds
+ * GBEES_NOALLOC_SCRATCH_BYTES (use the regular entry points with your own
+ * workspace instead), GBEES_EINVAL for bad arguments or more than cap_out
+ * result cells (the first cap_out are written), and any status of the
+ * calls it mirrors. No context outlives the call, so no error message is kept.
+ *
+ * The first call on a device looks up the device address of the array for
+ * the device that is current (once per device); make that first call before
+ * any stream capture starts. Every call on a device uses the same array and
+ * the array keeps the last call's contents; each call clears what has to
+ * start empty (the scalars and the hashtable) before using it. Calls whose
+ * work overlaps on one GPU (other host threads, other streams) race on the
+ * array and corrupt each other: serialise them. */
+int gbees_propagate_cells_noalloc(const gbees_config* cfg, const int32_t* idx, const double* p, int64_t N,
+                                  double t0, int64_t step0, double t_end, void* cuda_stream, int32_t* idx_out,
+                                  double* p_out, int64_t cap_out, int64_t* n_out, gbees_stats* stats);
+
 #ifdef __cplusplus
 }
 #endif

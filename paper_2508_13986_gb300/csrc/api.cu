@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <type_traits>
@@ -747,3 +748,121 @@ int gbees_moments(gbees_ctx* ctx, double* mean, double* cov) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ no-allocation entry point
+//
+// The workspace of gbees_propagate_cells_noalloc lives in this file-scope device
+// array. Host code must not pass the array's name to a kernel: on the host it is
+// only a stand-in symbol. Its device address is looked up once per device with
+// cudaGetSymbolAddress while that device is current.
+
+namespace {
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[GBEES_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void* g_noalloc_addr[kMaxDevices] = {};
+
+// Device address of the scratch on the current device (set up on first use).
+cudaError_t noalloc_scratch(void** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return cudaSuccess;
+}
+
+// A context over a given workspace, on the stack (the set-up of gbees_create).
+bool noalloc_setup(gbees_ctx* ctx, const gbees_config* cfg, void* base_ptr, cudaStream_t stream) {
+    Layout L;
+    if (!make_layout(cfg, &L)) return false;
+    ctx->cfg = *cfg;
+    ctx->stream = stream;
+    ctx->status = GBEES_OK;
+    ctx->has_grid = false;
+    Model& m = ctx->m;
+    std::memset(&m, 0, sizeof m);
+    m.n = cfg->n;
+    m.dyn = cfg->dynamics;
+    m.limiter = cfg->limiter;
+    m.key_bits = key_bits_for(cfg->n);
+    m.prune_interval = cfg->prune_interval;
+    m.probe_width = cfg->probe_width ? cfg->probe_width : 1;
+    m.cap = cfg->max_cells;
+    m.tmask = L.slots - 1;
+    std::memcpy(m.a, cfg->params, sizeof m.a);
+    m.prod_h = 1.0;
+    for (int j = 0; j < cfg->n; ++j) {
+        m.h[j] = cfg->h[j];
+        m.x0[j] = cfg->x0[j];
+        m.prod_h *= cfg->h[j];
+    }
+    m.thr_rel = cfg->thr_rel;
+    m.cfl = cfg->cfl;
+    char* base = (char*)base_ptr;
+    Bufs& b = ctx->b;
+    b.sc = (DevScalars*)(base + L.sc);
+    b.blk = (long long*)(base + L.blk);
+    for (int g = 0; g < 2; ++g) {
+        b.key[g] = (unsigned long long*)(base + L.key[g]);
+        b.q[g] = (void*)(base + L.q[g]);
+        b.link[g] = (int*)(base + L.link[g]);
+    }
+    b.keep = (unsigned char*)(base + L.keep);
+    b.map = (int*)(base + L.map);
+    b.table = (Slot*)(base + L.table);
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return false;
+    ctx->grid = std::min(GRID_MAX, std::max(1, sms * 4));
+    return true;
+}
+
+}  // namespace
+
+extern "C" int gbees_propagate_cells_noalloc(const gbees_config* cfg, const int32_t* idx, const double* p, int64_t N,
+                                             double t0, int64_t step0, double t_end, void* cuda_stream,
+                                             int32_t* idx_out, double* p_out, int64_t cap_out, int64_t* n_out,
+                                             gbees_stats* stats) {
+    if (!config_ok(cfg, nullptr) || !n_out || cap_out < 0 || (cap_out > 0 && (!idx_out || !p_out)))
+        return GBEES_EINVAL;
+    if (gbees_workspace_bytes(cfg) > GBEES_NOALLOC_SCRATCH_BYTES) return GBEES_ECAPACITY;
+    void* base = nullptr;
+    if (noalloc_scratch(&base) != cudaSuccess) return GBEES_ECUDA;
+    gbees_ctx ctx;
+    if (!noalloc_setup(&ctx, cfg, base, (cudaStream_t)cuda_stream)) return GBEES_ECUDA;
+    int st = gbees_init_cells(&ctx, idx, p, N, t0, step0);
+    if (st) return st;
+    st = gbees_propagate(&ctx, t_end, stats);
+    if (st) return st;
+    const long long Nc = ctx.hs.N;
+    *n_out = Nc;
+    if (Nc == 0) return GBEES_OK;
+    const int n = cfg->n;
+    const int g = ctx.hs.gen;
+    int* d_idx = ctx.b.link[g ^ 1];
+    double* d_p = reinterpret_cast<double*>(ctx.b.key[g ^ 1]);
+    with_nt(&ctx, [&](auto NN, auto TT) {
+        constexpr int NC = decltype(NN)::value;
+        using T = decltype(TT);
+        k_readout<NC, T><<<ctx.grid, THREADS, 0, ctx.stream>>>(ctx.m, ctx.b, d_idx, d_p);
+    });
+    const long long w = std::min<long long>(Nc, cap_out);
+    if (w > 0) {
+        if (cudaMemcpyAsync(idx_out, d_idx, sizeof(int32_t) * n * w, cudaMemcpyDeviceToHost, ctx.stream) != cudaSuccess ||
+            cudaMemcpyAsync(p_out, d_p, sizeof(double) * w, cudaMemcpyDeviceToHost, ctx.stream) != cudaSuccess)
+            return GBEES_ECUDA;
+    }
+    if (cudaStreamSynchronize(ctx.stream) != cudaSuccess || cudaGetLastError() != cudaSuccess) return GBEES_ECUDA;
+    return Nc > cap_out ? GBEES_EINVAL : GBEES_OK;
+}

@@ -89,7 +89,10 @@ _SIGNATURES = {
     "gbees_profile_read": (ctypes.c_int, [_vp, _P(gbees_profile)]),
     "gbees_last_error": (ctypes.c_char_p, [_vp]),
     "gbees_destroy": (None, [_vp]),
+    "gbees_propagate_cells_noalloc": (ctypes.c_int, [_P(gbees_config), _P(_i32), _P(_d), _i64, _d, _i64, _d, _vp,
+                                                     _P(_i32), _P(_d), _i64, _P(_i64), _P(gbees_stats)]),
 }
+GBEES_NOALLOC_SCRATCH_BYTES = 16 << 20
 
 _lib = None
 
@@ -181,6 +184,18 @@ def gbees_last_error(ctx: int) -> str:
 
 def gbees_destroy(ctx: int) -> None:
     _f("gbees_destroy")(_vp(ctx))
+
+
+def gbees_propagate_cells_noalloc(cfg: gbees_config, idx: np.ndarray, p: np.ndarray, t0: float, step0: int,
+                                  t_end: float, stream: int, idx_out: np.ndarray, p_out: np.ndarray,
+                                  stats: gbees_stats) -> Tuple[int, int]:
+    """Propagate host cells with the library's built-in device scratch (no
+    allocation at all); see include/gbees.h. Returns (status, cell count)."""
+    n = _i64()
+    rc = _f("gbees_propagate_cells_noalloc")(ctypes.byref(cfg), _ip(idx), _dp(p), int(p.shape[0]), float(t0),
+                                             int(step0), float(t_end), _vp(stream), _ip(idx_out), _dp(p_out),
+                                             int(p_out.shape[0]), ctypes.byref(n), ctypes.byref(stats))
+    return rc, int(n.value)
 
 
 def _dp(a: np.ndarray):
