@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-secondary", action="store_true", help="skip the other precision's line")
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--max-cells", type=int, default=1 << 22)
+    ap.add_argument("--launch-mode", choices=["auto", "persistent", "graph", "direct"], default="auto")
     return ap.parse_args()
 
 
@@ -181,14 +182,17 @@ def time_precision(args, w, precision, dev, rank, world):
     from paper_2508_13986_gb300 import gbees
 
     prec = gbees.GBEES_FP64 if precision == "f64" else gbees.GBEES_FP32
-    grid = gbees.grid_for_workload(w, precision=prec, max_cells=args.max_cells, device=f"cuda:{dev}")
+    mode = {"auto": gbees.GBEES_LAUNCH_AUTO, "persistent": gbees.GBEES_LAUNCH_PERSISTENT,
+            "graph": gbees.GBEES_LAUNCH_GRAPH, "direct": gbees.GBEES_LAUNCH_DIRECT}[args.launch_mode]
+    grid = gbees.grid_for_workload(w, precision=prec, max_cells=args.max_cells, device=f"cuda:{dev}",
+                                   launch_mode=mode)
     stream = grid.stream
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=f"cuda:{dev}")
     for _ in range(args.warmup):
         run_workload(grid, w)
     barrier(world)
     torch.cuda.synchronize(dev)
-    grid.profile(enable=True, reset=True)
+    grid.profile(enable=False, reset=True)
     clocks = ClockSampler(dev)
     clocks.start()
     total_ms, total_updates, total_steps, peak = 0.0, 0, 0, 0
@@ -206,9 +210,20 @@ def time_precision(args, w, precision, dev, rank, world):
         total_steps += s
         peak = max(peak, pk)
     clk = clocks.stop()
-    prof = grid.profile(enable=False)
+    launches = grid.profile()["total_launches"]
     barrier(world)
     torch.cuda.synchronize(dev)
+
+    # profiled pass: the same runs with one launch per kernel and CUDA events
+    # around every phase on the library's stream (per-kernel durations)
+    grid.profile(enable=True, reset=True)
+    prof_updates = 0
+    for _ in range(max(1, min(args.steps, 2))):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        u, _, _, _, _ = run_workload(grid, w)
+        prof_updates += u
+    prof = grid.profile(enable=False)
 
     # end to end through the C ABI with host buffers: inputs from host memory,
     # final density and moments read back to host memory, wall clock
@@ -232,15 +247,17 @@ def time_precision(args, w, precision, dev, rank, world):
     peak_gbs, peak_src = load_peaks()
     bpc = bytes_per_update(w.n, precision)
     upd_ms = prof["ms"]["update"]
-    achieved = bpc * total_updates / (upd_ms / 1e3) / 1e9 if upd_ms > 0 else None
+    achieved = bpc * prof_updates / (upd_ms / 1e3) / 1e9 if upd_ms > 0 else None
     launches_upd = max(prof["timed"]["update"], 1)
     traffic = None
     key = f"{w.name}/{precision}"
     rec = TRAFFIC_BYTES_PER_CELL.get(key)
     if rec and rec.get("src") == ctu_source_hash():
-        traffic = rec["bytes_per_cell"] * total_updates / launches_upd
-    phase_share = {k: (v / sum(prof["ms"].values()) if sum(prof["ms"].values()) > 0 else 0.0)
-                   for k, v in prof["ms"].items()}
+        traffic = rec["bytes_per_cell"] * prof_updates / launches_upd
+    tot_ms = sum(prof["ms"].values())
+    phase_share = {k: (v / tot_ms if tot_ms > 0 else 0.0) for k, v in prof["ms"].items()}
+    kernels = ("k_ctu (single-pass gather)" if precision == "f32"
+               else "k_waves + k_faces + k_apply (three-pass FP64 update)")
     return {
         "value": upd_sum / (ms_max / 1e3),
         "ms_per_step": ms_max / args.steps,
@@ -251,7 +268,8 @@ def time_precision(args, w, precision, dev, rank, world):
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_max / args.steps},
         "roofline": {
             "bound": "hbm",
-            "kernel": "k_ctu (DCU + CTU + high-resolution update)",
+            "kernel": kernels,
+            "timing": "CUDA events around each update phase in a profiled pass of the same runs",
             "achieved": achieved,
             "peak": peak_gbs,
             "peak_source": peak_src,
@@ -259,11 +277,11 @@ def time_precision(args, w, precision, dev, rank, world):
             "frac": (achieved / peak_gbs) if achieved else None,
             "traffic": traffic,
             "algorithmic_bytes_per_cell": bpc,
-            "cells_per_launch": total_updates / launches_upd,
+            "cells_per_launch": prof_updates / launches_upd,
             "avg_launch_us": upd_ms * 1e3 / launches_upd,
         },
         "phase_share": phase_share,
-        "gpu_launches": prof["total_launches"],
+        "gpu_launches": launches,
         "fallback_lookups": prof["fallback_lookups"],
         "clocks": clk,
     }
@@ -353,6 +371,7 @@ def main_ours(args):
             "config": {"workload": args.workload, "parallelism": f"replicas{world}",
                        "step": "one whole run: init + propagate/correct to t_end",
                        "l2": "flushed between timed runs (256 MiB write)",
+                       "launch_mode": args.launch_mode,
                        "cell_updates_per_step": main["updates_per_step"],
                        "time_steps_per_run": main["time_steps_per_run"],
                        "peak_cells": main["peak_cells"]},

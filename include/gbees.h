@@ -97,7 +97,17 @@ typedef struct {
     int32_t probe_width;    /* lanes that probe the hashtable together: 1, 2, 4, 8, 16 or 32 (0 = 1) */
     int64_t max_cells;      /* fixed cell capacity (Sec. 4.1) */
     double table_factor;    /* hashtable slots per cell of capacity, >= 1.25 (0 = 2.0, Sec. 4.2) */
+    int32_t launch_mode;    /* GBEES_LAUNCH_*: how propagate drives the time steps */
 } gbees_config;
+
+/* Launch modes of gbees_propagate (all give bit-identical results):
+ *   AUTO        persistent kernel while the grid is small, CUDA graph beyond
+ *   PERSISTENT  one cooperative launch runs many steps, phases separated by
+ *               grid barriers (one block per SM)
+ *   GRAPH       one CUDA-graph launch runs many steps: a device-side WHILE loop
+ *               over the step's kernels, an IF node around the prune
+ *   DIRECT      one host launch per kernel (used whenever profiling is on) */
+enum { GBEES_LAUNCH_AUTO = 0, GBEES_LAUNCH_PERSISTENT = 1, GBEES_LAUNCH_GRAPH = 2, GBEES_LAUNCH_DIRECT = 3 };
 
 typedef struct {
     int64_t steps;        /* time steps taken by the call */

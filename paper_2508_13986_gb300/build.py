@@ -15,7 +15,10 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libgbees_gb300.so")
-SOURCES = ["api.cu", "ctu_f64.cu", "ctu_f32.cu"]
+# (source, extra defines, object name): update_inst.cu once per precision and model family
+SOURCES = [("api.cu", [], "api.o")] + [
+    ("update_inst.cu", [f"-DGBEES_PREC={p}", f"-DGBEES_FAMILY={f}"], f"update_p{p}_f{f}.o")
+    for p in (64, 32) for f in range(6)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
          "-I", os.path.join(ROOT, "include")]
@@ -48,9 +51,10 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     os.makedirs(LIBDIR, exist_ok=True)
     objs = []
 
-    def compile_one(src):
-        obj = os.path.join(LIBDIR, src.replace(".cu", ".o"))
-        cmd = [nvcc(), *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
+    def compile_one(item):
+        src, defines, name = item
+        obj = os.path.join(LIBDIR, name)
+        cmd = [nvcc(), *ARCH, *FLAGS, *defines, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
@@ -58,8 +62,11 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
             sys.stderr.write(r.stdout + r.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
+    workers = max(1, min(len(SOURCES), os.cpu_count() or 1))
+    # the longest jobs first
+    order = sorted(SOURCES, key=lambda s: (s[0] != "update_inst.cu", s[2]))
+    with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+        objs = list(ex.map(compile_one, order))
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)

@@ -13,11 +13,32 @@
 #include <vector>
 
 #include "../../include/gbees.h"
-#include "gbees_kernels.cuh"
+#include "gbees_misc_kernels.cuh"
 
 namespace gbees {
-cudaError_t launch_ctu_f64(const Model& m, const Bufs& b, int grid, cudaStream_t s);
-cudaError_t launch_ctu_f32(const Model& m, const Bufs& b, int grid, cudaStream_t s);
+// update_inst.cu, one object per precision and model family
+#define GBEES_DECL(p, fam) int update_kernels_p##p##_f##fam(int n, int dyn, void** f, void** persist);
+GBEES_DECL(64, 0) GBEES_DECL(64, 1) GBEES_DECL(64, 2) GBEES_DECL(64, 3) GBEES_DECL(64, 4) GBEES_DECL(64, 5)
+GBEES_DECL(32, 0) GBEES_DECL(32, 1) GBEES_DECL(32, 2) GBEES_DECL(32, 3) GBEES_DECL(32, 4) GBEES_DECL(32, 5)
+#undef GBEES_DECL
+
+// The update kernels of a model (launch order) and its persistent kernel.
+int update_kernels(const Model& m, bool f32, void** f, void** persist) {
+    int fam;
+    switch (m.dyn) {
+        case DYN_LORENZ63:
+        case DYN_LORENZ63_SHIFTED: fam = 0; break;
+        case DYN_LORENZ96: fam = 1; break;
+        case DYN_LINEAR: fam = m.n <= 3 ? 2 : 3; break;
+        default: fam = m.n <= 3 ? 4 : 5; break;
+    }
+    typedef int (*Entry)(int, int, void**, void**);
+    static const Entry e64[6] = {update_kernels_p64_f0, update_kernels_p64_f1, update_kernels_p64_f2,
+                                 update_kernels_p64_f3, update_kernels_p64_f4, update_kernels_p64_f5};
+    static const Entry e32[6] = {update_kernels_p32_f0, update_kernels_p32_f1, update_kernels_p32_f2,
+                                 update_kernels_p32_f3, update_kernels_p32_f4, update_kernels_p32_f5};
+    return (f32 ? e32 : e64)[fam](m.n, m.dyn, f, persist);
+}
 }  // namespace gbees
 
 using namespace gbees;
@@ -41,7 +62,22 @@ struct gbees_ctx {
         cudaEvent_t a, b;
     };
     std::vector<Pending> pending;
+    // the propagate loop as one CUDA graph: a WHILE node over one step, an IF
+    // node around the prune (built on first use; direct launches if it fails)
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    bool graph_tried = false;
+    long long graph_launches = 0;
+    // update kernels of the configured model (graph and direct paths) and the
+    // persistent step-loop kernel with its cooperative grid size (0: unusable)
+    void* upd[4] = {nullptr, nullptr, nullptr, nullptr};
+    int n_upd = 0;
+    void* persist = nullptr;
+    int persist_grid = 0;
+    long long persist_max_cells = 1ll << 18;
     ~gbees_ctx() {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        if (graph) cudaGraphDestroy(graph);
         for (auto& p : pending) {
             cudaEventDestroy(p.a);
             cudaEventDestroy(p.b);
@@ -57,7 +93,7 @@ constexpr size_t ALIGN = 256;
 size_t align_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
 
 struct Layout {
-    size_t sc, blk, key[2], q[2], link[2], keep, map, table, total;
+    size_t sc, blk, part, key[2], q[2], link[2], om[2], keep, map, table, wv_u, wv_g, fl, fu, total;
     unsigned long long slots;
 };
 
@@ -98,6 +134,7 @@ bool config_ok(const gbees_config* c, std::string* why) {
         return fail("probe_width must be 1, 2, 4, 8, 16 or 32");
     if (c->max_cells < 1 || c->max_cells > 0x7fffffffll) return fail("max_cells must be in 1..2^31-1");
     if (!(c->table_factor == 0.0 || c->table_factor >= 1.25)) return fail("table_factor must be 0 or >= 1.25");
+    if (c->launch_mode < GBEES_LAUNCH_AUTO || c->launch_mode > GBEES_LAUNCH_DIRECT) return fail("unknown launch_mode");
     return true;
 }
 
@@ -117,12 +154,20 @@ bool make_layout(const gbees_config* c, Layout* L) {
     };
     L->sc = take(sizeof(DevScalars));
     L->blk = take(sizeof(long long) * (GRID_MAX + 1));
+    L->part = take(sizeof(Partial) * GRID_MAX);
     for (int g = 0; g < 2; ++g) L->key[g] = take(8 * cap);
     for (int g = 0; g < 2; ++g) L->q[g] = take(S * cap);
     for (int g = 0; g < 2; ++g) L->link[g] = take((size_t)4 * 2 * c->n * cap);
+    for (int g = 0; g < 2; ++g) L->om[g] = take(2 * cap);
     L->keep = take(cap);
     L->map = take(4 * cap);
     L->table = take(sizeof(Slot) * slots);
+    // scratch of the three-pass FP64 update
+    const size_t fp64 = c->precision == GBEES_FP64 ? (size_t)8 * c->n * cap : 0;
+    L->wv_u = take(fp64);
+    L->wv_g = take(fp64);
+    L->fl = take(fp64);
+    L->fu = take(fp64);
     L->total = off;
     L->slots = slots;
     return true;
@@ -250,22 +295,41 @@ void with_nt(const gbees_ctx* ctx, F&& f) {
 }
 
 template <int N>
-void launch_link(gbees_ctx* ctx) {
-    const int G = ctx->grid;
-    cudaStream_t s = ctx->stream;
-    switch (ctx->m.probe_width) {
-        case 2: k_link<N, 2><<<G, THREADS, 0, s>>>(ctx->m, ctx->b); break;
-        case 4: k_link<N, 4><<<G, THREADS, 0, s>>>(ctx->m, ctx->b); break;
-        case 8: k_link<N, 8><<<G, THREADS, 0, s>>>(ctx->m, ctx->b); break;
-        case 16: k_link<N, 16><<<G, THREADS, 0, s>>>(ctx->m, ctx->b); break;
-        case 32: k_link<N, 32><<<G, THREADS, 0, s>>>(ctx->m, ctx->b); break;
-        default: k_link<N, 1><<<G, THREADS, 0, s>>>(ctx->m, ctx->b); break;
+void* link_kernel(int probe_width) {
+    switch (probe_width) {
+        case 2: return (void*)k_link<N, 2>;
+        case 4: return (void*)k_link<N, 4>;
+        case 8: return (void*)k_link<N, 8>;
+        case 16: return (void*)k_link<N, 16>;
+        case 32: return (void*)k_link<N, 32>;
+        default: return (void*)k_link<N, 1>;
     }
 }
 
-cudaError_t launch_ctu(gbees_ctx* ctx) {
-    if (ctx->cfg.precision == GBEES_FP32) return launch_ctu_f32(ctx->m, ctx->b, ctx->grid, ctx->stream);
-    return launch_ctu_f64(ctx->m, ctx->b, ctx->grid, ctx->stream);
+// step != 0: the link of a time step (its last block also fixes dt).
+template <int N>
+void launch_link(gbees_ctx* ctx, int step) {
+    void* args[] = {&ctx->m, &ctx->b, &step};
+    cudaLaunchKernel(link_kernel<N>(ctx->m.probe_width), dim3(ctx->grid), dim3(THREADS), args, 0, ctx->stream);
+}
+
+void resolve_update_kernels(gbees_ctx* ctx) {
+    if (ctx->n_upd) return;
+    ctx->n_upd = update_kernels(ctx->m, ctx->cfg.precision == GBEES_FP32, ctx->upd, &ctx->persist);
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ctx->persist, THREADS, 0) == cudaSuccess &&
+        per_sm >= 1)
+        ctx->persist_grid = std::min(GRID_MAX, sms);
+    cudaGetLastError();
+}
+
+void launch_ctu(gbees_ctx* ctx) {
+    resolve_update_kernels(ctx);
+    void* args[] = {&ctx->m, &ctx->b};
+    for (int i = 0; i < ctx->n_upd; ++i)
+        cudaLaunchKernel(ctx->upd[i], dim3(ctx->grid), dim3(THREADS), args, 0, ctx->stream);
 }
 
 // The prune of Algorithm 3 (directional marking, scan, compaction, relink,
@@ -273,16 +337,15 @@ cudaError_t launch_ctu(gbees_ctx* ctx) {
 void launch_prune(gbees_ctx* ctx) {
     const int G = ctx->grid;
     cudaStream_t s = ctx->stream;
-    Phase ph(ctx, GBEES_PHASE_PRUNE, 6);
+    Phase ph(ctx, GBEES_PHASE_PRUNE, 5);
     with_nt(ctx, [&](auto NN, auto TT) {
         constexpr int N = decltype(NN)::value;
         using T = decltype(TT);
         k_prune_mark<T><<<G, THREADS, 0, s>>>(ctx->m, ctx->b);
         k_prune_scatter<N, T><<<G, THREADS, 0, s>>>(ctx->m, ctx->b);
         k_prune_count<<<G, THREADS, 0, s>>>(ctx->m, ctx->b);
-        k_scan_prune<<<1, THREADS, 0, s>>>(ctx->b, G, ctx->m.cap);
         k_prune_compact<N, T><<<G, THREADS, 0, s>>>(ctx->m, ctx->b);
-        k_prune_relink<N><<<G, THREADS, 0, s>>>(ctx->m, ctx->b);
+        k_prune_relink<N><<<G, THREADS, 0, s>>>(ctx->m, ctx->b, G);
     });
 }
 
@@ -299,10 +362,111 @@ void launch_step(gbees_ctx* ctx) {
             k_grow<N, T><<<G, THREADS, 0, s>>>(ctx->m, ctx->b);
         }
         Phase ph(ctx, GBEES_PHASE_LINK, 1);
-        launch_link<N>(ctx);
+        launch_link<N>(ctx, 1);
     });
-    Phase ph(ctx, GBEES_PHASE_UPDATE, 1);
+    Phase ph(ctx, GBEES_PHASE_UPDATE, ctx->cfg.precision == GBEES_FP32 ? 1 : 3);
     launch_ctu(ctx);
+}
+
+// ---- the step loop as a CUDA graph
+
+constexpr long long kGraphMaxIter = 1ll << 16;  // steps per graph launch at most
+constexpr long long kPersistSteps = 1ll << 13;  // steps per persistent launch at most
+
+struct GraphBuilder {
+    cudaGraph_t g;
+    cudaError_t err = cudaSuccess;
+    cudaGraphNode_t add(cudaGraph_t into, cudaGraphNode_t prev, void* func, int grid, int block, void** args) {
+        cudaKernelNodeParams p{};
+        p.func = func;
+        p.gridDim = dim3(grid);
+        p.blockDim = dim3(block);
+        p.sharedMemBytes = 0;
+        p.kernelParams = args;
+        p.extra = nullptr;
+        cudaGraphNode_t node = nullptr;
+        if (err == cudaSuccess) err = cudaGraphAddKernelNode(&node, into, prev ? &prev : nullptr, prev ? 1 : 0, &p);
+        return node;
+    }
+    cudaGraphNode_t cond(cudaGraph_t into, cudaGraphNode_t prev, cudaGraphConditionalHandle h,
+                         cudaGraphConditionalNodeType type, cudaGraph_t* body) {
+        cudaGraphNodeParams p{};
+        p.type = cudaGraphNodeTypeConditional;
+        p.conditional.handle = h;
+        p.conditional.type = type;
+        p.conditional.size = 1;
+        cudaGraphNode_t node = nullptr;
+        if (err == cudaSuccess) err = cudaGraphAddNode(&node, into, prev ? &prev : nullptr, nullptr, prev ? 1 : 0, &p);
+        if (err == cudaSuccess) *body = p.conditional.phGraph_out[0];
+        return node;
+    }
+};
+
+template <int N, typename T>
+void graph_nodes(gbees_ctx* ctx, GraphBuilder& gb, cudaGraph_t body, cudaGraphConditionalHandle hw,
+                 cudaGraphConditionalHandle hp) {
+    const int G = ctx->grid;
+    Model* m = &ctx->m;
+    Bufs* b = &ctx->b;
+    void* mb[] = {m, b};
+    int one = 1;
+    void* link_args[] = {m, b, &one};
+    cudaGraphNode_t n = gb.add(body, nullptr, (void*)k_grow<N, T>, G, THREADS, mb);
+    n = gb.add(body, n, link_kernel<N>(ctx->m.probe_width), G, THREADS, link_args);
+    resolve_update_kernels(ctx);
+    for (int i = 0; i < ctx->n_upd; ++i) n = gb.add(body, n, ctx->upd[i], G, THREADS, mb);
+    DevScalars* sc = ctx->b.sc;
+    long long maxit = kGraphMaxIter;
+    int step_kernels = 2 + ctx->n_upd + 1;
+    void* ctl_args[] = {&sc, &hw, &hp, &maxit, &step_kernels};
+    n = gb.add(body, n, (void*)k_loop_ctl, 1, 1, ctl_args);
+    cudaGraph_t pb = nullptr;
+    gb.cond(body, n, hp, cudaGraphCondTypeIf, &pb);
+    if (gb.err != cudaSuccess) return;
+    int nblk = G;
+    void* relink_args[] = {m, b, &nblk};
+    cudaGraphNode_t q = gb.add(pb, nullptr, (void*)k_prune_mark<T>, G, THREADS, mb);
+    q = gb.add(pb, q, (void*)k_prune_scatter<N, T>, G, THREADS, mb);
+    q = gb.add(pb, q, (void*)k_prune_count, G, THREADS, mb);
+    q = gb.add(pb, q, (void*)k_prune_compact<N, T>, G, THREADS, mb);
+    gb.add(pb, q, (void*)k_prune_relink<N>, G, THREADS, relink_args);
+}
+
+// Build and instantiate the step-loop graph of this context. False if the
+// runtime cannot (the caller then launches kernel by kernel).
+bool build_step_graph(gbees_ctx* ctx) {
+    ctx->graph_tried = true;
+    GraphBuilder gb;
+    if (cudaGraphCreate(&gb.g, 0) != cudaSuccess) return false;
+    cudaGraphConditionalHandle hw = 0, hp = 0;
+    if (cudaGraphConditionalHandleCreate(&hw, gb.g, 1, cudaGraphCondAssignDefault) != cudaSuccess ||
+        cudaGraphConditionalHandleCreate(&hp, gb.g, 0, cudaGraphCondAssignDefault) != cudaSuccess) {
+        cudaGraphDestroy(gb.g);
+        cudaGetLastError();
+        return false;
+    }
+    DevScalars* sc = ctx->b.sc;
+    void* reset_args[] = {&sc};
+    cudaGraphNode_t r = gb.add(gb.g, nullptr, (void*)k_loop_reset, 1, 1, reset_args);
+    cudaGraph_t body = nullptr;
+    gb.cond(gb.g, r, hw, cudaGraphCondTypeWhile, &body);
+    if (gb.err == cudaSuccess) {
+        with_nt(ctx, [&](auto NN, auto TT) {
+            constexpr int N = decltype(NN)::value;
+            using T = decltype(TT);
+            graph_nodes<N, T>(ctx, gb, body, hw, hp);
+        });
+    }
+    cudaGraphExec_t exec = nullptr;
+    if (gb.err == cudaSuccess) gb.err = cudaGraphInstantiate(&exec, gb.g, 0);
+    if (gb.err != cudaSuccess) {
+        cudaGraphDestroy(gb.g);
+        cudaGetLastError();
+        return false;
+    }
+    ctx->graph = gb.g;
+    ctx->gexec = exec;
+    return true;
 }
 
 // Inverse of a small symmetric positive definite matrix (Cholesky factor,
@@ -401,14 +565,20 @@ int gbees_create(const gbees_config* cfg, void* d_workspace, size_t workspace_by
     Bufs& b = ctx->b;
     b.sc = (DevScalars*)(base + L.sc);
     b.blk = (long long*)(base + L.blk);
+    b.part = (Partial*)(base + L.part);
     for (int g = 0; g < 2; ++g) {
         b.key[g] = (unsigned long long*)(base + L.key[g]);
         b.q[g] = (void*)(base + L.q[g]);
         b.link[g] = (int*)(base + L.link[g]);
     }
+    for (int g = 0; g < 2; ++g) b.om[g] = (unsigned short*)(base + L.om[g]);
     b.keep = (unsigned char*)(base + L.keep);
     b.map = (int*)(base + L.map);
     b.table = (Slot*)(base + L.table);
+    b.wv_u = (double*)(base + L.wv_u);
+    b.wv_g = (double*)(base + L.wv_g);
+    b.fl = (double*)(base + L.fl);
+    b.fu = (double*)(base + L.fu);
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
         delete ctx;
@@ -521,7 +691,7 @@ int gbees_init_gaussian(gbees_ctx* ctx, const double* mean, const double* cov, d
         k_set_count_from_new<<<1, 1, 0, s>>>(ctx->b.sc);
         with_nt(ctx, [&](auto NN, auto) {
             constexpr int N = decltype(NN)::value;
-            launch_link<N>(ctx);
+            launch_link<N>(ctx, 0);
         });
         k_finalise<<<1, 1, 0, s>>>(ctx->m, ctx->b.sc, 0);
     }
@@ -565,7 +735,7 @@ int gbees_init_cells(gbees_ctx* ctx, const int32_t* idx, const double* p, int64_
     k_set_count<<<1, 1, 0, s>>>(ctx->b.sc, N, step0);
     with_nt(ctx, [&](auto NN, auto) {
         constexpr int NC = decltype(NN)::value;
-        launch_link<NC>(ctx);
+        launch_link<NC>(ctx, 0);
     });
     k_finalise<<<1, 1, 0, s>>>(ctx->m, ctx->b.sc, 2);
     if (!sync_scalars(ctx, "init_cells")) return ctx->status;
@@ -597,6 +767,59 @@ int gbees_propagate(gbees_ctx* ctx, double t_end, gbees_stats* stats) {
         k_begin<<<1, 1, 0, s>>>(ctx->b.sc, t_end);
     }
     if (!sync_scalars(ctx, "propagate")) return ctx->status;
+    // Persistent path: one cooperative launch runs up to kPersistSteps steps
+    // with grid barriers between the phases (small grids).
+    resolve_update_kernels(ctx);
+    const int mode = ctx->cfg.launch_mode;
+    if (mode == GBEES_LAUNCH_PERSISTENT && ctx->persist_grid == 0) {
+        set_err(ctx, GBEES_ECUDA, "propagate: the persistent kernel cannot be made resident");
+        return ctx->status;
+    }
+    const bool persist_ok = !ctx->prof_on && ctx->persist_grid > 0 &&
+                            (mode == GBEES_LAUNCH_PERSISTENT || mode == GBEES_LAUNCH_AUTO);
+    if (persist_ok) {
+        bool used = false;
+        const long long limit = mode == GBEES_LAUNCH_PERSISTENT ? (1ll << 62) : ctx->persist_max_cells;
+        while (!ctx->hs.done && ctx->hs.N <= limit) {
+            used = true;
+            const long long before = ctx->hs.steps_call;
+            long long max_steps = kPersistSteps;
+            void* args[] = {&ctx->m, &ctx->b, &max_steps};
+            if (!cuda_ok(ctx, cudaLaunchCooperativeKernel(ctx->persist, dim3(ctx->persist_grid), dim3(THREADS), args, 0, s),
+                         "propagate"))
+                return ctx->status;
+            ctx->prof.total_launches += 1;
+            if (!sync_scalars(ctx, "propagate")) return ctx->status;
+            if (!ctx->hs.done && ctx->hs.steps_call == before) {
+                set_err(ctx, GBEES_ETIMEOUT, "propagate: a persistent launch made no progress");
+                return ctx->status;
+            }
+        }
+        if (used && ctx->hs.done) {
+            fill_stats(ctx, stats);
+            return GBEES_OK;
+        }
+    }
+    // Graph path: one launch runs the whole loop on the device (up to
+    // kGraphMaxIter steps); the per-phase event timing needs the direct path.
+    const bool graph_ok = !ctx->prof_on && mode != GBEES_LAUNCH_DIRECT;
+    if (graph_ok && !ctx->graph_tried) build_step_graph(ctx);
+    if (graph_ok && ctx->gexec) {
+        const long long k0 = ctx->hs.graph_kernels;
+        while (!ctx->hs.done) {
+            const long long before = ctx->hs.steps_call;
+            if (!cuda_ok(ctx, cudaGraphLaunch(ctx->gexec, s), "propagate")) return ctx->status;
+            ctx->graph_launches += 1;
+            if (!sync_scalars(ctx, "propagate")) return ctx->status;
+            if (!ctx->hs.done && ctx->hs.steps_call == before) {
+                set_err(ctx, GBEES_ETIMEOUT, "propagate: a graph launch made no progress");
+                return ctx->status;
+            }
+        }
+        ctx->prof.total_launches += ctx->hs.graph_kernels - k0;
+        fill_stats(ctx, stats);
+        return GBEES_OK;
+    }
     const int K = ctx->cfg.prune_interval;
     long long host_step = ctx->hs.step;
     long long batch = 4;
@@ -812,14 +1035,20 @@ bool noalloc_setup(gbees_ctx* ctx, const gbees_config* cfg, void* base_ptr, cuda
     Bufs& b = ctx->b;
     b.sc = (DevScalars*)(base + L.sc);
     b.blk = (long long*)(base + L.blk);
+    b.part = (Partial*)(base + L.part);
     for (int g = 0; g < 2; ++g) {
         b.key[g] = (unsigned long long*)(base + L.key[g]);
         b.q[g] = (void*)(base + L.q[g]);
         b.link[g] = (int*)(base + L.link[g]);
     }
+    for (int g = 0; g < 2; ++g) b.om[g] = (unsigned short*)(base + L.om[g]);
     b.keep = (unsigned char*)(base + L.keep);
     b.map = (int*)(base + L.map);
     b.table = (Slot*)(base + L.table);
+    b.wv_u = (double*)(base + L.wv_u);
+    b.wv_g = (double*)(base + L.wv_g);
+    b.fl = (double*)(base + L.fl);
+    b.fu = (double*)(base + L.fu);
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)

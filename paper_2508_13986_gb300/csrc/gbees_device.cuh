@@ -69,6 +69,17 @@ struct alignas(256) DevScalars {
     int prune_now;        // the step just taken is a prune step
     unsigned int ticket;  // last-block election
     unsigned long long tmp_ord;  // scratch maximum (init)
+    long long loop_iter;  // iterations of the device-side step loop in the current graph launch
+    long long graph_kernels;  // kernels executed by graph launches (counted on the device)
+    unsigned int bar_count;   // grid barrier of the persistent kernel: arrivals
+    unsigned int bar_gen;     // and generation
+    // the current step (written by the last block of the grow kernel)
+    double step_dt;       // dt of the step being taken
+    double step_t_new;    // time after it
+    int step_last;        // the step lands on t_target
+    int step_pad;
+    double coef_dth[MAXN];  // dt / h_j
+    double coef_ch[MAXN];   // dt / (2 h_j)
     long long mom[28][NDIG];     // exact sums for moments
     double mom_mean[MAXN];       // mean, input of the covariance pass
     double mom_out[28];          // moments times prod h
@@ -92,18 +103,65 @@ struct Model {
     double prod_h;
 };
 
+// One block's share of a grid-wide reduction, written without atomics and
+// combined by whoever finishes the step (deterministic: integer digits, max).
+struct alignas(64) Partial {
+    long long acc[NDIG];           // exact-sum digits of the block's values
+    unsigned long long maxq_ord;   // order key of the block's maximum value (0: none)
+    unsigned long long rate_bits;  // the block's maximum CFL rate (non-negative double bits)
+};
+
 // Device buffers (by value). link[g] holds 2n arrays of cap int32: entry
 // (2j + s) * cap + c is the index of the neighbour of cell c one step down
 // (s = 0) or up (s = 1) in dimension j, or -1.
+//
+// om[g][c]: bits 0..2n-1 are the outward directions of cell c (bit 2j+1: the
+// flow leaves through the upper j-face, bit 2j: through the lower j-face),
+// fixed at creation because the drift does not depend on time; bit 15 marks a
+// cell whose downwind set is known to be present (cleared by every prune).
+//
+// FP64 update scratch (n arrays of cap doubles each): wv_u[j] lower-face
+// velocity, wv_g[d] d-direction wave entering the cell, fl[j] flux through the
+// lower j-face, fu[j] flux through the upper j-face of cells whose upper
+// neighbour is missing.
 struct Bufs {
     unsigned long long* key[2];
     void* q[2];
     int* link[2];
+    unsigned short* om[2];
     unsigned char* keep;
     int* map;
     Slot* table;
     DevScalars* sc;
     long long* blk;
+    double* wv_u;
+    double* wv_g;
+    double* fl;
+    double* fu;
+    Partial* part;   // GRID_MAX per-block partials
+};
+
+constexpr unsigned short OM_COMPLETE = 0x8000;
+
+
+
+// ------------------------------------------------------------------ cell iteration
+// Cells are handed out in runs of 32 consecutive cells (one warp, coalesced),
+// consecutive runs to consecutive blocks, so that a small grid still spreads
+// over every SM. Usage:
+//   for (WarpRuns r(ncell); r.next();) { const long long c = r.c; if (c >= ncell) continue; ... }
+struct WarpRuns {
+    long long k, step, n, c;
+    __device__ __forceinline__ explicit WarpRuns(long long ncell)
+        : k(blockIdx.x + (long long)gridDim.x * (threadIdx.x >> 5) - (long long)gridDim.x * (blockDim.x >> 5)),
+          step((long long)gridDim.x * (blockDim.x >> 5)),
+          n(ncell),
+          c(0) {}
+    __device__ __forceinline__ bool next() {
+        k += step;
+        c = k * 32 + (threadIdx.x & 31);
+        return k * 32 < n;
+    }
 };
 
 // ------------------------------------------------------------------ keys
@@ -295,6 +353,33 @@ __device__ __forceinline__ double cfl_rate64(const Model& m, const int* I) {
 #pragma unroll
     for (int j = 0; j < N; ++j) r = __dadd_rn(r, __ddiv_rn(fabs(face_velocity64<N>(m, I, j)), m.h[j]));
     return r;
+}
+
+// Velocity f_d at the lower (face = -1) or upper (face = +1) d-face of the cell
+// whose centre is xc shifted by s cells in dimension js (js < 0: no shift).
+// Positions are formed from the centre, so they may differ from the exact
+// x0 + (i - 1/2) h in the last bit; only the flux update uses this form.
+template <int N, int DYN, typename T>
+__device__ __forceinline__ T vel_at(const Model& m, const T* xc, const T* h, int js, int s, int d, int face) {
+    T y[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) y[k] = xc[k];
+    if (js >= 0) y[js] += (T)s * h[js];
+    y[d] += (T)face * (T)0.5 * h[d];
+    return drift<T, N>(m, DYN, y, d);
+}
+
+template <typename T>
+__device__ __forceinline__ T limited_wave(int lim, T W, T Wup) {
+    if (lim == LIM_LW) return W;
+    // MC limiter phi(theta) = max(0, min((1+theta)/2, 2, 2 theta)) with theta = Wup / W,
+    // multiplied by W and written without the division.
+    if ((W > (T)0 && Wup > (T)0) || (W < (T)0 && Wup < (T)0)) {
+        T aW = fabs(W), aU = fabs(Wup);
+        T v = fmin(fmin((T)0.5 * (aW + aU), (T)2 * aW), (T)2 * aU);
+        return W > (T)0 ? v : -v;
+    }
+    return (T)0;
 }
 
 // ------------------------------------------------------------------ exact accumulator
@@ -496,6 +581,145 @@ __device__ __forceinline__ void finalise_norm(const Model& m, DevScalars* sc, in
     sc->maxq_ord = 0;
     sc->ticket = 0;
     if (sc->N == 0 && !(mode & 2)) set_error(sc, ST_EDEGENERATE);
+}
+
+// Bookkeeping after the flux update of a step (last block, one thread): time,
+// step count, buffer swap, prune schedule and the normalisation scalars.
+__device__ __forceinline__ void finish_step(const Model& m, DevScalars* sc, long long ncell, int pb) {
+    sc->dt = sc->step_dt;
+    sc->t = sc->step_t_new;
+    sc->step += 1;
+    sc->steps_call += 1;
+    sc->updates_call += ncell;
+    sc->done = sc->step_last;
+    sc->pbuf = pb ^ 1;
+    sc->prune_now = (m.prune_interval > 0 && (sc->step % m.prune_interval) == 0);
+    finalise_norm(m, sc, 0);
+}
+
+// Write this block's partial (exact digits, maximum value, maximum rate).
+// All threads of the block must call it; d, mx, rate are per thread.
+__device__ __forceinline__ void block_partial(Partial* part, long long (&d)[NDIG], double mx, double rate) {
+    __shared__ long long s_acc[WARPS][NDIG];
+    __shared__ double s_mx[WARPS], s_rt[WARPS];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NDIG; ++q) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) d[q] += __shfl_down_sync(0xffffffffu, d[q], off);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, off));
+        rate = fmax(rate, __shfl_down_sync(0xffffffffu, rate, off));
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < NDIG; ++q) s_acc[wid][q] = d[q];
+        s_mx[wid] = mx;
+        s_rt[wid] = rate;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        Partial p;
+        double m = -INFINITY, r = 0.0;
+        for (int q = 0; q < NDIG; ++q) p.acc[q] = 0;
+        for (int w = 0; w < WARPS; ++w) {
+            for (int q = 0; q < NDIG; ++q) p.acc[q] += s_acc[w][q];
+            m = fmax(m, s_mx[w]);
+            r = fmax(r, s_rt[w]);
+        }
+        p.maxq_ord = m > -INFINITY ? ord_key(m) : 0ull;
+        p.rate_bits = r > 0.0 ? (unsigned long long)__double_as_longlong(r) : 0ull;
+        part[blockIdx.x] = p;
+    }
+    __syncthreads();
+}
+
+// Combine the partials of blocks [0, nblk) in every thread of the calling
+// block (the same result everywhere): digit sums, maximum value, maximum rate.
+struct Combined {
+    long long acc[NDIG];
+    unsigned long long maxq_ord;
+    unsigned long long rate_bits;
+};
+__device__ __forceinline__ Combined combine_partials(const Partial* part, int nblk) {
+    __shared__ long long s_acc[WARPS][NDIG];
+    __shared__ unsigned long long s_mo[WARPS], s_rt[WARPS];
+    long long d[NDIG] = {0, 0, 0, 0, 0, 0};
+    unsigned long long mo = 0, rt = 0;
+    for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
+        const Partial* p = part + i;
+#pragma unroll
+        for (int q = 0; q < NDIG; ++q) d[q] += __ldcg(&p->acc[q]);
+        mo = max(mo, __ldcg(&p->maxq_ord));
+        rt = max(rt, __ldcg(&p->rate_bits));
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NDIG; ++q)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) d[q] += __shfl_down_sync(0xffffffffu, d[q], off);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        mo = max(mo, __shfl_down_sync(0xffffffffu, mo, off));
+        rt = max(rt, __shfl_down_sync(0xffffffffu, rt, off));
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < NDIG; ++q) s_acc[wid][q] = d[q];
+        s_mo[wid] = mo;
+        s_rt[wid] = rt;
+    }
+    __syncthreads();
+    Combined c;
+    for (int q = 0; q < NDIG; ++q) c.acc[q] = 0;
+    c.maxq_ord = 0;
+    c.rate_bits = 0;
+    for (int w = 0; w < WARPS; ++w) {
+        for (int q = 0; q < NDIG; ++q) c.acc[q] += s_acc[w][q];
+        c.maxq_ord = max(c.maxq_ord, s_mo[w]);
+        c.rate_bits = max(c.rate_bits, s_rt[w]);
+    }
+    __syncthreads();
+    return c;
+}
+
+// Grid-wide barrier of a cooperative launch (all blocks resident). The wait is
+// bounded: it gives up when another block has set an error or after about
+// two seconds, sets ST_ETIMEOUT, and returns false; callers then leave.
+constexpr long long BARRIER_SPIN_LIMIT = 1ll << 26;
+__device__ __forceinline__ bool grid_barrier(DevScalars* sc) {
+    __shared__ int s_ok;
+    unsigned int* bar = &sc->bar_count;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int* vgen = &sc->bar_gen;
+        const unsigned int gen = *vgen;
+        __threadfence();
+        const unsigned int arrived = atomicAdd(bar, 1u);
+        int ok = 1;
+        if (arrived == gridDim.x - 1) {
+            *(volatile unsigned int*)bar = 0u;
+            __threadfence();
+            atomicAdd(&sc->bar_gen, 1u);
+        } else {
+            long long spins = 0;
+            while (*vgen == gen) {
+                if (*(volatile int*)&sc->error) { ok = 0; break; }
+                if (++spins > BARRIER_SPIN_LIMIT) {
+                    set_error(sc, ST_ETIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+        s_ok = ok && !*(volatile int*)&sc->error;
+    }
+    __syncthreads();
+    return s_ok != 0;
 }
 
 // Exclusive prefix of a 0/1 flag over the block (in thread order) and the total.

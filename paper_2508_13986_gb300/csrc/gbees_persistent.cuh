@@ -1,0 +1,146 @@
+// The whole step loop of a propagate call in one cooperative launch.
+//
+// For the grids of 10^4-10^5 cells of the Lorenz '63 workloads a time step is a
+// few microseconds of work split into dependent phases; kernel launches and
+// their drain would dominate. This kernel keeps one block per SM resident and
+// separates the phases by a bounded grid barrier (the cooperative-kernel
+// structure of Sec. 4, with GB300's block count). Every block computes the
+// step's scalars (dt, normalisation, maximum) itself from the same per-block
+// partials, so the scalars need no extra barrier; block 0 writes them back.
+//
+// Barriers per step: grow | link | (FP64: waves | faces |) update; a prune adds
+// mark | scatter | count | compact | relink.
+#pragma once
+
+#include "gbees_kernels.cuh"
+
+namespace gbees {
+
+template <int N, int DYN, typename T>
+__global__ void __launch_bounds__(THREADS, 1) k_persistent(const Model m, Bufs b, long long max_steps) {
+    DevScalars* sc = b.sc;
+    StepView v = view_of(m, sc);
+    double t = *(volatile double*)&sc->t;
+    const double tt = *(volatile double*)&sc->t_target;
+    int done = *(volatile int*)&sc->done;
+    long long step = *(volatile long long*)&sc->step;
+    unsigned long long maxrate = *(volatile unsigned long long*)&sc->maxrate_bits;
+    double w = *(volatile double*)&sc->w;
+    double last_dt = *(volatile double*)&sc->dt;
+    long long nsteps = 0, nupd = 0, fb = 0;
+    // every block has read the state before anyone changes it
+    if (done || *(volatile int*)&sc->error || !grid_barrier(sc)) return;
+
+    for (long long it = 0; it < max_steps && !done; ++it) {
+        // grow (appends to sc->N)
+        grow_body<N, T>(m, b, v);
+        if (!grid_barrier(sc)) return;
+        v.N = min(*(volatile long long*)&sc->N, m.cap);
+        // link the new cells; their CFL rates
+        {
+            const double r = link_body<N>(m, b, v.N_prev, v.N, v.g);
+            long long zero[NDIG] = {0, 0, 0, 0, 0, 0};
+            block_partial(b.part, zero, -INFINITY, r);
+        }
+        if (!grid_barrier(sc)) return;
+        {
+            Combined cr = combine_partials(b.part, gridDim.x);
+            maxrate = max(maxrate, cr.rate_bits);
+        }
+        const StepTime st = step_time(m, __longlong_as_double((long long)maxrate), t, tt, v.dth, v.ch);
+        if (!(st.dt > 0.0)) {
+            set_error(sc, ST_EDEGENERATE);
+            return;
+        }
+        // flux update
+        long long d[NDIG] = {0, 0, 0, 0, 0, 0};
+        double mx = -INFINITY;
+        int err = 0;
+        if constexpr (sizeof(T) == 8) {
+            waves_body<N, DYN>(m, b, v);
+            if (!grid_barrier(sc)) return;
+            fb += faces_body<N, DYN>(m, b, v);
+            if (!grid_barrier(sc)) return;
+            apply_body<N>(m, b, v, d, mx, err);
+        } else {
+            fb += gather_body<N, DYN, T>(m, b, v, d, mx, err);
+        }
+        if (err) set_error(sc, ST_EDEGENERATE);
+        block_partial(b.part, d, mx, 0.0);
+        if (!grid_barrier(sc)) return;
+        {
+            Combined cs = combine_partials(b.part, gridDim.x);
+            w = m.prod_h * acc_to_double(cs.acc);
+            if (!(w > 0.0) || !isfinite(w)) {
+                set_error(sc, ST_EDEGENERATE);
+                return;
+            }
+            v.scale = 1.0 / w;
+            v.maxq = cs.maxq_ord ? ord_val(cs.maxq_ord) : 0.0;
+        }
+        t = st.t_new;
+        last_dt = st.dt;
+        done = st.last;
+        step += 1;
+        nsteps += 1;
+        nupd += v.N;
+        v.pb ^= 1;
+        v.N_prev = v.N;
+        // prune (Algorithm 3) every prune_interval steps
+        if (m.prune_interval > 0 && step % m.prune_interval == 0) {
+            prune_mark_body<T>(m, b, v);
+            if (!grid_barrier(sc)) return;
+            prune_scatter_body<N, T>(m, b, v);
+            if (!grid_barrier(sc)) return;
+            prune_count_body(m, b, v);
+            if (!grid_barrier(sc)) return;
+            long long base, total;
+            block_offset_total(b, base, total);
+            if (blockIdx.x == 0 && threadIdx.x == 0) sc->N = total;  // before the next grow appends
+            {
+                long long dp[NDIG] = {0, 0, 0, 0, 0, 0};
+                double mxp = -INFINITY, rmax = 0.0;
+                int errp = 0;
+                prune_compact_body<N, T>(m, b, v, base, dp, mxp, rmax, errp);
+                if (errp) set_error(sc, ST_EDEGENERATE);
+                block_partial(b.part, dp, mxp, rmax);
+            }
+            if (!grid_barrier(sc)) return;
+            prune_relink_body<N>(m, b, v);
+            if (!grid_barrier(sc)) return;
+            Combined cp = combine_partials(b.part, gridDim.x);
+            w = m.prod_h * acc_to_double(cp.acc);
+            if (!(w > 0.0) || !isfinite(w) || total == 0) {
+                set_error(sc, ST_EDEGENERATE);
+                return;
+            }
+            v.scale = 1.0 / w;
+            v.maxq = cp.maxq_ord ? ord_val(cp.maxq_ord) : 0.0;
+            maxrate = cp.rate_bits;
+            v.N = total;
+            v.N_prev = total;
+            v.g ^= 1;
+            v.pb ^= 1;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        sc->N = v.N;
+        sc->N_prev = v.N_prev;
+        sc->pbuf = v.pb;
+        sc->gen = v.g;
+        sc->maxq = v.maxq;
+        sc->scale = v.scale;
+        sc->w = w;
+        sc->t = t;
+        sc->dt = last_dt;
+        sc->step = step;
+        sc->done = done;
+        sc->maxrate_bits = maxrate;
+        sc->steps_call += nsteps;
+        sc->updates_call += nupd;
+        sc->prune_now = 0;
+    }
+    if (fb) atomicAdd((unsigned long long*)&sc->lookups_fallback, (unsigned long long)fb);
+}
+
+}  // namespace gbees

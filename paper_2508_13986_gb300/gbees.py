@@ -25,6 +25,7 @@ STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ECAPACITY", -3: "EKEYRANGE", -4: "ED
 GBEES_DYN_CONSTANT, GBEES_DYN_LINEAR, GBEES_DYN_LORENZ63, GBEES_DYN_LORENZ63_SHIFTED, GBEES_DYN_LORENZ96 = range(5)
 GBEES_LIM_MC, GBEES_LIM_NONE, GBEES_LIM_LW = range(3)
 GBEES_FP64, GBEES_FP32 = 0, 1
+GBEES_LAUNCH_AUTO, GBEES_LAUNCH_PERSISTENT, GBEES_LAUNCH_GRAPH, GBEES_LAUNCH_DIRECT = range(4)
 
 
 class gbees_config(ctypes.Structure):
@@ -42,6 +43,7 @@ class gbees_config(ctypes.Structure):
         ("probe_width", ctypes.c_int32),
         ("max_cells", ctypes.c_int64),
         ("table_factor", ctypes.c_double),
+        ("launch_mode", ctypes.c_int32),
     ]
 
 
@@ -232,7 +234,7 @@ class Stats:
 def make_config(n: int, dynamics: int, params: Sequence[float], h: Sequence[float], x0: Sequence[float],
                 thr_rel: float = 1e-7, cfl: float = 0.9, prune_interval: int = 20, precision: int = GBEES_FP64,
                 limiter: int = GBEES_LIM_MC, max_cells: int = 1 << 20, table_factor: float = 2.0,
-                probe_width: int = 1) -> gbees_config:
+                probe_width: int = 1, launch_mode: int = GBEES_LAUNCH_AUTO) -> gbees_config:
     c = gbees_config()
     c.n, c.dynamics = int(n), int(dynamics)
     for k, v in enumerate(params):
@@ -243,6 +245,7 @@ def make_config(n: int, dynamics: int, params: Sequence[float], h: Sequence[floa
     c.thr_rel, c.cfl = float(thr_rel), float(cfl)
     c.prune_interval, c.precision, c.limiter = int(prune_interval), int(precision), int(limiter)
     c.probe_width, c.max_cells, c.table_factor = int(probe_width), int(max_cells), float(table_factor)
+    c.launch_mode = int(launch_mode)
     return c
 
 
@@ -350,8 +353,8 @@ class Grid:
 
 
 def grid_for_workload(w, precision: int = GBEES_FP64, max_cells: int = 1 << 20, device: str = "cuda:0",
-                      probe_width: int = 1, table_factor: float = 2.0) -> Grid:
+                      probe_width: int = 1, table_factor: float = 2.0, launch_mode: int = GBEES_LAUNCH_AUTO) -> Grid:
     """A Grid configured for a paper_2508_13986_gb300.workloads.Workload."""
     cfg = make_config(w.n, w.dynamics, w.params, w.h, w.x0, w.thr_rel, w.cfl, w.prune_interval, precision,
-                      w.limiter, max_cells, table_factor, probe_width)
+                      w.limiter, max_cells, table_factor, probe_width, launch_mode)
     return Grid(cfg, device)

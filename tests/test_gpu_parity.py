@@ -237,3 +237,34 @@ def test_very_unlikely_measurement_matches_oracle():
     g.propagate(0.01)
     o.propagate(0.01)
     assert_fp64_parity(g, o, w)
+
+
+@pytest.mark.parametrize("prec", [gbees.GBEES_FP64, gbees.GBEES_FP32])
+def test_launch_modes_agree_bitwise(prec):
+    """The persistent step-loop kernel, the CUDA-graph loop and one launch per kernel
+    run the same phase code and exact reductions: identical bits."""
+    w = W.lorenz63(h=0.5, t_end=0.06, measure_every=0.03, prune_interval=4)
+    modes = [gbees.GBEES_LAUNCH_PERSISTENT, gbees.GBEES_LAUNCH_GRAPH, gbees.GBEES_LAUNCH_DIRECT]
+    res = []
+    for mode in modes:
+        g = gbees.grid_for_workload(w, precision=prec, max_cells=1 << 16, launch_mode=mode)
+        g.init_gaussian(w.mean, w.cov)
+        for t_target, meas in w.segments():
+            g.propagate(t_target)
+            if meas is not None:
+                g.correct_gaussian(meas.y, meas.R, meas.H_idx)
+        res.append((*g.read_cells(), g.stats().total_steps))
+        g.close()
+    for i, p, s in res[1:]:
+        assert np.array_equal(i, res[0][0]) and np.array_equal(p, res[0][1]) and s == res[0][2]
+
+
+def test_profiled_direct_path_times_every_phase():
+    w = W.lorenz63(h=0.5, t_end=0.03, prune_interval=4)
+    g = gbees.grid_for_workload(w, max_cells=1 << 16)
+    g.profile(enable=True, reset=True)
+    g.init_gaussian(w.mean, w.cov)
+    st = g.propagate(w.t_end)
+    prof = g.profile(enable=False)
+    assert prof["timed"]["update"] >= st.steps and prof["ms"]["update"] > 0
+    assert prof["timed"]["grow"] >= st.steps and prof["launches"]["prune"] >= 5
