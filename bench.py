@@ -210,7 +210,10 @@ def time_precision(args, w, precision, dev, rank, world):
         total_steps += s
         peak = max(peak, pk)
     clk = clocks.stop()
-    launches = grid.profile()["total_launches"]
+    pt = grid.profile()
+    launches = pt["total_launches"]
+    persist_split = ({k: v / pt["persist_steps"] for k, v in pt["persist_us"].items()}
+                     if pt["persist_steps"] else None)
     barrier(world)
     torch.cuda.synchronize(dev)
 
@@ -281,6 +284,7 @@ def time_precision(args, w, precision, dev, rank, world):
             "avg_launch_us": upd_ms * 1e3 / launches_upd,
         },
         "phase_share": phase_share,
+        "persistent_us_per_step": persist_split,
         "gpu_launches": launches,
         "fallback_lookups": prof["fallback_lookups"],
         "clocks": clk,
@@ -381,6 +385,7 @@ def main_ours(args):
             "gpu_launches": main["gpu_launches"],
             "clocks": main["clocks"],
             "phase_share": main["phase_share"],
+            "persistent_us_per_step": main["persistent_us_per_step"],
             "fallback_lookups": main["fallback_lookups"],
         }
         if other is not None:
@@ -388,7 +393,8 @@ def main_ours(args):
                 "dtype": "f32" if args.precision == "f64" else "f64",
                 "value": other["value"], "ms_per_step": other["ms_per_step"], "e2e": other["e2e"],
                 "roofline": other["roofline"], "gpu_launches": other["gpu_launches"], "clocks": other["clocks"],
-                "phase_share": other["phase_share"]}
+                "phase_share": other["phase_share"],
+                "persistent_us_per_step": other["persistent_us_per_step"]}
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist

@@ -199,6 +199,13 @@ typedef struct {
     int64_t timed[GBEES_NPHASES];    /* launches that were timed */
     int64_t total_launches;          /* all kernel launches since the last reset */
     int64_t fallback_lookups;        /* edge and second-neighbour lookups that needed the hashtable */
+    /* persistent kernel (GBEES_LAUNCH_PERSISTENT / AUTO): microseconds that its
+     * block 0 spent per phase, measured with the SM clock between grid
+     * barriers -- grow (FP64: with the waves), link, faces (FP64), update
+     * (apply or single-pass), prune, step scalars -- and the steps covered
+     * (accumulated since the last init, not reset by reset) */
+    double persist_us[6];
+    int64_t persist_steps;
 } gbees_profile;
 
 /* enable != 0 turns event timing on; reset != 0 zeroes the counters. */

@@ -17,13 +17,14 @@
 
 namespace gbees {
 // update_inst.cu, one object per precision and model family
-#define GBEES_DECL(p, fam) int update_kernels_p##p##_f##fam(int n, int dyn, void** f, void** persist);
+#define GBEES_DECL(p, fam) bool update_kernels_p##p##_f##fam(int n, int dyn, Kernels* k);
 GBEES_DECL(64, 0) GBEES_DECL(64, 1) GBEES_DECL(64, 2) GBEES_DECL(64, 3) GBEES_DECL(64, 4) GBEES_DECL(64, 5)
 GBEES_DECL(32, 0) GBEES_DECL(32, 1) GBEES_DECL(32, 2) GBEES_DECL(32, 3) GBEES_DECL(32, 4) GBEES_DECL(32, 5)
 #undef GBEES_DECL
 
-// The update kernels of a model (launch order) and its persistent kernel.
-int update_kernels(const Model& m, bool f32, void** f, void** persist) {
+// The kernels of one time step of a model (before and after the link phase)
+// and its persistent step-loop kernel.
+bool update_kernels(const Model& m, bool f32, Kernels* k) {
     int fam;
     switch (m.dyn) {
         case DYN_LORENZ63:
@@ -32,12 +33,12 @@ int update_kernels(const Model& m, bool f32, void** f, void** persist) {
         case DYN_LINEAR: fam = m.n <= 3 ? 2 : 3; break;
         default: fam = m.n <= 3 ? 4 : 5; break;
     }
-    typedef int (*Entry)(int, int, void**, void**);
+    typedef bool (*Entry)(int, int, Kernels*);
     static const Entry e64[6] = {update_kernels_p64_f0, update_kernels_p64_f1, update_kernels_p64_f2,
                                  update_kernels_p64_f3, update_kernels_p64_f4, update_kernels_p64_f5};
     static const Entry e32[6] = {update_kernels_p32_f0, update_kernels_p32_f1, update_kernels_p32_f2,
                                  update_kernels_p32_f3, update_kernels_p32_f4, update_kernels_p32_f5};
-    return (f32 ? e32 : e64)[fam](m.n, m.dyn, f, persist);
+    return (f32 ? e32 : e64)[fam](m.n, m.dyn, k);
 }
 }  // namespace gbees
 
@@ -70,9 +71,8 @@ struct gbees_ctx {
     long long graph_launches = 0;
     // update kernels of the configured model (graph and direct paths) and the
     // persistent step-loop kernel with its cooperative grid size (0: unusable)
-    void* upd[4] = {nullptr, nullptr, nullptr, nullptr};
-    int n_upd = 0;
-    void* persist = nullptr;
+    Kernels kern{};
+    bool kern_ok = false;
     int persist_grid = 0;
     long long persist_max_cells = 1ll << 18;
     ~gbees_ctx() {
@@ -93,7 +93,8 @@ constexpr size_t ALIGN = 256;
 size_t align_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
 
 struct Layout {
-    size_t sc, blk, part, key[2], q[2], link[2], om[2], keep, map, table, wv_u, wv_g, fl, fu, total;
+    size_t sc, blk, part, key[2], q[2], link[2], om[2], slot[2], keep, map, table, wv_u, wv_g, fl, fu, bu, bt, bp,
+        total;
     unsigned long long slots;
 };
 
@@ -159,6 +160,7 @@ bool make_layout(const gbees_config* c, Layout* L) {
     for (int g = 0; g < 2; ++g) L->q[g] = take(S * cap);
     for (int g = 0; g < 2; ++g) L->link[g] = take((size_t)4 * 2 * c->n * cap);
     for (int g = 0; g < 2; ++g) L->om[g] = take(2 * cap);
+    for (int g = 0; g < 2; ++g) L->slot[g] = take(4 * cap);
     L->keep = take(cap);
     L->map = take(4 * cap);
     L->table = take(sizeof(Slot) * slots);
@@ -168,6 +170,10 @@ bool make_layout(const gbees_config* c, Layout* L) {
     L->wv_g = take(fp64);
     L->fl = take(fp64);
     L->fu = take(fp64);
+    // boundary faces, storage type
+    L->bu = take(S * 2 * c->n * cap);
+    L->bt = take(S * 2 * c->n * cap);
+    L->bp = take(S * 2 * c->n * cap);
     L->total = off;
     L->slots = slots;
     return true;
@@ -314,22 +320,20 @@ void launch_link(gbees_ctx* ctx, int step) {
 }
 
 void resolve_update_kernels(gbees_ctx* ctx) {
-    if (ctx->n_upd) return;
-    ctx->n_upd = update_kernels(ctx->m, ctx->cfg.precision == GBEES_FP32, ctx->upd, &ctx->persist);
+    if (ctx->kern_ok) return;
+    ctx->kern_ok = update_kernels(ctx->m, ctx->cfg.precision == GBEES_FP32, &ctx->kern);
     int dev = 0, sms = 0, per_sm = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess &&
+    if (ctx->kern_ok && cudaGetDevice(&dev) == cudaSuccess &&
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ctx->persist, THREADS, 0) == cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ctx->kern.persist, THREADS, 0) == cudaSuccess &&
         per_sm >= 1)
         ctx->persist_grid = std::min(GRID_MAX, sms);
     cudaGetLastError();
 }
 
-void launch_ctu(gbees_ctx* ctx) {
-    resolve_update_kernels(ctx);
+void launch_list(gbees_ctx* ctx, void* const* f, int nf) {
     void* args[] = {&ctx->m, &ctx->b};
-    for (int i = 0; i < ctx->n_upd; ++i)
-        cudaLaunchKernel(ctx->upd[i], dim3(ctx->grid), dim3(THREADS), args, 0, ctx->stream);
+    for (int i = 0; i < nf; ++i) cudaLaunchKernel(f[i], dim3(ctx->grid), dim3(THREADS), args, 0, ctx->stream);
 }
 
 // The prune of Algorithm 3 (directional marking, scan, compaction, relink,
@@ -352,20 +356,20 @@ void launch_prune(gbees_ctx* ctx) {
 // One time step: grow, link the new cells, flux update (the last block of the
 // update advances t and decides whether a prune is due).
 void launch_step(gbees_ctx* ctx) {
-    const int G = ctx->grid;
-    cudaStream_t s = ctx->stream;
-    with_nt(ctx, [&](auto NN, auto TT) {
-        constexpr int N = decltype(NN)::value;
-        using T = decltype(TT);
-        {
-            Phase ph(ctx, GBEES_PHASE_GROW, 1);
-            k_grow<N, T><<<G, THREADS, 0, s>>>(ctx->m, ctx->b);
-        }
+    resolve_update_kernels(ctx);
+    {
+        Phase ph(ctx, GBEES_PHASE_GROW, ctx->kern.npre);
+        launch_list(ctx, ctx->kern.pre, ctx->kern.npre);
+    }
+    {
         Phase ph(ctx, GBEES_PHASE_LINK, 1);
-        launch_link<N>(ctx, 1);
-    });
-    Phase ph(ctx, GBEES_PHASE_UPDATE, ctx->cfg.precision == GBEES_FP32 ? 1 : 3);
-    launch_ctu(ctx);
+        with_nt(ctx, [&](auto NN, auto) {
+            constexpr int N = decltype(NN)::value;
+            launch_link<N>(ctx, 1);
+        });
+    }
+    Phase ph(ctx, GBEES_PHASE_UPDATE, ctx->kern.npost);
+    launch_list(ctx, ctx->kern.post, ctx->kern.npost);
 }
 
 // ---- the step loop as a CUDA graph
@@ -411,13 +415,14 @@ void graph_nodes(gbees_ctx* ctx, GraphBuilder& gb, cudaGraph_t body, cudaGraphCo
     void* mb[] = {m, b};
     int one = 1;
     void* link_args[] = {m, b, &one};
-    cudaGraphNode_t n = gb.add(body, nullptr, (void*)k_grow<N, T>, G, THREADS, mb);
-    n = gb.add(body, n, link_kernel<N>(ctx->m.probe_width), G, THREADS, link_args);
     resolve_update_kernels(ctx);
-    for (int i = 0; i < ctx->n_upd; ++i) n = gb.add(body, n, ctx->upd[i], G, THREADS, mb);
+    cudaGraphNode_t n = nullptr;
+    for (int i = 0; i < ctx->kern.npre; ++i) n = gb.add(body, n, ctx->kern.pre[i], G, THREADS, mb);
+    n = gb.add(body, n, link_kernel<N>(ctx->m.probe_width), G, THREADS, link_args);
+    for (int i = 0; i < ctx->kern.npost; ++i) n = gb.add(body, n, ctx->kern.post[i], G, THREADS, mb);
     DevScalars* sc = ctx->b.sc;
     long long maxit = kGraphMaxIter;
-    int step_kernels = 2 + ctx->n_upd + 1;
+    int step_kernels = ctx->kern.npre + 1 + ctx->kern.npost + 1;
     void* ctl_args[] = {&sc, &hw, &hp, &maxit, &step_kernels};
     n = gb.add(body, n, (void*)k_loop_ctl, 1, 1, ctl_args);
     cudaGraph_t pb = nullptr;
@@ -561,6 +566,13 @@ int gbees_create(const gbees_config* cfg, void* d_workspace, size_t workspace_by
     }
     m.thr_rel = cfg->thr_rel;
     m.cfl = cfg->cfl;
+    for (int j = 0; j < cfg->n; ++j) {
+        m.inv_h[j] = 1.0 / cfg->h[j];
+        m.inv_2h[j] = 1.0 / (2.0 * cfg->h[j]);
+        m.hf[j] = (float)cfg->h[j];
+        m.x0f[j] = (float)cfg->x0[j];
+    }
+    for (int i = 0; i < 48; ++i) m.af[i] = (float)cfg->params[i];
     char* base = (char*)d_workspace;
     Bufs& b = ctx->b;
     b.sc = (DevScalars*)(base + L.sc);
@@ -572,6 +584,7 @@ int gbees_create(const gbees_config* cfg, void* d_workspace, size_t workspace_by
         b.link[g] = (int*)(base + L.link[g]);
     }
     for (int g = 0; g < 2; ++g) b.om[g] = (unsigned short*)(base + L.om[g]);
+    for (int g = 0; g < 2; ++g) b.slot[g] = (unsigned int*)(base + L.slot[g]);
     b.keep = (unsigned char*)(base + L.keep);
     b.map = (int*)(base + L.map);
     b.table = (Slot*)(base + L.table);
@@ -579,6 +592,9 @@ int gbees_create(const gbees_config* cfg, void* d_workspace, size_t workspace_by
     b.wv_g = (double*)(base + L.wv_g);
     b.fl = (double*)(base + L.fl);
     b.fu = (double*)(base + L.fu);
+    b.bu = (void*)(base + L.bu);
+    b.bt = (void*)(base + L.bt);
+    b.bp = (void*)(base + L.bp);
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
         delete ctx;
@@ -617,6 +633,16 @@ int gbees_profile_read(gbees_ctx* ctx, gbees_profile* out) {
     cudaStreamSynchronize(ctx->stream);
     drain_events(ctx);
     *out = ctx->prof;
+    DevScalars hs;
+    if (cudaMemcpy(&hs, ctx->b.sc, sizeof(DevScalars), cudaMemcpyDeviceToHost) == cudaSuccess) {
+        int dev = 0, khz = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
+        const double per_us = khz > 0 ? khz / 1e3 : 1.0;
+        for (int q = 0; q < 6; ++q) out->persist_us[q] = hs.phase_cycles[q] / per_us;
+        out->persist_steps = hs.phase_steps;
+    }
+    cudaGetLastError();
     return GBEES_OK;
 }
 
@@ -785,7 +811,7 @@ int gbees_propagate(gbees_ctx* ctx, double t_end, gbees_stats* stats) {
             const long long before = ctx->hs.steps_call;
             long long max_steps = kPersistSteps;
             void* args[] = {&ctx->m, &ctx->b, &max_steps};
-            if (!cuda_ok(ctx, cudaLaunchCooperativeKernel(ctx->persist, dim3(ctx->persist_grid), dim3(THREADS), args, 0, s),
+            if (!cuda_ok(ctx, cudaLaunchCooperativeKernel(ctx->kern.persist, dim3(ctx->persist_grid), dim3(THREADS), args, 0, s),
                          "propagate"))
                 return ctx->status;
             ctx->prof.total_launches += 1;
@@ -1031,6 +1057,13 @@ bool noalloc_setup(gbees_ctx* ctx, const gbees_config* cfg, void* base_ptr, cuda
     }
     m.thr_rel = cfg->thr_rel;
     m.cfl = cfg->cfl;
+    for (int j = 0; j < cfg->n; ++j) {
+        m.inv_h[j] = 1.0 / cfg->h[j];
+        m.inv_2h[j] = 1.0 / (2.0 * cfg->h[j]);
+        m.hf[j] = (float)cfg->h[j];
+        m.x0f[j] = (float)cfg->x0[j];
+    }
+    for (int i = 0; i < 48; ++i) m.af[i] = (float)cfg->params[i];
     char* base = (char*)base_ptr;
     Bufs& b = ctx->b;
     b.sc = (DevScalars*)(base + L.sc);
@@ -1042,6 +1075,7 @@ bool noalloc_setup(gbees_ctx* ctx, const gbees_config* cfg, void* base_ptr, cuda
         b.link[g] = (int*)(base + L.link[g]);
     }
     for (int g = 0; g < 2; ++g) b.om[g] = (unsigned short*)(base + L.om[g]);
+    for (int g = 0; g < 2; ++g) b.slot[g] = (unsigned int*)(base + L.slot[g]);
     b.keep = (unsigned char*)(base + L.keep);
     b.map = (int*)(base + L.map);
     b.table = (Slot*)(base + L.table);
@@ -1049,6 +1083,9 @@ bool noalloc_setup(gbees_ctx* ctx, const gbees_config* cfg, void* base_ptr, cuda
     b.wv_g = (double*)(base + L.wv_g);
     b.fl = (double*)(base + L.fl);
     b.fu = (double*)(base + L.fu);
+    b.bu = (void*)(base + L.bu);
+    b.bt = (void*)(base + L.bt);
+    b.bp = (void*)(base + L.bp);
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)

@@ -73,6 +73,10 @@ struct alignas(256) DevScalars {
     long long graph_kernels;  // kernels executed by graph launches (counted on the device)
     unsigned int bar_count;   // grid barrier of the persistent kernel: arrivals
     unsigned int bar_gen;     // and generation
+    // SM cycles spent by block 0 of the persistent kernel per phase (grow,
+    // link, faces, update, prune, combine/scalars) and the steps they cover
+    long long phase_cycles[8];
+    long long phase_steps;
     // the current step (written by the last block of the grow kernel)
     double step_dt;       // dt of the step being taken
     double step_t_new;    // time after it
@@ -101,7 +105,21 @@ struct Model {
     double thr_rel;
     double cfl;
     double prod_h;
+    double inv_h[MAXN];    // 1 / h_j
+    double inv_2h[MAXN];   // 1 / (2 h_j)
+    // float copies for the FP32 update (no double-to-float conversion per use)
+    float af[48];
+    float hf[MAXN];
+    float x0f[MAXN];
 };
+
+// Model parameter i in the arithmetic type of the caller.
+template <typename R>
+__device__ __forceinline__ R par(const Model& m, int i);
+template <>
+__device__ __forceinline__ double par<double>(const Model& m, int i) { return m.a[i]; }
+template <>
+__device__ __forceinline__ float par<float>(const Model& m, int i) { return m.af[i]; }
 
 // One block's share of a grid-wide reduction, written without atomics and
 // combined by whoever finishes the step (deterministic: integer digits, max).
@@ -129,6 +147,7 @@ struct Bufs {
     void* q[2];
     int* link[2];
     unsigned short* om[2];
+    unsigned int* slot[2];  // hashtable slot of each cell
     unsigned char* keep;
     int* map;
     Slot* table;
@@ -138,10 +157,28 @@ struct Bufs {
     double* wv_g;
     double* fl;
     double* fu;
+    // Boundary faces (2n arrays of cap values of the storage type, entry
+    // f * cap + c for face f = 2j + s of cell c whose neighbour across it is
+    // missing), filled before grow: bu = velocity at the face; when the missing
+    // neighbour is upwind, bt = sum_{d != j} G_d(neighbour) / (2 h_d) (times dt
+    // later) and bp = the value two cells away across the face (limiter).
+    void* bu;
+    void* bt;
+    void* bp;
     Partial* part;   // GRID_MAX per-block partials
 };
 
 constexpr unsigned short OM_COMPLETE = 0x8000;
+
+// The kernels of one time step for one model and precision: those before the
+// link phase, those after it, and the persistent step-loop kernel.
+struct Kernels {
+    void* pre[2];
+    int npre;
+    void* post[3];
+    int npost;
+    void* persist;
+};
 
 
 
@@ -303,26 +340,27 @@ __device__ __forceinline__ R drift(const Model& m, int dyn, const R* y, int j) {
     using A = Ar<R>;
     switch (dyn) {
         case DYN_CONSTANT:
-            return (R)m.a[j];
+            return par<R>(m, j);
         case DYN_LINEAR: {
             R s = 0;
 #pragma unroll
-            for (int k = 0; k < N; ++k) s = A::add(s, A::mul((R)m.a[j * N + k], y[k]));
-            return A::add(s, (R)m.a[N * N + j]);
+            for (int k = 0; k < N; ++k) s = A::add(s, A::mul(par<R>(m, j * N + k), y[k]));
+            return A::add(s, par<R>(m, N * N + j));
         }
         case DYN_LORENZ63:
             if (N != 3) return 0;
-            if (j == 0) return A::mul((R)m.a[0], A::sub(y[1], y[0]));
-            if (j == 1) return A::sub(A::mul(y[0], A::sub((R)m.a[1], y[2 % N])), y[1]);
-            return A::sub(A::mul(y[0], y[1]), A::mul((R)m.a[2], y[2 % N]));
+            if (j == 0) return A::mul(par<R>(m, 0), A::sub(y[1], y[0]));
+            if (j == 1) return A::sub(A::mul(y[0], A::sub(par<R>(m, 1), y[2 % N])), y[1]);
+            return A::sub(A::mul(y[0], y[1]), A::mul(par<R>(m, 2), y[2 % N]));
         case DYN_LORENZ63_SHIFTED:
             if (N != 3) return 0;
-            if (j == 0) return A::mul((R)m.a[0], A::sub(y[1], y[0]));
+            if (j == 0) return A::mul(par<R>(m, 0), A::sub(y[1], y[0]));
             if (j == 1) return A::sub(-y[1], A::mul(y[0], y[2 % N]));
-            return A::sub(A::add(A::mul(-(R)m.a[1], y[2 % N]), A::mul(y[0], y[1])), A::mul((R)m.a[1], (R)m.a[2]));
+            return A::sub(A::add(A::mul(-par<R>(m, 1), y[2 % N]), A::mul(y[0], y[1])),
+                          A::mul(par<R>(m, 1), par<R>(m, 2)));
         case DYN_LORENZ96: {
             const int jp = (j + 1) % N, jm2 = (j + N - 2) % N, jm1 = (j + N - 1) % N;
-            return A::add(A::sub(A::mul(A::sub(y[jp], y[jm2]), y[jm1]), y[j]), (R)m.a[0]);
+            return A::add(A::sub(A::mul(A::sub(y[jp], y[jm2]), y[jm1]), y[j]), par<R>(m, 0));
         }
     }
     return 0;
@@ -413,6 +451,37 @@ __device__ __forceinline__ void acc_add(long long (&d)[NDIG], double x, int& err
 #pragma unroll
     for (int q = 0; q < NDIG; ++q) {
         long long v = (q == k) ? d0 : (q == k + 1) ? d1 : (q == k + 2) ? d2 : 0;
+        d[q] += neg ? -v : v;
+    }
+}
+
+// The same for a float (integer operations only; a float is exactly a double).
+__device__ __forceinline__ void acc_add(long long (&d)[NDIG], float x, int& err) {
+    const unsigned int bits = __float_as_uint(x);
+    int ex = (int)((bits >> 23) & 0xff);
+    unsigned long long mt = bits & 0x7FFFFFu;
+    if (ex == 0xff) { err = 1; return; }
+    if (ex == 0) {
+        if (mt == 0) return;
+        ex = 1;
+    } else {
+        mt |= 1u << 23;
+    }
+    int pos = ex - 150 - ACC_LSB;  // x = mt * 2^(pos + ACC_LSB)
+    if (pos < 0) {
+        if (pos <= -32) return;
+        mt >>= -pos;
+        pos = 0;
+        if (mt == 0) return;
+    }
+    if (pos > 32 * NDIG - 24 - 1) { err = 1; return; }
+    const bool neg = (bits >> 31) != 0;
+    const int k = pos >> 5, r = pos & 31;
+    const unsigned long long sh = mt << r;  // at most 55 bits
+    const long long d0 = (long long)(sh & 0xffffffffull), d1 = (long long)(sh >> 32);
+#pragma unroll
+    for (int q = 0; q < NDIG; ++q) {
+        long long v = (q == k) ? d0 : (q == k + 1) ? d1 : 0;
         d[q] += neg ? -v : v;
     }
 }
@@ -533,17 +602,19 @@ __device__ __forceinline__ double block_max(double mx) {
     return m;
 }
 
-// True in every thread of exactly one block: the last one to arrive.
+// True in every thread of exactly one block: the last one to arrive. One
+// thread per block fences and takes a ticket (the block barrier before it
+// orders the block's writes; fences are cumulative).
 __device__ __forceinline__ bool last_block(DevScalars* sc) {
     __shared__ bool s_last;
-    __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
+        __threadfence();
         unsigned int t = atomicAdd(&sc->ticket, 1u);
         s_last = (t == gridDim.x - 1);
+        if (s_last) __threadfence();
     }
     __syncthreads();
-    if (s_last) __threadfence();
     return s_last;
 }
 
@@ -598,11 +669,14 @@ __device__ __forceinline__ void finish_step(const Model& m, DevScalars* sc, long
 }
 
 // Write this block's partial (exact digits, maximum value, maximum rate).
-// All threads of the block must call it; d, mx, rate are per thread.
+// All threads of the block must call it; d, mx, rate are per thread. The
+// maxima are reduced as order-preserving integer keys (integer pipe).
 __device__ __forceinline__ void block_partial(Partial* part, long long (&d)[NDIG], double mx, double rate) {
     __shared__ long long s_acc[WARPS][NDIG];
-    __shared__ double s_mx[WARPS], s_rt[WARPS];
+    __shared__ unsigned long long s_mx[WARPS], s_rt[WARPS];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned long long mk = mx > -INFINITY ? ord_key(mx) : 0ull;
+    unsigned long long rk = rate > 0.0 ? (unsigned long long)__double_as_longlong(rate) : 0ull;
 #pragma unroll
     for (int q = 0; q < NDIG; ++q) {
 #pragma unroll
@@ -610,27 +684,27 @@ __device__ __forceinline__ void block_partial(Partial* part, long long (&d)[NDIG
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
-        mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, off));
-        rate = fmax(rate, __shfl_down_sync(0xffffffffu, rate, off));
+        mk = max(mk, __shfl_down_sync(0xffffffffu, mk, off));
+        rk = max(rk, __shfl_down_sync(0xffffffffu, rk, off));
     }
     if (lane == 0) {
 #pragma unroll
         for (int q = 0; q < NDIG; ++q) s_acc[wid][q] = d[q];
-        s_mx[wid] = mx;
-        s_rt[wid] = rate;
+        s_mx[wid] = mk;
+        s_rt[wid] = rk;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         Partial p;
-        double m = -INFINITY, r = 0.0;
+        unsigned long long mm = 0, rr = 0;
         for (int q = 0; q < NDIG; ++q) p.acc[q] = 0;
         for (int w = 0; w < WARPS; ++w) {
             for (int q = 0; q < NDIG; ++q) p.acc[q] += s_acc[w][q];
-            m = fmax(m, s_mx[w]);
-            r = fmax(r, s_rt[w]);
+            mm = max(mm, s_mx[w]);
+            rr = max(rr, s_rt[w]);
         }
-        p.maxq_ord = m > -INFINITY ? ord_key(m) : 0ull;
-        p.rate_bits = r > 0.0 ? (unsigned long long)__double_as_longlong(r) : 0ull;
+        p.maxq_ord = mm;
+        p.rate_bits = rr;
         part[blockIdx.x] = p;
     }
     __syncthreads();

@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(THREADS) k_init_write(const Model m, Bufs b, c
                 b.key[0][c] = k;
                 static_cast<T*>(b.q[0])[c] = v;
                 b.om[0][c] = (unsigned short)outward_mask<N>(m, I);
-                table_insert_new(m, b, k, c);
+                table_insert_new(m, b, k, c, b.slot[0]);
                 acc_add(d, (double)v, err);
                 mx = fmax(mx, (double)v);
                 rmax = fmax(rmax, cfl_rate64<N>(m, I));
@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(THREADS) k_init_cells(const Model m, Bufs b, c
         b.key[0][c] = k;
         static_cast<T*>(b.q[0])[c] = v;
         b.om[0][c] = (unsigned short)outward_mask<N>(m, I);
-        table_insert_new(m, b, k, c);
+        table_insert_new(m, b, k, c, b.slot[0]);
         mx = fmax(mx, (double)v);
         rmax = fmax(rmax, cfl_rate64<N>(m, I));
     }
@@ -235,11 +235,26 @@ __device__ __forceinline__ void finish_step(const Model& m, DevScalars* sc, cons
     sc->ticket = 0;
 }
 
+// FP64 step, first phase: grow, and the waves and boundary faces of the cells
+// that existed before it.
 template <int N, int DYN>
-__global__ void __launch_bounds__(THREADS) k_waves(const Model m, Bufs b) {
+__global__ void __launch_bounds__(THREADS) k_grow_waves(const Model m, Bufs b) {
     DevScalars* sc = b.sc;
     if (*(volatile int*)&sc->done | *(volatile int*)&sc->error) return;
-    waves_body<N, DYN>(m, b, view_of(m, sc));
+    const StepView v = view_of(m, sc);
+    grow_body<N, double>(m, b, v);
+    waves_body<N, DYN>(m, b, v, v.N_prev);
+    boundary_body<N, DYN, double>(m, b, v, v.N_prev);
+}
+
+// Single-pass step, first phase: grow and the boundary faces of the old cells.
+template <int N, int DYN, typename T>
+__global__ void __launch_bounds__(THREADS) k_grow_boundary(const Model m, Bufs b) {
+    DevScalars* sc = b.sc;
+    if (*(volatile int*)&sc->done | *(volatile int*)&sc->error) return;
+    const StepView v = view_of(m, sc);
+    grow_body<N, T>(m, b, v);
+    boundary_body<N, DYN, T>(m, b, v, v.N_prev);
 }
 
 template <int N, int DYN>
@@ -275,7 +290,7 @@ __global__ void __launch_bounds__(THREADS) k_ctu(const Model m, Bufs b) {
     long long d[NDIG] = {0, 0, 0, 0, 0, 0};
     double mx = -INFINITY;
     int err = 0;
-    long long fb = gather_body<N, DYN, T>(m, b, v, d, mx, err);
+    long long fb = gather_faces_body<N, DYN, T>(m, b, v, d, mx, err);
     if (err) set_error(sc, ST_EDEGENERATE);
     if (fb) atomicAdd((unsigned long long*)&sc->lookups_fallback, (unsigned long long)fb);
     block_partial(b.part, d, mx, 0.0);

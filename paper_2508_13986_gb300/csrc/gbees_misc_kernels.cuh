@@ -42,7 +42,7 @@ __global__ void k_table_clear(const Model m, Bufs b) {
     const unsigned long long T = m.tmask + 1;
     for (unsigned long long s = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; s < T;
          s += (unsigned long long)gridDim.x * blockDim.x) {
-        reinterpret_cast<ulonglong2*>(b.table)[s] = make_ulonglong2(EMPTY_KEY, 0ull);
+        reinterpret_cast<ulonglong2*>(b.table)[s] = make_ulonglong2(EMPTY_KEY, ~0ull);
     }
 }
 
@@ -104,6 +104,8 @@ __global__ void k_reset(DevScalars* sc, double t0) {
     sc->graph_kernels = 0;
     sc->bar_count = 0;
     sc->bar_gen = 0;
+    for (int q = 0; q < 8; ++q) sc->phase_cycles[q] = 0;
+    sc->phase_steps = 0;
 }
 
 __global__ void k_set_count_from_new(DevScalars* sc) {

@@ -8,16 +8,35 @@
 // step's scalars (dt, normalisation, maximum) itself from the same per-block
 // partials, so the scalars need no extra barrier; block 0 writes them back.
 //
-// Barriers per step: grow | link | (FP64: waves | faces |) update; a prune adds
-// mark | scatter | count | compact | relink.
+// Barriers per step: grow (+ boundary faces, FP64: + waves) | link | (FP64:
+// faces |) update; a prune adds mark | scatter | count | compact | relink.
 #pragma once
 
 #include "gbees_kernels.cuh"
 
 namespace gbees {
 
+// The step's scalars, computed by one thread of each block (FP64 divisions are
+// expensive on this chip) and read by the others from shared memory.
+struct StepShared {
+    double dt, t_new, scale, maxq, w;
+    double dth[MAXN], ch[MAXN];
+    unsigned long long maxrate;
+    int last, bad;
+};
+
+// w = (prod h) sum, 1 / w and the maximum from combined partials (one thread).
+__device__ __forceinline__ void normalisation(const Model& m, const Combined& c, StepShared& ss) {
+    const double w = m.prod_h * acc_to_double(c.acc);
+    ss.w = w;
+    ss.bad = !(w > 0.0) || !isfinite(w);
+    ss.scale = ss.bad ? 0.0 : 1.0 / w;
+    ss.maxq = c.maxq_ord ? ord_val(c.maxq_ord) : 0.0;
+}
+
 template <int N, int DYN, typename T>
 __global__ void __launch_bounds__(THREADS, 1) k_persistent(const Model m, Bufs b, long long max_steps) {
+    __shared__ StepShared ss;
     DevScalars* sc = b.sc;
     StepView v = view_of(m, sc);
     double t = *(volatile double*)&sc->t;
@@ -30,11 +49,24 @@ __global__ void __launch_bounds__(THREADS, 1) k_persistent(const Model m, Bufs b
     long long nsteps = 0, nupd = 0, fb = 0;
     // every block has read the state before anyone changes it
     if (done || *(volatile int*)&sc->error || !grid_barrier(sc)) return;
+    // phase timing by block 0 (cycles between the barriers it passes)
+    long long pc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    long long t_mark = clock64();
+    auto mark = [&](int ph) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            const long long now = clock64();
+            pc[ph] += now - t_mark;
+            t_mark = now;
+        }
+    };
 
     for (long long it = 0; it < max_steps && !done; ++it) {
-        // grow (appends to sc->N)
+        // grow (appends to sc->N); FP64: the waves of the existing cells alongside
         grow_body<N, T>(m, b, v);
+        if constexpr (sizeof(T) == 8) waves_body<N, DYN>(m, b, v, v.N_prev);
+        boundary_body<N, DYN, T>(m, b, v, v.N_prev);
         if (!grid_barrier(sc)) return;
+        mark(0);
         v.N = min(*(volatile long long*)&sc->N, m.cap);
         // link the new cells; their CFL rates
         {
@@ -43,40 +75,63 @@ __global__ void __launch_bounds__(THREADS, 1) k_persistent(const Model m, Bufs b
             block_partial(b.part, zero, -INFINITY, r);
         }
         if (!grid_barrier(sc)) return;
+        mark(1);
         {
             Combined cr = combine_partials(b.part, gridDim.x);
             maxrate = max(maxrate, cr.rate_bits);
         }
-        const StepTime st = step_time(m, __longlong_as_double((long long)maxrate), t, tt, v.dth, v.ch);
+        if (threadIdx.x == 0) {
+            const StepTime st0 = step_time(m, __longlong_as_double((long long)maxrate), t, tt, ss.dth, ss.ch);
+            ss.dt = st0.dt;
+            ss.t_new = st0.t_new;
+            ss.last = st0.last;
+        }
+        __syncthreads();
+        StepTime st;
+        st.dt = ss.dt;
+        st.t_new = ss.t_new;
+        st.last = ss.last;
+        v.dt = ss.dt;
+#pragma unroll
+        for (int k = 0; k < MAXN; ++k) {
+            v.dth[k] = ss.dth[k];
+            v.ch[k] = ss.ch[k];
+        }
+        __syncthreads();
         if (!(st.dt > 0.0)) {
             set_error(sc, ST_EDEGENERATE);
             return;
         }
+        mark(5);
         // flux update
         long long d[NDIG] = {0, 0, 0, 0, 0, 0};
         double mx = -INFINITY;
         int err = 0;
         if constexpr (sizeof(T) == 8) {
-            waves_body<N, DYN>(m, b, v);
-            if (!grid_barrier(sc)) return;
             fb += faces_body<N, DYN>(m, b, v);
             if (!grid_barrier(sc)) return;
+            mark(2);
             apply_body<N>(m, b, v, d, mx, err);
         } else {
-            fb += gather_body<N, DYN, T>(m, b, v, d, mx, err);
+            fb += gather_faces_body<N, DYN, T>(m, b, v, d, mx, err);
         }
         if (err) set_error(sc, ST_EDEGENERATE);
         block_partial(b.part, d, mx, 0.0);
         if (!grid_barrier(sc)) return;
+        mark(3);
         {
             Combined cs = combine_partials(b.part, gridDim.x);
-            w = m.prod_h * acc_to_double(cs.acc);
-            if (!(w > 0.0) || !isfinite(w)) {
+            if (threadIdx.x == 0) normalisation(m, cs, ss);
+            __syncthreads();
+            w = ss.w;
+            v.scale = ss.scale;
+            v.maxq = ss.maxq;
+            const int bad = ss.bad;
+            __syncthreads();
+            if (bad) {
                 set_error(sc, ST_EDEGENERATE);
                 return;
             }
-            v.scale = 1.0 / w;
-            v.maxq = cs.maxq_ord ? ord_val(cs.maxq_ord) : 0.0;
         }
         t = st.t_new;
         last_dt = st.dt;
@@ -86,6 +141,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_persistent(const Model m, Bufs b
         nupd += v.N;
         v.pb ^= 1;
         v.N_prev = v.N;
+        mark(5);
         // prune (Algorithm 3) every prune_interval steps
         if (m.prune_interval > 0 && step % m.prune_interval == 0) {
             prune_mark_body<T>(m, b, v);
@@ -109,14 +165,19 @@ __global__ void __launch_bounds__(THREADS, 1) k_persistent(const Model m, Bufs b
             prune_relink_body<N>(m, b, v);
             if (!grid_barrier(sc)) return;
             Combined cp = combine_partials(b.part, gridDim.x);
-            w = m.prod_h * acc_to_double(cp.acc);
-            if (!(w > 0.0) || !isfinite(w) || total == 0) {
+            if (threadIdx.x == 0) normalisation(m, cp, ss);
+            __syncthreads();
+            w = ss.w;
+            v.scale = ss.scale;
+            v.maxq = ss.maxq;
+            const int bad = ss.bad || total == 0;
+            __syncthreads();
+            if (bad) {
                 set_error(sc, ST_EDEGENERATE);
                 return;
             }
-            v.scale = 1.0 / w;
-            v.maxq = cp.maxq_ord ? ord_val(cp.maxq_ord) : 0.0;
             maxrate = cp.rate_bits;
+            mark(4);
             v.N = total;
             v.N_prev = total;
             v.g ^= 1;
@@ -141,6 +202,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_persistent(const Model m, Bufs b
         sc->prune_now = 0;
     }
     if (fb) atomicAdd((unsigned long long*)&sc->lookups_fallback, (unsigned long long)fb);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        for (int q = 0; q < 8; ++q) sc->phase_cycles[q] += pc[q];
+        sc->phase_steps += nsteps;
+    }
 }
 
 }  // namespace gbees

@@ -27,6 +27,7 @@ struct StepView {
     double scale;      // 1 / w of the previous normalisation
     double dth[MAXN];  // dt / h_j of this step
     double ch[MAXN];   // dt / (2 h_j)
+    double dt;         // dt of this step
 };
 
 __device__ __forceinline__ StepView view_of(const Model& m, DevScalars* sc) {
@@ -41,6 +42,7 @@ __device__ __forceinline__ StepView view_of(const Model& m, DevScalars* sc) {
         v.dth[j] = *(volatile double*)&sc->coef_dth[j];
         v.ch[j] = *(volatile double*)&sc->coef_ch[j];
     }
+    v.dt = *(volatile double*)&sc->step_dt;
     return v;
 }
 
@@ -57,8 +59,8 @@ __device__ __forceinline__ StepTime step_time(const Model& m, double rate, doubl
     const bool last = dt >= rem;
     if (last) dt = rem;
     for (int j = 0; j < MAXN; ++j) {
-        dth[j] = j < m.n ? dt / m.h[j] : 0.0;
-        ch[j] = j < m.n ? dt / (2.0 * m.h[j]) : 0.0;
+        dth[j] = j < m.n ? dt * m.inv_h[j] : 0.0;
+        ch[j] = j < m.n ? dt * m.inv_2h[j] : 0.0;
     }
     StepTime s;
     s.dt = dt;
@@ -95,12 +97,15 @@ __device__ __forceinline__ int edge_by_links(const int* link, long long cap, con
     return -2;
 }
 
-// Insert cell c (key k) into the table; the key must be new.
-__device__ __forceinline__ void table_insert_new(const Model& m, const Bufs& b, unsigned long long k, long long c) {
+// Insert cell c (key k) into the table; the key must be new. slots[c]
+// records the table slot, so that a prune can empty exactly the used slots.
+__device__ __forceinline__ void table_insert_new(const Model& m, const Bufs& b, unsigned long long k, long long c,
+                                                 unsigned int* slots) {
     unsigned long long slot;
     int r = table_claim(m, b.table, k, &slot);
     if (r == 1) {
         b.table[slot].val = c;
+        slots[c] = (unsigned int)slot;
     } else if (r == 0) {
         set_error(b.sc, ST_EINVAL);  // duplicate cell
     } else {
@@ -133,6 +138,7 @@ __device__ __forceinline__ void grow_insert(const Model& m, const Bufs& b, int g
         return;
     }
     b.table[slot].val = c;
+    b.slot[g][c] = (unsigned int)slot;
     b.key[g][c] = k;
     static_cast<T*>(b.q[pb])[c] = (T)0;
 }
@@ -322,43 +328,144 @@ __device__ __forceinline__ T waves_of_missing(const Model& m, const Bufs& b, con
     return S;
 }
 
-// Pass 1: lower-face velocities and entering waves of every cell.
+// Pass 1, one work item per (cell, dimension d) of the cells [0, ncell): the
+// lower-face velocity u_d and the entering wave G_d of the cell. New cells (of
+// this step's grow) are left out: with P = 0 their waves are formed on the spot.
 template <int N, int DYN>
-__device__ __forceinline__ void waves_body(const Model& m, const Bufs& b, const StepView& v) {
-    const long long ncell = v.N;
+__device__ __forceinline__ void waves_body(const Model& m, const Bufs& b, const StepView& v, long long ncell) {
     const double* Q = static_cast<const double*>(b.q[v.pb]);
     const unsigned long long* key = b.key[v.g];
     const int* link = b.link[v.g];
     const long long cap = m.cap;
+    const long long items = ncell * N;
     double h[N];
 #pragma unroll
     for (int k = 0; k < N; ++k) h[k] = m.h[k];
-    for (WarpRuns wr(ncell); wr.next();) {
-        const long long c = wr.c;
-        if (c >= ncell) continue;
+    for (WarpRuns wr(items); wr.next();) {
+        const long long it = wr.c;
+        if (it >= items) continue;
+        const long long c = it / N;
+        const int d = (int)(it - c * N);
         int I[N];
         unpack_key<N>(m, key[c], I);
         const double P0 = Q[c];
+        const double Pm = q_or_zero<double>(Q, link[(long long)(2 * d) * cap + c]);
+        const double Pp = q_or_zero<double>(Q, link[(long long)(2 * d + 1) * cap + c]);
         double xc[N];
 #pragma unroll
         for (int k = 0; k < N; ++k) xc[k] = m.x0[k] + (double)I[k] * h[k];
+        double ul = 0.0, uh = 0.0;
 #pragma unroll
-        for (int d = 0; d < N; ++d) {
-            const double Pm = q_or_zero<double>(Q, link[(long long)(2 * d) * cap + c]);
-            const double Pp = q_or_zero<double>(Q, link[(long long)(2 * d + 1) * cap + c]);
-            const double ul = vel_at<N, DYN, double>(m, xc, h, -1, 0, d, -1);
-            const double uh = vel_at<N, DYN, double>(m, xc, h, -1, 0, d, +1);
-            b.wv_u[(long long)d * cap + c] = ul;
-            b.wv_g[(long long)d * cap + c] = fmax(ul, 0.0) * (P0 - Pm) + fmin(uh, 0.0) * (Pp - P0);
-        }
+        for (int dd = 0; dd < N; ++dd)
+            if (dd == d) {
+                ul = vel_at<N, DYN, double>(m, xc, h, -1, 0, dd, -1);
+                uh = vel_at<N, DYN, double>(m, xc, h, -1, 0, dd, +1);
+            }
+        b.wv_u[(long long)d * cap + c] = ul;
+        b.wv_g[(long long)d * cap + c] = fmax(ul, 0.0) * (P0 - Pm) + fmin(uh, 0.0) * (Pp - P0);
     }
 }
 
-// Pass 2: the flux through the lower face of every cell, and through its upper
-// face when the upper neighbour is missing. Returns the fallback lookups.
+// sum_{d != j} dt/(2 h_d) G_d(Y) for Y = c + s e_j (s = -1, 0, +1) formed on the
+// spot: y is Y's index (-1 when Y is missing, then P_Y = 0 and its transverse
+// neighbours are found through c's links). Used for missing and new cells.
+template <int N, int DYN>
+__device__ __forceinline__ double waves_here(const Model& m, const Bufs& b, const double* Q, const int* link,
+                                             long long cap, const int* L, const int* I, const double* xc,
+                                             const double* h, const double* ch, int j, int s, long long y,
+                                             long long& fb) {
+    const double PY = y >= 0 ? Q[y] : 0.0;
+    double S = 0.0;
+#pragma unroll
+    for (int d = 0; d < N; ++d) {
+        if (d == j) continue;
+        double Pm, Pp;
+        if (y >= 0) {
+            Pm = q_or_zero<double>(Q, link[(long long)(2 * d) * cap + y]);
+            Pp = q_or_zero<double>(Q, link[(long long)(2 * d + 1) * cap + y]);
+        } else {
+            Pm = q_or_zero<double>(Q, edge_index<N>(m, b, link, cap, L, I, j, s > 0, d, 0, fb));
+            Pp = q_or_zero<double>(Q, edge_index<N>(m, b, link, cap, L, I, j, s > 0, d, 1, fb));
+        }
+        const double ul = vel_at<N, DYN, double>(m, xc, h, s ? j : -1, s, d, -1);
+        const double uh = vel_at<N, DYN, double>(m, xc, h, s ? j : -1, s, d, +1);
+        S += ch[d] * (fmax(ul, 0.0) * (PY - Pm) + fmin(uh, 0.0) * (Pp - PY));
+    }
+    return S;
+}
+
+// Boundary faces, one item per (cell c, face f = 2j + s) of the cells [0, ncell)
+// whose neighbour across f is missing; run before grow (with it), so that a
+// neighbour that grow creates (P = 0, like a missing cell) has the same waves.
+// Writes bu (face velocity) and, when the missing neighbour is upwind of the
+// face, bt (its transverse waves over 2 h_d) and bp (the value two cells away).
+template <int N, int DYN, typename T>
+__device__ __forceinline__ void boundary_body(const Model& m, const Bufs& b, const StepView& v, long long ncell) {
+    const T* Q = static_cast<const T*>(b.q[v.pb]);
+    const unsigned long long* key = b.key[v.g];
+    const int* link = b.link[v.g];
+    const long long cap = m.cap;
+    T* bu = static_cast<T*>(b.bu);
+    T* bt = static_cast<T*>(b.bt);
+    T* bp = static_cast<T*>(b.bp);
+    T h[N], x0[N], i2h[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        h[k] = sizeof(T) == 4 ? (T)m.hf[k] : (T)m.h[k];
+        x0[k] = sizeof(T) == 4 ? (T)m.x0f[k] : (T)m.x0[k];
+        i2h[k] = (T)m.inv_2h[k];
+    }
+    long long fb = 0;
+    const long long items = ncell * 2 * N;
+    // grow runs concurrently: only cells below ncell count, anything it creates
+    // (or a slot it has claimed but not yet filled, value -1) is P = 0
+    auto qold = [&](int i) -> T { return (i >= 0 && i < ncell) ? Q[i] : (T)0; };
+    for (WarpRuns wr(items); wr.next();) {
+        const long long it = wr.c;
+        if (it >= items) continue;
+        const long long c = it / (2 * N);
+        const int f = (int)(it - c * 2 * N);
+        if (link[(long long)f * cap + c] >= 0) continue;
+        const int j = f >> 1, s = f & 1;
+        int I[N];
+        unpack_key<N>(m, key[c], I);
+        T xc[N];
+#pragma unroll
+        for (int k = 0; k < N; ++k) xc[k] = x0[k] + (T)I[k] * h[k];
+        T u = (T)0;
+#pragma unroll
+        for (int d = 0; d < N; ++d)
+            if (d == j) u = vel_at<N, DYN, T>(m, xc, h, -1, 0, d, s ? +1 : -1);
+        bu[(long long)f * cap + c] = u;
+        if (s ? !(u < (T)0) : !(u > (T)0)) continue;  // the missing neighbour is not upwind
+        int L[2 * N];
+#pragma unroll
+        for (int d = 0; d < 2 * N; ++d) L[d] = link[(long long)d * cap + c];
+        const int sgn = s ? 1 : -1;
+        T S = (T)0;
+#pragma unroll
+        for (int d = 0; d < N; ++d) {
+            if (d == j) continue;
+            const T Pm = qold(edge_index<N>(m, b, link, cap, L, I, j, s, d, 0, fb));
+            const T Pp = qold(edge_index<N>(m, b, link, cap, L, I, j, s, d, 1, fb));
+            const T ul = vel_at<N, DYN, T>(m, xc, h, j, sgn, d, -1);
+            const T uh = vel_at<N, DYN, T>(m, xc, h, j, sgn, d, +1);
+            S += i2h[d] * (fmax(ul, (T)0) * ((T)0 - Pm) + fmin(uh, (T)0) * Pp);
+        }
+        bt[(long long)f * cap + c] = S;
+        bp[(long long)f * cap + c] = qold(second_index<N>(m, b, link, cap, L, I, j, s, fb));
+    }
+    if (fb) atomicAdd((unsigned long long*)&b.sc->lookups_fallback, (unsigned long long)fb);
+}
+
+// Pass 2, one work item per (cell c, dimension j): the flux through the lower
+// j-face of c, and through its upper j-face when the upper neighbour is missing
+// (Eq. 7, the gathered corrections of Algorithm 1, the limited HR term).
+// Returns the fallback lookups.
 template <int N, int DYN>
 __device__ __forceinline__ long long faces_body(const Model& m, const Bufs& b, const StepView& v) {
     const long long ncell = v.N;
+    const long long nold = v.N_prev;
     const double* Q = static_cast<const double*>(b.q[v.pb]);
     const unsigned long long* key = b.key[v.g];
     const int* link = b.link[v.g];
@@ -366,92 +473,113 @@ __device__ __forceinline__ long long faces_body(const Model& m, const Bufs& b, c
     const double* wg = b.wv_g;
     const long long cap = m.cap;
     const int lim = m.limiter;
-    double h[N], ch[N], dth[N];
+    double h[N];
 #pragma unroll
-    for (int k = 0; k < N; ++k) {
-        h[k] = m.h[k];
-        ch[k] = v.ch[k];
-        dth[k] = v.dth[k];
-    }
+    for (int k = 0; k < N; ++k) h[k] = m.h[k];
     long long fb = 0;
-    for (WarpRuns wr(ncell); wr.next();) {
-        const long long c = wr.c;
-        if (c >= ncell) continue;
-        int L[2 * N];
-#pragma unroll
-        for (int d = 0; d < 2 * N; ++d) L[d] = link[(long long)d * cap + c];
+    const long long items = ncell * N;
+    for (WarpRuns wr(items); wr.next();) {
+        const long long it = wr.c;
+        if (it >= items) continue;
+        const long long c = it / N;
+        const int j = (int)(it - c * N);
+        const int Llo = link[(long long)(2 * j) * cap + c];
+        const int Lhi = link[(long long)(2 * j + 1) * cap + c];
         const double P0 = Q[c];
+        const double PL = q_or_zero<double>(Q, Llo);
+        const double dthj = v.dth[j];
+        int L[2 * N];
         int I[N];
         double xc[N];
         bool have_pos = false;
         auto pos = [&]() {
             if (!have_pos) {
+#pragma unroll
+                for (int d = 0; d < 2 * N; ++d) L[d] = link[(long long)d * cap + c];
                 unpack_key<N>(m, key[c], I);
 #pragma unroll
                 for (int k = 0; k < N; ++k) xc[k] = m.x0[k] + (double)I[k] * h[k];
                 have_pos = true;
             }
         };
+        auto face_u = [&](int side) -> double {  // velocity at the lower (0) or upper (1) j-face of c
+            pos();
+            double u = 0.0;
 #pragma unroll
-        for (int j = 0; j < N; ++j) {
-            {  // lower face (c, j)
-                const double u = wu[(long long)j * cap + c];
-                const double PL = q_or_zero<double>(Q, L[2 * j]);
-                double f = 0.0;
-                if (u != 0.0) {
-                    f = fmax(u, 0.0) * PL + fmin(u, 0.0) * P0;  // Eq. 7
-                    double S = 0.0;
-                    const long long Y = u > 0.0 ? (long long)L[2 * j] : c;
-                    if (Y >= 0) {
+            for (int dd = 0; dd < N; ++dd)
+                if (dd == j) u = vel_at<N, DYN, double>(m, xc, h, -1, 0, dd, side ? +1 : -1);
+            return u;
+        };
+        const bool old_cell = c < nold;
+        const double* bt = static_cast<const double*>(b.bt);
+        const double* bp = static_cast<const double*>(b.bp);
+        const double* bu = static_cast<const double*>(b.bu);
+        // transverse sum of the upwind cell Y = c + s e_j with index y; a missing or
+        // new neighbour of an old cell has its sum precomputed (boundary_body)
+        auto trans = [&](int s, long long y) -> double {
+            if (y >= 0 && y < nold) {
+                double S = 0.0;
 #pragma unroll
-                        for (int d = 0; d < N; ++d)
-                            if (d != j) S += ch[d] * wg[(long long)d * cap + Y];
-                    } else {
-                        pos();
-                        S = waves_of_missing<N, DYN, double>(m, b, Q, link, cap, L, I, xc, h, ch, j, 0, fb);
-                    }
-                    f -= u * S;  // Algorithm 1, gathered
-                    const double W = P0 - PL;
-                    if (lim != LIM_NONE && W != 0.0) {
-                        double Wup;
-                        if (u > 0.0) {
-                            pos();
-                            Wup = PL - q_or_zero<double>(Q, second_index<N>(m, b, link, cap, L, I, j, 0, fb));
-                        } else {
-                            Wup = q_or_zero<double>(Q, L[2 * j + 1]) - P0;
-                        }
-                        const double au = fabs(u);
-                        f += 0.5 * au * (1.0 - dth[j] * au) * limited_wave<double>(lim, W, Wup);
-                    }
-                }
-                b.fl[(long long)j * cap + c] = f;
+                for (int d = 0; d < N; ++d)
+                    if (d != j) S += v.ch[d] * wg[(long long)d * cap + y];
+                return S;
             }
-            if (L[2 * j + 1] < 0) {  // upper face (c + e_j, j): nobody else owns it
-                pos();
-                const double u = vel_at<N, DYN, double>(m, xc, h, -1, 0, j, +1);
-                double f = 0.0;
-                if (u != 0.0) {
-                    f = fmax(u, 0.0) * P0;  // PR = 0
-                    double S = 0.0;
+            if (old_cell && s != 0) {
+                const int f = 2 * j + (s > 0);
+                return v.dt * bt[(long long)f * cap + c];
+            }
+            pos();
+            return waves_here<N, DYN>(m, b, Q, link, cap, L, I, xc, h, v.ch, j, s, y, fb);
+        };
+        // value at c + 2 s e_j (limiter)
+        auto second = [&](int s) -> double {
+            const int Lm = s > 0 ? Lhi : Llo;
+            if (Lm >= 0) return q_or_zero<double>(Q, link[(long long)(2 * j + (s > 0)) * cap + Lm]);
+            if (old_cell) return bp[(long long)(2 * j + (s > 0)) * cap + c];
+            pos();
+            return q_or_zero<double>(Q, second_index<N>(m, b, link, cap, L, I, j, s > 0, fb));
+        };
+        {  // lower face (c, j)
+            const double u = old_cell ? wu[(long long)j * cap + c] : face_u(0);
+            double f = 0.0;
+            if (u != 0.0) {
+                f = fmax(u, 0.0) * PL + fmin(u, 0.0) * P0;  // Eq. 7
+                const double S = u > 0.0 ? trans(-1, (long long)Llo) : trans(0, c);
+                f -= u * S;  // Algorithm 1, gathered
+                const double W = P0 - PL;
+                if (lim != LIM_NONE && W != 0.0) {
+                    double Wup;
                     if (u > 0.0) {
-#pragma unroll
-                        for (int d = 0; d < N; ++d)
-                            if (d != j) S += ch[d] * wg[(long long)d * cap + c];
+                        Wup = PL - second(-1);
                     } else {
-                        S = waves_of_missing<N, DYN, double>(m, b, Q, link, cap, L, I, xc, h, ch, j, 1, fb);
+                        Wup = q_or_zero<double>(Q, Lhi) - P0;
                     }
-                    f -= u * S;
-                    const double W = 0.0 - P0;
-                    if (lim != LIM_NONE && W != 0.0) {
-                        double Wup;
-                        if (u > 0.0) Wup = P0 - q_or_zero<double>(Q, L[2 * j]);
-                        else Wup = q_or_zero<double>(Q, second_index<N>(m, b, link, cap, L, I, j, 1, fb)) - 0.0;
-                        const double au = fabs(u);
-                        f += 0.5 * au * (1.0 - dth[j] * au) * limited_wave<double>(lim, W, Wup);
-                    }
+                    const double au = fabs(u);
+                    f += 0.5 * au * (1.0 - dthj * au) * limited_wave<double>(lim, W, Wup);
                 }
-                b.fu[(long long)j * cap + c] = f;
             }
+            b.fl[(long long)j * cap + c] = f;
+        }
+        if (Lhi < 0) {  // upper face (c + e_j, j): nobody else owns it
+            const double u = old_cell ? bu[(long long)(2 * j + 1) * cap + c] : face_u(1);
+            double f = 0.0;
+            if (u != 0.0) {
+                f = fmax(u, 0.0) * P0;  // PR = 0
+                const double S = u > 0.0 ? trans(0, c) : trans(+1, -1);
+                f -= u * S;
+                const double W = 0.0 - P0;
+                if (lim != LIM_NONE && W != 0.0) {
+                    double Wup;
+                    if (u > 0.0) {
+                        Wup = P0 - PL;
+                    } else {
+                        Wup = second(+1) - 0.0;
+                    }
+                    const double au = fabs(u);
+                    f += 0.5 * au * (1.0 - dthj * au) * limited_wave<double>(lim, W, Wup);
+                }
+            }
+            b.fu[(long long)j * cap + c] = f;
         }
     }
     return fb;
@@ -603,6 +731,149 @@ __device__ __forceinline__ long long gather_body(const Model& m, const Bufs& b, 
     return fb;
 }
 
+// ------------------------------------------------------------------ single-pass update, one lane per face
+
+// The same update as gather_body with the 2n faces of a cell spread over a
+// group of G lanes (G = 8 for n <= 4, 16 for n = 5, 6; lane 2j + s owns the
+// lower (s = 0) or upper (s = 1) j-face). The cell's own waves and the update
+// are combined with shuffles inside the group, so each lane walks one face's
+// neighbourhood: 2n times more independent work than one lane per cell.
+template <int N, int DYN, typename T>
+__device__ __forceinline__ long long gather_faces_body(const Model& m, const Bufs& b, const StepView& v,
+                                                       long long (&dacc)[NDIG], double& mx, int& err) {
+    constexpr int G = (2 * N <= 8) ? 8 : 16;
+    const long long ncell = v.N;
+    const T* Q = static_cast<const T*>(b.q[v.pb]);
+    T* Qn = static_cast<T*>(b.q[v.pb ^ 1]);
+    const unsigned long long* key = b.key[v.g];
+    const int* link = b.link[v.g];
+    const long long cap = m.cap;
+    const int lim = m.limiter;
+    const T scale = (T)v.scale;
+    T h[N], x0[N], chT[N], dthT[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        h[k] = sizeof(T) == 4 ? (T)m.hf[k] : (T)m.h[k];
+        x0[k] = sizeof(T) == 4 ? (T)m.x0f[k] : (T)m.x0[k];
+        chT[k] = (T)v.ch[k];
+        dthT[k] = (T)v.dth[k];
+    }
+    T tmax = -INFINITY;
+    long long fb = 0;
+    const long long items = ncell * G;
+    const unsigned full = 0xffffffffu;
+    for (WarpRuns wr(items); wr.next();) {
+        // every lane of the warp takes part in the shuffles below
+        const long long it = wr.c;
+        const long long c = it / G;
+        const int l = (int)(it % G);
+        const bool cell_ok = c < ncell;
+        const bool face_ok = cell_ok && l < 2 * N;
+        const int j = face_ok ? (l >> 1) : 0;
+        const int side = l & 1;
+        T P0 = (T)0, Pn = (T)0, u = (T)0;
+        int Ls = -1;
+        int I[N];
+        T xc[N];
+        if (cell_ok) {
+            P0 = Q[c];
+            unpack_key<N>(m, key[c], I);
+#pragma unroll
+            for (int k = 0; k < N; ++k) xc[k] = x0[k] + (T)I[k] * h[k];
+        }
+        if (face_ok) {
+            Ls = link[(long long)(2 * j + side) * cap + c];
+            Pn = q_or_zero<T>(Q, Ls);
+#pragma unroll
+            for (int d = 0; d < N; ++d)
+                if (d == j) u = vel_at<N, DYN, T>(m, xc, h, -1, 0, d, side ? +1 : -1);
+        }
+        // the partner lane holds the other face of the same dimension
+        const T u_o = __shfl_xor_sync(full, u, 1, G);
+        const T Pn_o = __shfl_xor_sync(full, Pn, 1, G);
+        const T ulo = side ? u_o : u, uhi = side ? u : u_o;
+        const T Plo = side ? Pn_o : Pn, Phi = side ? Pn : Pn_o;
+        // G_j(c), the j-waves entering c; and sum over d of dt/(2 h_d) G_d(c)
+        const T Gj = face_ok ? fmax(ulo, (T)0) * (P0 - Plo) + fmin(uhi, (T)0) * (Phi - P0) : (T)0;
+        T chj = (T)0, dthj = (T)0;
+#pragma unroll
+        for (int k = 0; k < N; ++k)
+            if (k == j && face_ok) {
+                chj = chT[k];
+                dthj = dthT[k];
+            }
+        T tot = (side == 0) ? chj * Gj : (T)0;
+#pragma unroll
+        for (int off = G / 2; off > 0; off >>= 1) tot += __shfl_xor_sync(full, tot, off, G);
+        T contrib = (T)0;
+        if (face_ok) {
+            const T PL = side ? P0 : Pn;
+            const T PR = side ? Pn : P0;
+            T f = (T)0;
+            if (u != (T)0) {
+                f = fmax(u, (T)0) * PL + fmin(u, (T)0) * PR;  // Eq. 7
+                const bool upwind_is_c = side ? (u > (T)0) : (u < (T)0);
+                T S;
+                if (upwind_is_c) {
+                    S = tot - chj * Gj;
+                } else if (Ls < 0 && c < v.N_prev) {  // missing neighbour: precomputed waves
+                    S = (T)v.dt * static_cast<const T*>(b.bt)[(long long)(2 * j + side) * cap + c];
+                } else {  // the neighbour across this face (possibly new or missing)
+                    int L[2 * N];
+#pragma unroll
+                    for (int d = 0; d < 2 * N; ++d) L[d] = link[(long long)d * cap + c];
+                    const int sgn = side ? 1 : -1;
+                    S = (T)0;
+#pragma unroll
+                    for (int d = 0; d < N; ++d) {
+                        if (d == j) continue;
+                        T Pm, Pp;
+                        if (Ls >= 0) {
+                            Pm = q_or_zero<T>(Q, link[(long long)(2 * d) * cap + Ls]);
+                            Pp = q_or_zero<T>(Q, link[(long long)(2 * d + 1) * cap + Ls]);
+                        } else {
+                            Pm = q_or_zero<T>(Q, edge_index<N>(m, b, link, cap, L, I, j, side, d, 0, fb));
+                            Pp = q_or_zero<T>(Q, edge_index<N>(m, b, link, cap, L, I, j, side, d, 1, fb));
+                        }
+                        const T ul = vel_at<N, DYN, T>(m, xc, h, j, sgn, d, -1);
+                        const T uh = vel_at<N, DYN, T>(m, xc, h, j, sgn, d, +1);
+                        S += chT[d] * (fmax(ul, (T)0) * (Pn - Pm) + fmin(uh, (T)0) * (Pp - Pn));
+                    }
+                }
+                f -= u * S;  // Algorithm 1
+                const T W = PR - PL;
+                if (lim != LIM_NONE && W != (T)0) {
+                    T Wup;
+                    // value two cells away across this face
+                    auto second = [&]() -> T {
+                        if (Ls >= 0) return q_or_zero<T>(Q, link[(long long)(2 * j + side) * cap + Ls]);
+                        if (c < v.N_prev) return static_cast<const T*>(b.bp)[(long long)(2 * j + side) * cap + c];
+                        int L[2 * N];
+#pragma unroll
+                        for (int d = 0; d < 2 * N; ++d) L[d] = link[(long long)d * cap + c];
+                        return q_or_zero<T>(Q, second_index<N>(m, b, link, cap, L, I, j, side, fb));
+                    };
+                    if (u > (T)0) Wup = side ? (P0 - Plo) : (Plo - second());
+                    else Wup = side ? (second() - Phi) : (Phi - P0);
+                    const T au = fabs(u);
+                    f += (T)0.5 * au * ((T)1 - dthj * au) * limited_wave<T>(lim, W, Wup);
+                }
+            }
+            contrib = (side ? (T)1 : (T)-1) * dthj * f;
+        }
+#pragma unroll
+        for (int off = G / 2; off > 0; off >>= 1) contrib += __shfl_xor_sync(full, contrib, off, G);
+        if (cell_ok && l == 0) {
+            const T qn = (P0 - contrib) * scale;
+            Qn[c] = qn;
+            acc_add(dacc, qn, err);
+            tmax = fmax(tmax, qn);
+        }
+    }
+    if (tmax > -INFINITY) mx = fmax(mx, (double)tmax);
+    return fb;
+}
+
 // ------------------------------------------------------------------ prune
 
 // keep[c] = (p_c > p*): the significant cells S.
@@ -667,8 +938,8 @@ __device__ __forceinline__ void block_chunk(long long total, long long& c0, long
     c1 = min(total, c0 + per);
 }
 
-// This block's count of kept cells into blk[blockIdx.x]; the table is cleared
-// (grid-stride) for the rehash.
+// This block's count of kept cells into blk[blockIdx.x]; the table slots of
+// the current cells are emptied for the rehash (the table holds nothing else).
 __device__ __forceinline__ void prune_count_body(const Model& m, const Bufs& b, const StepView& v) {
     long long c0, c1;
     block_chunk(v.N, c0, c1);
@@ -684,10 +955,9 @@ __device__ __forceinline__ void prune_count_body(const Model& m, const Bufs& b, 
         b.blk[blockIdx.x] = t;
     }
     __syncthreads();
-    const unsigned long long T = m.tmask + 1;
-    for (unsigned long long s2 = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; s2 < T;
-         s2 += (unsigned long long)gridDim.x * blockDim.x)
-        reinterpret_cast<ulonglong2*>(b.table)[s2] = make_ulonglong2(EMPTY_KEY, 0ull);
+    const unsigned int* slots = b.slot[v.g];
+    for (long long c = c0 + threadIdx.x; c < c1; c += blockDim.x)
+        reinterpret_cast<ulonglong2*>(b.table)[slots[c]] = make_ulonglong2(EMPTY_KEY, ~0ull);
 }
 
 // Offset of this block's survivors (sum of the counts of the blocks before it)
@@ -782,7 +1052,7 @@ __device__ __forceinline__ void prune_relink_body(const Model& m, const Bufs& b,
             int l = link[(long long)d * cap + c];
             linko[(long long)d * cap + nc] = l >= 0 ? b.map[l] : -1;
         }
-        table_insert_new(m, b, keyo[nc], nc);
+        table_insert_new(m, b, keyo[nc], nc, b.slot[v.g ^ 1]);
     }
 }
 

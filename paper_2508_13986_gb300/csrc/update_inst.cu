@@ -23,17 +23,21 @@ using Real = double;
 using Real = float;
 #endif
 
+// pre: the kernels before the link phase; post: after it (all take (Model, Bufs)).
 template <int N, int DYN>
-static int kernels_of(void** f, void** persist) {
-    *persist = (void*)k_persistent<N, DYN, Real>;
+static void kernels_of(Kernels* k) {
+    k->persist = (void*)k_persistent<N, DYN, Real>;
 #if GBEES_PREC == 64
-    f[0] = (void*)k_waves<N, DYN>;
-    f[1] = (void*)k_faces<N, DYN>;
-    f[2] = (void*)k_apply<N>;
-    return 3;
+    k->pre[0] = (void*)k_grow_waves<N, DYN>;
+    k->npre = 1;
+    k->post[0] = (void*)k_faces<N, DYN>;
+    k->post[1] = (void*)k_apply<N>;
+    k->npost = 2;
 #else
-    f[0] = (void*)k_ctu<N, DYN, Real>;
-    return 1;
+    k->pre[0] = (void*)k_grow_boundary<N, DYN, Real>;
+    k->npre = 1;
+    k->post[0] = (void*)k_ctu<N, DYN, Real>;
+    k->npost = 1;
 #endif
 }
 
@@ -41,36 +45,36 @@ static int kernels_of(void** f, void** persist) {
 #define GBEES_JOIN(a, b) GBEES_JOIN2(a, b)
 #define GBEES_ENTRY GBEES_JOIN(GBEES_JOIN(update_kernels_p, GBEES_PREC), GBEES_JOIN(_f, GBEES_FAMILY))
 
-// Kernels for dimension n and model dyn of this family; 0 when not covered.
-int GBEES_ENTRY(int n, int dyn, void** f, void** persist) {
+// Kernels for dimension n and model dyn of this family; false when not covered.
+bool GBEES_ENTRY(int n, int dyn, Kernels* k) {
 #if GBEES_FAMILY == 0
-    if (n != 3) return 0;
-    if (dyn == DYN_LORENZ63) return kernels_of<3, DYN_LORENZ63>(f, persist);
-    if (dyn == DYN_LORENZ63_SHIFTED) return kernels_of<3, DYN_LORENZ63_SHIFTED>(f, persist);
-    return 0;
+    if (n != 3) return false;
+    if (dyn == DYN_LORENZ63) { kernels_of<3, DYN_LORENZ63>(k); return true; }
+    if (dyn == DYN_LORENZ63_SHIFTED) { kernels_of<3, DYN_LORENZ63_SHIFTED>(k); return true; }
+    return false;
 #elif GBEES_FAMILY == 1
     switch (n) {
-        case 4: return kernels_of<4, DYN_LORENZ96>(f, persist);
-        case 5: return kernels_of<5, DYN_LORENZ96>(f, persist);
-        case 6: return kernels_of<6, DYN_LORENZ96>(f, persist);
+        case 4: kernels_of<4, DYN_LORENZ96>(k); return true;
+        case 5: kernels_of<5, DYN_LORENZ96>(k); return true;
+        case 6: kernels_of<6, DYN_LORENZ96>(k); return true;
     }
-    return 0;
+    return false;
 #elif GBEES_FAMILY == 2 || GBEES_FAMILY == 4
     constexpr int D = GBEES_FAMILY == 2 ? DYN_LINEAR : DYN_CONSTANT;
     switch (n) {
-        case 1: return kernels_of<1, D>(f, persist);
-        case 2: return kernels_of<2, D>(f, persist);
-        case 3: return kernels_of<3, D>(f, persist);
+        case 1: kernels_of<1, D>(k); return true;
+        case 2: kernels_of<2, D>(k); return true;
+        case 3: kernels_of<3, D>(k); return true;
     }
-    return 0;
+    return false;
 #else
     constexpr int D = GBEES_FAMILY == 3 ? DYN_LINEAR : DYN_CONSTANT;
     switch (n) {
-        case 4: return kernels_of<4, D>(f, persist);
-        case 5: return kernels_of<5, D>(f, persist);
-        case 6: return kernels_of<6, D>(f, persist);
+        case 4: kernels_of<4, D>(k); return true;
+        case 5: kernels_of<5, D>(k); return true;
+        case 6: kernels_of<6, D>(k); return true;
     }
-    return 0;
+    return false;
 #endif
 }
 

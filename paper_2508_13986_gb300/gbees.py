@@ -70,6 +70,8 @@ class gbees_profile(ctypes.Structure):
         ("timed", ctypes.c_int64 * GBEES_NPHASES),
         ("total_launches", ctypes.c_int64),
         ("fallback_lookups", ctypes.c_int64),
+        ("persist_us", ctypes.c_double * 6),
+        ("persist_steps", ctypes.c_int64),
     ]
 
 
@@ -347,6 +349,9 @@ class Grid:
             "timed": {k: int(pr.timed[i]) for i, k in enumerate(PHASE_NAMES)},
             "total_launches": int(pr.total_launches),
             "fallback_lookups": int(pr.fallback_lookups),
+            "persist_us": {k: float(pr.persist_us[i]) for i, k in
+                           enumerate(("grow", "link", "faces", "update", "prune", "scalars"))},
+            "persist_steps": int(pr.persist_steps),
         }
 
     _prof_on = False
