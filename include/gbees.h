@@ -31,8 +31,13 @@
  *     read or written only during the call.
  *   - Cell indices are signed integers; cell i has centre x0 + i * h (Eq. 5).
  *     Keys pack the indices with floor(63 / n) bits per dimension (32 for n = 1),
- *     so |i_j| must stay below 2^(bits-1); a cell outside that range is
- *     GBEES_EKEYRANGE.
+ *     i.e. -2^(bits-1) <= i_j < 2^(bits-1). An active cell must lie one layer
+ *     inside that range (-2^(bits-1) < i_j < 2^(bits-1) - 1), so that its face
+ *     neighbours have keys; an active cell outside is GBEES_EKEYRANGE.
+ *   - Capacity: the pool holds the active cells and their halo (every face
+ *     neighbour of an active cell that is not active, kept with p = 0 so that
+ *     the update reaches all its stencil cells through links). max_cells
+ *     bounds both together; gbees_stats.n_pool reports the current total.
  */
 #ifndef GBEES_H
 #define GBEES_H
@@ -47,7 +52,7 @@ extern "C" {
 typedef enum {
     GBEES_OK = 0,
     GBEES_EINVAL = -1,      /* bad argument or configuration */
-    GBEES_ECAPACITY = -2,   /* more active cells than max_cells (fixed capacity, Sec. 4.1) */
+    GBEES_ECAPACITY = -2,   /* more active and halo cells than max_cells (fixed capacity, Sec. 4.1) */
     GBEES_EKEYRANGE = -3,   /* a cell index does not fit the packed key */
     GBEES_EDEGENERATE = -4, /* total probability is zero or not finite (e.g. C = 0 in Eq. 4) */
     GBEES_ECUDA = -5,       /* a CUDA runtime call failed */
@@ -95,7 +100,7 @@ typedef struct {
     int32_t precision;      /* GBEES_FP64 | GBEES_FP32 */
     int32_t limiter;        /* GBEES_LIM_* */
     int32_t probe_width;    /* lanes that probe the hashtable together: 1, 2, 4, 8, 16 or 32 (0 = 1) */
-    int64_t max_cells;      /* fixed cell capacity (Sec. 4.1) */
+    int64_t max_cells;      /* fixed capacity of active plus halo cells (Sec. 4.1) */
     double table_factor;    /* hashtable slots per cell of capacity, >= 1.25 (0 = 2.0, Sec. 4.2) */
     int32_t launch_mode;    /* GBEES_LAUNCH_*: how propagate drives the time steps */
 } gbees_config;
@@ -117,6 +122,7 @@ typedef struct {
     int64_t total_steps;  /* steps since the last init */
     int64_t n_cells;      /* active cells on return */
     double norm;          /* (prod h) * sum of the stored values before the last normalisation */
+    int64_t n_pool;       /* active cells plus halo cells on return (what max_cells bounds) */
 } gbees_stats;
 
 typedef struct gbees_ctx gbees_ctx;

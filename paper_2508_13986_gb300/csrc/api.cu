@@ -93,8 +93,7 @@ constexpr size_t ALIGN = 256;
 size_t align_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
 
 struct Layout {
-    size_t sc, blk, part, key[2], q[2], link[2], om[2], slot[2], keep, map, table, wv_u, wv_g, fl, fu, bu, bt, bp,
-        total;
+    size_t sc, blk, part, key[2], q[2], link[2], om[2], slot[2], keep, map, table, wv_u, wv_g, fl, total;
     unsigned long long slots;
 };
 
@@ -154,7 +153,7 @@ bool make_layout(const gbees_config* c, Layout* L) {
         return at;
     };
     L->sc = take(sizeof(DevScalars));
-    L->blk = take(sizeof(long long) * (GRID_MAX + 1));
+    L->blk = take(sizeof(long long) * 2 * (GRID_MAX + 1));
     L->part = take(sizeof(Partial) * GRID_MAX);
     for (int g = 0; g < 2; ++g) L->key[g] = take(8 * cap);
     for (int g = 0; g < 2; ++g) L->q[g] = take(S * cap);
@@ -169,14 +168,63 @@ bool make_layout(const gbees_config* c, Layout* L) {
     L->wv_u = take(fp64);
     L->wv_g = take(fp64);
     L->fl = take(fp64);
-    L->fu = take(fp64);
-    // boundary faces, storage type
-    L->bu = take(S * 2 * c->n * cap);
-    L->bt = take(S * 2 * c->n * cap);
-    L->bp = take(S * 2 * c->n * cap);
     L->total = off;
     L->slots = slots;
     return true;
+}
+
+// The model constants and the buffer pointers of a context over a workspace
+// laid out by make_layout.
+void bind_context(gbees_ctx* ctx, const gbees_config* cfg, const Layout& L, void* workspace, cudaStream_t stream) {
+    ctx->cfg = *cfg;
+    ctx->stream = stream;
+    ctx->status = GBEES_OK;
+    ctx->has_grid = false;
+    Model& m = ctx->m;
+    std::memset(&m, 0, sizeof m);
+    m.n = cfg->n;
+    m.dyn = cfg->dynamics;
+    m.limiter = cfg->limiter;
+    m.key_bits = key_bits_for(cfg->n);
+    m.prune_interval = cfg->prune_interval;
+    m.probe_width = cfg->probe_width ? cfg->probe_width : 1;
+    m.cap = cfg->max_cells;
+    m.tmask = L.slots - 1;
+    std::memcpy(m.a, cfg->params, sizeof m.a);
+    m.prod_h = 1.0;
+    for (int j = 0; j < cfg->n; ++j) {
+        m.h[j] = cfg->h[j];
+        m.x0[j] = cfg->x0[j];
+        m.prod_h *= cfg->h[j];
+    }
+    m.thr_rel = cfg->thr_rel;
+    m.cfl = cfg->cfl;
+    for (int j = 0; j < cfg->n; ++j) {
+        m.inv_h[j] = 1.0 / cfg->h[j];
+        m.inv_2h[j] = 1.0 / (2.0 * cfg->h[j]);
+        m.hf[j] = (float)cfg->h[j];
+        m.x0f[j] = (float)cfg->x0[j];
+    }
+    for (int i = 0; i < 48; ++i) m.af[i] = (float)cfg->params[i];
+    char* base = (char*)workspace;
+    Bufs& b = ctx->b;
+    b.sc = (DevScalars*)(base + L.sc);
+    b.blk = (long long*)(base + L.blk);
+    b.blk2 = b.blk + (GRID_MAX + 1);
+    b.part = (Partial*)(base + L.part);
+    for (int g = 0; g < 2; ++g) {
+        b.key[g] = (unsigned long long*)(base + L.key[g]);
+        b.q[g] = (void*)(base + L.q[g]);
+        b.link[g] = (int*)(base + L.link[g]);
+        b.om[g] = (unsigned short*)(base + L.om[g]);
+        b.slot[g] = (unsigned int*)(base + L.slot[g]);
+    }
+    b.keep = (unsigned char*)(base + L.keep);
+    b.map = (int*)(base + L.map);
+    b.table = (Slot*)(base + L.table);
+    b.wv_u = (double*)(base + L.wv_u);
+    b.wv_g = (double*)(base + L.wv_g);
+    b.fl = (double*)(base + L.fl);
 }
 
 void set_err(gbees_ctx* ctx, int st, const std::string& msg) {
@@ -347,13 +395,26 @@ void launch_prune(gbees_ctx* ctx) {
         using T = decltype(TT);
         k_prune_mark<T><<<G, THREADS, 0, s>>>(ctx->m, ctx->b);
         k_prune_scatter<N, T><<<G, THREADS, 0, s>>>(ctx->m, ctx->b);
-        k_prune_count<<<G, THREADS, 0, s>>>(ctx->m, ctx->b);
+        k_prune_count<N><<<G, THREADS, 0, s>>>(ctx->m, ctx->b);
         k_prune_compact<N, T><<<G, THREADS, 0, s>>>(ctx->m, ctx->b);
         k_prune_relink<N><<<G, THREADS, 0, s>>>(ctx->m, ctx->b, G);
     });
 }
 
-// One time step: grow, link the new cells, flux update (the last block of the
+// The active cells (indices, densities) into d_idx / d_p in storage order.
+void launch_readout(gbees_ctx* ctx, int* d_idx, double* d_p) {
+    const int G = ctx->grid;
+    cudaStream_t s = ctx->stream;
+    k_readout_count<<<G, THREADS, 0, s>>>(ctx->m, ctx->b);
+    k_scan_blocks<<<1, THREADS, 0, s>>>(ctx->b, G, ctx->m.cap);
+    with_nt(ctx, [&](auto NN, auto TT) {
+        constexpr int NC = decltype(NN)::value;
+        using T = decltype(TT);
+        k_readout<NC, T><<<G, THREADS, 0, s>>>(ctx->m, ctx->b, d_idx, d_p);
+    });
+}
+
+// One time step: grow, halo, link the new entries, flux update (the last block of the
 // update advances t and decides whether a prune is due).
 void launch_step(gbees_ctx* ctx) {
     resolve_update_kernels(ctx);
@@ -432,7 +493,7 @@ void graph_nodes(gbees_ctx* ctx, GraphBuilder& gb, cudaGraph_t body, cudaGraphCo
     void* relink_args[] = {m, b, &nblk};
     cudaGraphNode_t q = gb.add(pb, nullptr, (void*)k_prune_mark<T>, G, THREADS, mb);
     q = gb.add(pb, q, (void*)k_prune_scatter<N, T>, G, THREADS, mb);
-    q = gb.add(pb, q, (void*)k_prune_count, G, THREADS, mb);
+    q = gb.add(pb, q, (void*)k_prune_count<N>, G, THREADS, mb);
     q = gb.add(pb, q, (void*)k_prune_compact<N, T>, G, THREADS, mb);
     gb.add(pb, q, (void*)k_prune_relink<N>, G, THREADS, relink_args);
 }
@@ -543,65 +604,14 @@ int gbees_create(const gbees_config* cfg, void* d_workspace, size_t workspace_by
     make_layout(cfg, &L);
     if (!d_workspace || workspace_bytes < L.total || ((uintptr_t)d_workspace % ALIGN) != 0) return GBEES_EINVAL;
     gbees_ctx* ctx = new gbees_ctx();
-    ctx->cfg = *cfg;
-    ctx->stream = (cudaStream_t)cuda_stream;
-    ctx->status = GBEES_OK;
-    ctx->has_grid = false;
-    Model& m = ctx->m;
-    std::memset(&m, 0, sizeof m);
-    m.n = cfg->n;
-    m.dyn = cfg->dynamics;
-    m.limiter = cfg->limiter;
-    m.key_bits = key_bits_for(cfg->n);
-    m.prune_interval = cfg->prune_interval;
-    m.probe_width = cfg->probe_width ? cfg->probe_width : 1;
-    m.cap = cfg->max_cells;
-    m.tmask = L.slots - 1;
-    std::memcpy(m.a, cfg->params, sizeof m.a);
-    m.prod_h = 1.0;
-    for (int j = 0; j < cfg->n; ++j) {
-        m.h[j] = cfg->h[j];
-        m.x0[j] = cfg->x0[j];
-        m.prod_h *= cfg->h[j];
-    }
-    m.thr_rel = cfg->thr_rel;
-    m.cfl = cfg->cfl;
-    for (int j = 0; j < cfg->n; ++j) {
-        m.inv_h[j] = 1.0 / cfg->h[j];
-        m.inv_2h[j] = 1.0 / (2.0 * cfg->h[j]);
-        m.hf[j] = (float)cfg->h[j];
-        m.x0f[j] = (float)cfg->x0[j];
-    }
-    for (int i = 0; i < 48; ++i) m.af[i] = (float)cfg->params[i];
-    char* base = (char*)d_workspace;
-    Bufs& b = ctx->b;
-    b.sc = (DevScalars*)(base + L.sc);
-    b.blk = (long long*)(base + L.blk);
-    b.part = (Partial*)(base + L.part);
-    for (int g = 0; g < 2; ++g) {
-        b.key[g] = (unsigned long long*)(base + L.key[g]);
-        b.q[g] = (void*)(base + L.q[g]);
-        b.link[g] = (int*)(base + L.link[g]);
-    }
-    for (int g = 0; g < 2; ++g) b.om[g] = (unsigned short*)(base + L.om[g]);
-    for (int g = 0; g < 2; ++g) b.slot[g] = (unsigned int*)(base + L.slot[g]);
-    b.keep = (unsigned char*)(base + L.keep);
-    b.map = (int*)(base + L.map);
-    b.table = (Slot*)(base + L.table);
-    b.wv_u = (double*)(base + L.wv_u);
-    b.wv_g = (double*)(base + L.wv_g);
-    b.fl = (double*)(base + L.fl);
-    b.fu = (double*)(base + L.fu);
-    b.bu = (void*)(base + L.bu);
-    b.bt = (void*)(base + L.bt);
-    b.bp = (void*)(base + L.bp);
+    bind_context(ctx, cfg, L, d_workspace, (cudaStream_t)cuda_stream);
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
         delete ctx;
         return GBEES_ECUDA;
     }
     ctx->grid = std::min(GRID_MAX, std::max(1, sms * 4));
-    k_reset<<<1, 1, 0, ctx->stream>>>(b.sc, 0.0);
+    k_reset<<<1, 1, 0, ctx->stream>>>(ctx->b.sc, 0.0);
     if (!sync_scalars(ctx, "create")) {
         int st = ctx->status;
         delete ctx;
@@ -706,7 +716,7 @@ int gbees_init_gaussian(gbees_ctx* ctx, const double* mean, const double* cov, d
         return GBEES_EINVAL;
     }
     {
-        Phase ph(ctx, GBEES_PHASE_OTHER, 6);
+        Phase ph(ctx, GBEES_PHASE_OTHER, 7);
         with_nt(ctx, [&](auto NN, auto TT) {
             constexpr int N = decltype(NN)::value;
             using T = decltype(TT);
@@ -715,8 +725,10 @@ int gbees_init_gaussian(gbees_ctx* ctx, const double* mean, const double* cov, d
             k_init_write<N, T><<<G, THREADS, 0, s>>>(ctx->m, ctx->b, bx);
         });
         k_set_count_from_new<<<1, 1, 0, s>>>(ctx->b.sc);
-        with_nt(ctx, [&](auto NN, auto) {
+        with_nt(ctx, [&](auto NN, auto TT) {
             constexpr int N = decltype(NN)::value;
+            using T = decltype(TT);
+            k_halo<N, T, 0><<<G, THREADS, 0, s>>>(ctx->m, ctx->b);
             launch_link<N>(ctx, 0);
         });
         k_finalise<<<1, 1, 0, s>>>(ctx->m, ctx->b.sc, 0);
@@ -741,7 +753,7 @@ int gbees_init_cells(gbees_ctx* ctx, const int32_t* idx, const double* p, int64_
     }
     cudaStream_t s = ctx->stream;
     const int G = ctx->grid;
-    Phase ph(ctx, GBEES_PHASE_OTHER, N > 0 ? 6 : 5);
+    Phase ph(ctx, GBEES_PHASE_OTHER, N > 0 ? 7 : 6);
     k_reset<<<1, 1, 0, s>>>(ctx->b.sc, t0);
     k_table_clear<<<G, THREADS, 0, s>>>(ctx->m, ctx->b);
     // stage the inputs in the second buffer set (unused outside a prune)
@@ -759,8 +771,10 @@ int gbees_init_cells(gbees_ctx* ctx, const int32_t* idx, const double* p, int64_
         if (N > 0) k_init_cells<NC, T><<<G, THREADS, 0, s>>>(ctx->m, ctx->b, d_idx, d_p, N);
     });
     k_set_count<<<1, 1, 0, s>>>(ctx->b.sc, N, step0);
-    with_nt(ctx, [&](auto NN, auto) {
+    with_nt(ctx, [&](auto NN, auto TT) {
         constexpr int NC = decltype(NN)::value;
+        using T = decltype(TT);
+        k_halo<NC, T, 0><<<G, THREADS, 0, s>>>(ctx->m, ctx->b);
         launch_link<NC>(ctx, 0);
     });
     k_finalise<<<1, 1, 0, s>>>(ctx->m, ctx->b.sc, 2);
@@ -776,8 +790,9 @@ static void fill_stats(const gbees_ctx* ctx, gbees_stats* st) {
     st->t = ctx->hs.t;
     st->last_dt = ctx->hs.dt;
     st->total_steps = ctx->hs.step;
-    st->n_cells = ctx->hs.N;
+    st->n_cells = ctx->hs.NA;
     st->norm = ctx->hs.w;
+    st->n_pool = ctx->hs.N;
 }
 
 int gbees_propagate(gbees_ctx* ctx, double t_end, gbees_stats* stats) {
@@ -909,7 +924,7 @@ int gbees_count(gbees_ctx* ctx, int64_t* n_cells) {
     if (st) return st;
     if (!n_cells) return GBEES_EINVAL;
     if (!sync_scalars(ctx, "count")) return ctx->status;
-    *n_cells = ctx->hs.N;
+    *n_cells = ctx->hs.NA;
     return GBEES_OK;
 }
 
@@ -925,7 +940,7 @@ int gbees_read_cells(gbees_ctx* ctx, int32_t* idx, double* p, int64_t cap, int64
     int st = guard(ctx, true);
     if (st) return st;
     if (!sync_scalars(ctx, "read_cells")) return ctx->status;
-    const long long N = ctx->hs.N;
+    const long long N = ctx->hs.NA;
     if (n_cells) *n_cells = N;
     if (N == 0) return GBEES_OK;
     if ((!idx || !p) && cap > 0) return GBEES_EINVAL;
@@ -933,15 +948,10 @@ int gbees_read_cells(gbees_ctx* ctx, int32_t* idx, double* p, int64_t cap, int64
     const int g = ctx->hs.gen;
     int* d_idx = ctx->b.link[g ^ 1];
     double* d_p = reinterpret_cast<double*>(ctx->b.key[g ^ 1]);
-    const int G = ctx->grid;
     cudaStream_t s = ctx->stream;
     {
-        Phase ph(ctx, GBEES_PHASE_OTHER, 1);
-        with_nt(ctx, [&](auto NN, auto TT) {
-            constexpr int NC = decltype(NN)::value;
-            using T = decltype(TT);
-            k_readout<NC, T><<<G, THREADS, 0, s>>>(ctx->m, ctx->b, d_idx, d_p);
-        });
+        Phase ph(ctx, GBEES_PHASE_OTHER, 3);
+        launch_readout(ctx, d_idx, d_p);
     }
     std::vector<int32_t> hidx((size_t)N * n);
     std::vector<double> hp((size_t)N);
@@ -1034,58 +1044,7 @@ cudaError_t noalloc_scratch(void** out) {
 bool noalloc_setup(gbees_ctx* ctx, const gbees_config* cfg, void* base_ptr, cudaStream_t stream) {
     Layout L;
     if (!make_layout(cfg, &L)) return false;
-    ctx->cfg = *cfg;
-    ctx->stream = stream;
-    ctx->status = GBEES_OK;
-    ctx->has_grid = false;
-    Model& m = ctx->m;
-    std::memset(&m, 0, sizeof m);
-    m.n = cfg->n;
-    m.dyn = cfg->dynamics;
-    m.limiter = cfg->limiter;
-    m.key_bits = key_bits_for(cfg->n);
-    m.prune_interval = cfg->prune_interval;
-    m.probe_width = cfg->probe_width ? cfg->probe_width : 1;
-    m.cap = cfg->max_cells;
-    m.tmask = L.slots - 1;
-    std::memcpy(m.a, cfg->params, sizeof m.a);
-    m.prod_h = 1.0;
-    for (int j = 0; j < cfg->n; ++j) {
-        m.h[j] = cfg->h[j];
-        m.x0[j] = cfg->x0[j];
-        m.prod_h *= cfg->h[j];
-    }
-    m.thr_rel = cfg->thr_rel;
-    m.cfl = cfg->cfl;
-    for (int j = 0; j < cfg->n; ++j) {
-        m.inv_h[j] = 1.0 / cfg->h[j];
-        m.inv_2h[j] = 1.0 / (2.0 * cfg->h[j]);
-        m.hf[j] = (float)cfg->h[j];
-        m.x0f[j] = (float)cfg->x0[j];
-    }
-    for (int i = 0; i < 48; ++i) m.af[i] = (float)cfg->params[i];
-    char* base = (char*)base_ptr;
-    Bufs& b = ctx->b;
-    b.sc = (DevScalars*)(base + L.sc);
-    b.blk = (long long*)(base + L.blk);
-    b.part = (Partial*)(base + L.part);
-    for (int g = 0; g < 2; ++g) {
-        b.key[g] = (unsigned long long*)(base + L.key[g]);
-        b.q[g] = (void*)(base + L.q[g]);
-        b.link[g] = (int*)(base + L.link[g]);
-    }
-    for (int g = 0; g < 2; ++g) b.om[g] = (unsigned short*)(base + L.om[g]);
-    for (int g = 0; g < 2; ++g) b.slot[g] = (unsigned int*)(base + L.slot[g]);
-    b.keep = (unsigned char*)(base + L.keep);
-    b.map = (int*)(base + L.map);
-    b.table = (Slot*)(base + L.table);
-    b.wv_u = (double*)(base + L.wv_u);
-    b.wv_g = (double*)(base + L.wv_g);
-    b.fl = (double*)(base + L.fl);
-    b.fu = (double*)(base + L.fu);
-    b.bu = (void*)(base + L.bu);
-    b.bt = (void*)(base + L.bt);
-    b.bp = (void*)(base + L.bp);
+    bind_context(ctx, cfg, L, base_ptr, stream);
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
@@ -1111,18 +1070,14 @@ extern "C" int gbees_propagate_cells_noalloc(const gbees_config* cfg, const int3
     if (st) return st;
     st = gbees_propagate(&ctx, t_end, stats);
     if (st) return st;
-    const long long Nc = ctx.hs.N;
+    const long long Nc = ctx.hs.NA;
     *n_out = Nc;
     if (Nc == 0) return GBEES_OK;
     const int n = cfg->n;
     const int g = ctx.hs.gen;
     int* d_idx = ctx.b.link[g ^ 1];
     double* d_p = reinterpret_cast<double*>(ctx.b.key[g ^ 1]);
-    with_nt(&ctx, [&](auto NN, auto TT) {
-        constexpr int NC = decltype(NN)::value;
-        using T = decltype(TT);
-        k_readout<NC, T><<<ctx.grid, THREADS, 0, ctx.stream>>>(ctx.m, ctx.b, d_idx, d_p);
-    });
+    launch_readout(&ctx, d_idx, d_p);
     const long long w = std::min<long long>(Nc, cap_out);
     if (w > 0) {
         if (cudaMemcpyAsync(idx_out, d_idx, sizeof(int32_t) * n * w, cudaMemcpyDeviceToHost, ctx.stream) != cudaSuccess ||

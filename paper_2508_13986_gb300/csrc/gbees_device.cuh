@@ -45,9 +45,13 @@ struct alignas(16) Slot {
 
 // Scalars that live on the device so that a whole step needs no host round trip.
 struct alignas(256) DevScalars {
-    long long N;          // active cells (grows during grow)
-    long long N_prev;     // cells before the current grow
-    long long N_new;      // cells surviving the current prune
+    long long N;          // pool entries, active cells and halo cells (grows during grow)
+    long long N_prev;     // pool entries before the current grow
+    long long N_new;      // pool entries surviving the current prune
+    long long NA;         // active cells
+    long long NA_new;     // active cells surviving the current prune
+    long long n_halo;     // halo cells appended by the current halo phase
+    long long n_act;      // halo cells made active by the current grow (listed in map)
     double t;             // time
     double t_target;      // end of the current propagate call
     double dt;            // last step
@@ -61,7 +65,7 @@ struct alignas(256) DevScalars {
     long long step;       // steps since init
     long long steps_call; // steps of the current propagate call
     long long updates_call;  // cell updates of the current propagate call
-    long long lookups_fallback;  // edge/second-neighbour lookups that needed the hashtable
+    long long lookups_fallback;  // hashtable lookups of the flux update (none: every stencil cell is linked)
     int pbuf;             // current Q buffer
     int gen;              // current key/link buffer
     int done;             // t reached t_target
@@ -129,19 +133,23 @@ struct alignas(64) Partial {
     unsigned long long rate_bits;  // the block's maximum CFL rate (non-negative double bits)
 };
 
-// Device buffers (by value). link[g] holds 2n arrays of cap int32: entry
-// (2j + s) * cap + c is the index of the neighbour of cell c one step down
-// (s = 0) or up (s = 1) in dimension j, or -1.
+// Device buffers (by value). The pool holds the active cells and their halo:
+// every face neighbour of an active cell that is not active itself is kept as
+// a halo cell (p = 0, never updated, never counted), so that all cells of the
+// update stencil (face neighbours, their face neighbours, the second
+// neighbours) are reached through links. link[g] holds 2n arrays of cap int32:
+// entry (2j + s) * cap + c is the index of the neighbour of entry c one step
+// down (s = 0) or up (s = 1) in dimension j, or -1 when it is not in the pool.
 //
 // om[g][c]: bits 0..2n-1 are the outward directions of cell c (bit 2j+1: the
 // flow leaves through the upper j-face, bit 2j: through the lower j-face),
-// fixed at creation because the drift does not depend on time; bit 15 marks a
-// cell whose downwind set is known to be present (cleared by every prune).
+// fixed at creation because the drift does not depend on time; bit 14 marks a
+// halo cell; bit 15 marks an active cell whose downwind set is known to be
+// active (cleared by every prune).
 //
 // FP64 update scratch (n arrays of cap doubles each): wv_u[j] lower-face
 // velocity, wv_g[d] d-direction wave entering the cell, fl[j] flux through the
-// lower j-face, fu[j] flux through the upper j-face of cells whose upper
-// neighbour is missing.
+// lower j-face.
 struct Bufs {
     unsigned long long* key[2];
     void* q[2];
@@ -149,26 +157,19 @@ struct Bufs {
     unsigned short* om[2];
     unsigned int* slot[2];  // hashtable slot of each cell
     unsigned char* keep;
-    int* map;
+    int* map;        // prune: status, then new index; grow: the halo cells it activated
     Slot* table;
     DevScalars* sc;
-    long long* blk;
+    long long* blk;  // per-block counts (active cells)
+    long long* blk2; // per-block counts (halo cells)
     double* wv_u;
     double* wv_g;
     double* fl;
-    double* fu;
-    // Boundary faces (2n arrays of cap values of the storage type, entry
-    // f * cap + c for face f = 2j + s of cell c whose neighbour across it is
-    // missing), filled before grow: bu = velocity at the face; when the missing
-    // neighbour is upwind, bt = sum_{d != j} G_d(neighbour) / (2 h_d) (times dt
-    // later) and bp = the value two cells away across the face (limiter).
-    void* bu;
-    void* bt;
-    void* bp;
     Partial* part;   // GRID_MAX per-block partials
 };
 
 constexpr unsigned short OM_COMPLETE = 0x8000;
+constexpr unsigned short OM_GHOST = 0x4000;
 
 // The kernels of one time step for one model and precision: those before the
 // link phase, those after it, and the persistent step-loop kernel.

@@ -30,7 +30,7 @@ __device__ __forceinline__ void finish_link(const Model& m, DevScalars* sc, cons
     sc->ticket = 0;
 }
 
-// Link cells [N_prev, N) (neighbour references of Sec. 4.1), set their outward
+// Link entries [N_prev, N) (neighbour references of Sec. 4.1), set their outward
 // masks and rates; with step != 0 the last block also fixes dt (Eq. 8).
 // W lanes probe the hashtable together (warp-cooperative probing).
 template <int N, int W>
@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(THREADS) k_init_write(const Model m, Bufs b, c
             unsigned long long k;
             if (c >= m.cap) {
                 set_error(sc, ST_ECAPACITY);
-            } else if (!pack_key<N>(m, I, k)) {
+            } else if (!interior<N>(m, I) || !pack_key<N>(m, I, k)) {
                 set_error(sc, ST_EKEYRANGE);
             } else {
                 T v = (T)g;
@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(THREADS) k_init_cells(const Model m, Bufs b, c
 #pragma unroll
         for (int k = 0; k < N; ++k) I[k] = idx[c * N + k];
         unsigned long long k;
-        if (!pack_key<N>(m, I, k)) {
+        if (!interior<N>(m, I) || !pack_key<N>(m, I, k)) {
             set_error(sc, ST_EKEYRANGE);
             continue;
         }
@@ -202,23 +202,50 @@ __global__ void __launch_bounds__(THREADS) k_init_cells(const Model m, Bufs b, c
 
 // ------------------------------------------------------------------ grow
 
+// The CFL rates of the halo cells that grow made active join the running maximum.
+__device__ __forceinline__ void grow_rates(DevScalars* sc, double r) {
+    r = block_max(r);
+    if (threadIdx.x == 0 && r > 0.0) atomicMax(&sc->maxrate_bits, (unsigned long long)__double_as_longlong(r));
+}
+
 template <int N, typename T>
 __global__ void __launch_bounds__(THREADS) k_grow(const Model m, Bufs b) {
     DevScalars* sc = b.sc;
     if (*(volatile int*)&sc->done | *(volatile int*)&sc->error) return;
-    grow_body<N, T>(m, b, view_of(m, sc));
+    grow_rates(sc, grow_body<N, T>(m, b, view_of(m, sc)));
+}
+
+// Halo cells around the cells that grow made active (inserted ones: [N_prev, N)
+// at entry; activated ones: the n_act entries listed in map). With STEP == 0
+// (initial grid) it runs whatever the done flag says. The last block appends
+// the new halo cells to the count.
+template <int N, typename T, int STEP>
+__global__ void __launch_bounds__(THREADS) k_halo(const Model m, Bufs b) {
+    DevScalars* sc = b.sc;
+    if (*(volatile int*)&sc->error) return;
+    if (STEP && *(volatile int*)&sc->done) return;
+    const StepView v = view_of(m, sc);
+    halo_body<N, T>(m, b, v, v.N_prev, v.N, *(volatile long long*)&sc->n_act);
+    if (last_block(sc)) {
+        if (threadIdx.x == 0) {
+            sc->N = min(sc->N + sc->n_halo, m.cap);
+            sc->n_halo = 0;
+            sc->n_act = 0;
+            sc->ticket = 0;
+        }
+    }
 }
 
 // ------------------------------------------------------------------ step completion
 
 // Time, step count, buffers, prune schedule and normalisation after the flux
 // update of a step, from the combined partials of the update's blocks.
-__device__ __forceinline__ void finish_step(const Model& m, DevScalars* sc, const Combined& cs, long long ncell, int pb) {
+__device__ __forceinline__ void finish_step(const Model& m, DevScalars* sc, const Combined& cs, int pb) {
     sc->dt = sc->step_dt;
     sc->t = sc->step_t_new;
     sc->step += 1;
     sc->steps_call += 1;
-    sc->updates_call += ncell;
+    sc->updates_call += sc->NA;
     sc->done = sc->step_last;
     sc->pbuf = pb ^ 1;
     sc->prune_now = (m.prune_interval > 0 && (sc->step % m.prune_interval) == 0);
@@ -235,34 +262,24 @@ __device__ __forceinline__ void finish_step(const Model& m, DevScalars* sc, cons
     sc->ticket = 0;
 }
 
-// FP64 step, first phase: grow, and the waves and boundary faces of the cells
-// that existed before it.
+// FP64 step, first phase: grow, and the waves of the entries that existed
+// before it (a cell that grow or halo adds has p = 0, like a missing one, so
+// the waves of the old entries do not change).
 template <int N, int DYN>
 __global__ void __launch_bounds__(THREADS) k_grow_waves(const Model m, Bufs b) {
     DevScalars* sc = b.sc;
     if (*(volatile int*)&sc->done | *(volatile int*)&sc->error) return;
     const StepView v = view_of(m, sc);
-    grow_body<N, double>(m, b, v);
+    const double r = grow_body<N, double>(m, b, v);
     waves_body<N, DYN>(m, b, v, v.N_prev);
-    boundary_body<N, DYN, double>(m, b, v, v.N_prev);
-}
-
-// Single-pass step, first phase: grow and the boundary faces of the old cells.
-template <int N, int DYN, typename T>
-__global__ void __launch_bounds__(THREADS) k_grow_boundary(const Model m, Bufs b) {
-    DevScalars* sc = b.sc;
-    if (*(volatile int*)&sc->done | *(volatile int*)&sc->error) return;
-    const StepView v = view_of(m, sc);
-    grow_body<N, T>(m, b, v);
-    boundary_body<N, DYN, T>(m, b, v, v.N_prev);
+    grow_rates(sc, r);
 }
 
 template <int N, int DYN>
 __global__ void __launch_bounds__(THREADS) k_faces(const Model m, Bufs b) {
     DevScalars* sc = b.sc;
     if (*(volatile int*)&sc->done | *(volatile int*)&sc->error) return;
-    long long fb = faces_body<N, DYN>(m, b, view_of(m, sc));
-    if (fb) atomicAdd((unsigned long long*)&sc->lookups_fallback, (unsigned long long)fb);
+    faces_body<N, DYN>(m, b, view_of(m, sc));
 }
 
 template <int N>
@@ -278,7 +295,7 @@ __global__ void __launch_bounds__(THREADS) k_apply(const Model m, Bufs b) {
     block_partial(b.part, d, mx, 0.0);
     if (last_block(sc)) {
         Combined cs = combine_partials(b.part, gridDim.x);
-        if (threadIdx.x == 0) finish_step(m, sc, cs, v.N, v.pb);
+        if (threadIdx.x == 0) finish_step(m, sc, cs, v.pb);
     }
 }
 
@@ -290,13 +307,12 @@ __global__ void __launch_bounds__(THREADS) k_ctu(const Model m, Bufs b) {
     long long d[NDIG] = {0, 0, 0, 0, 0, 0};
     double mx = -INFINITY;
     int err = 0;
-    long long fb = gather_faces_body<N, DYN, T>(m, b, v, d, mx, err);
+    gather_faces_body<N, DYN, T>(m, b, v, d, mx, err);
     if (err) set_error(sc, ST_EDEGENERATE);
-    if (fb) atomicAdd((unsigned long long*)&sc->lookups_fallback, (unsigned long long)fb);
     block_partial(b.part, d, mx, 0.0);
     if (last_block(sc)) {
         Combined cs = combine_partials(b.part, gridDim.x);
-        if (threadIdx.x == 0) finish_step(m, sc, cs, v.N, v.pb);
+        if (threadIdx.x == 0) finish_step(m, sc, cs, v.pb);
     }
 }
 
@@ -365,18 +381,26 @@ __global__ void __launch_bounds__(THREADS) k_prune_scatter(const Model m, Bufs b
     prune_scatter_body<N, T>(m, b, view_of(m, b.sc));
 }
 
+template <int N>
+__global__ void __launch_bounds__(THREADS) k_prune_count(const Model m, Bufs b) {
+    if (!prune_due(b.sc)) return;
+    prune_count_body<N>(m, b, view_of(m, b.sc));
+}
+
 template <int N, typename T>
 __global__ void __launch_bounds__(THREADS) k_prune_compact(const Model m, Bufs b) {
     DevScalars* sc = b.sc;
     if (!prune_due(sc)) return;
     const StepView v = view_of(m, sc);
-    long long base, total;
-    block_offset_total(b, base, total);
-    if (blockIdx.x == 0 && threadIdx.x == 0) sc->N_new = total;
+    const Survivors sv = block_offsets(b);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        sc->N_new = sv.total_a + sv.total_g;
+        sc->NA_new = sv.total_a;
+    }
     long long d[NDIG] = {0, 0, 0, 0, 0, 0};
     double mx = -INFINITY, rmax = 0.0;
     int err = 0;
-    prune_compact_body<N, T>(m, b, v, base, d, mx, rmax, err);
+    prune_compact_body<N, T>(m, b, v, sv, d, mx, rmax, err);
     if (err) set_error(sc, ST_EDEGENERATE);
     block_partial(b.part, d, mx, rmax);
 }
@@ -386,6 +410,7 @@ __global__ void __launch_bounds__(THREADS) k_prune_compact(const Model m, Bufs b
 __device__ __forceinline__ void finish_prune(const Model& m, DevScalars* sc, const Combined& cp, long long n_new) {
     sc->N = n_new;
     sc->N_prev = n_new;
+    sc->NA = sc->NA_new;
     sc->gen ^= 1;
     sc->pbuf ^= 1;
     sc->maxrate_bits = cp.rate_bits;
@@ -415,6 +440,9 @@ __global__ void __launch_bounds__(THREADS) k_prune_relink(const Model m, Bufs b,
 
 // ------------------------------------------------------------------ read-out
 
+// Read-out of the active cells in storage order: per-block counts
+// (k_readout_count), an exclusive scan of them (k_scan_blocks), then every
+// block writes its active cells at its offset.
 template <int N, typename T>
 __global__ void __launch_bounds__(THREADS) k_readout(const Model m, Bufs b, int* __restrict__ idx,
                                                      double* __restrict__ p) {
@@ -422,14 +450,25 @@ __global__ void __launch_bounds__(THREADS) k_readout(const Model m, Bufs b, int*
     const long long ncell = min(*(volatile long long*)&sc->N, m.cap);
     const int g = *(volatile int*)&sc->gen, pb = *(volatile int*)&sc->pbuf;
     const T* Q = static_cast<const T*>(b.q[pb]);
+    const unsigned short* om = b.om[g];
     const double w = *(volatile double*)&sc->w;
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
-         c += (long long)gridDim.x * blockDim.x) {
-        int I[N];
-        unpack_key<N>(m, b.key[g][c], I);
+    long long c0, c1;
+    block_chunk(ncell, c0, c1);
+    long long base = b.blk[blockIdx.x];
+    for (long long t0 = c0; t0 < c1; t0 += blockDim.x) {
+        const long long c = t0 + threadIdx.x;
+        const int f = c < c1 && !is_halo(om, c);
+        int total;
+        const int pos = block_exclusive_scan(f, total);
+        if (f) {
+            const long long r = base + pos;
+            int I[N];
+            unpack_key<N>(m, b.key[g][c], I);
 #pragma unroll
-        for (int k = 0; k < N; ++k) idx[c * N + k] = I[k];
-        p[c] = __ddiv_rn((double)Q[c], w);
+            for (int k = 0; k < N; ++k) idx[r * N + k] = I[k];
+            p[r] = __ddiv_rn((double)Q[c], w);
+        }
+        base += total;
     }
 }
 

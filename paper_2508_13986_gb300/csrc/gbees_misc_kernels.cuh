@@ -79,6 +79,10 @@ __global__ void k_reset(DevScalars* sc, double t0) {
     sc->N = 0;
     sc->N_prev = 0;
     sc->N_new = 0;
+    sc->NA = 0;
+    sc->NA_new = 0;
+    sc->n_halo = 0;
+    sc->n_act = 0;
     sc->t = t0;
     sc->t_target = t0;
     sc->dt = 0.0;
@@ -108,20 +112,34 @@ __global__ void k_reset(DevScalars* sc, double t0) {
     sc->phase_steps = 0;
 }
 
+// Initial grid: the active cells written so far are the whole pool; the halo
+// kernel adds their halo next.
 __global__ void k_set_count_from_new(DevScalars* sc) {
     sc->N = sc->N_new;
+    sc->NA = sc->N_new;
     sc->N_prev = 0;
+    sc->n_act = 0;
 }
 
 __global__ void k_set_count(DevScalars* sc, long long count, long long step0) {
     sc->N = count;
+    sc->NA = count;
     sc->N_prev = 0;
+    sc->n_act = 0;
     sc->step = step0;
 }
 
-__global__ void __launch_bounds__(THREADS) k_prune_count(const Model m, Bufs b) {
-    if (!prune_due(b.sc)) return;
-    prune_count_body(m, b, view_of(m, b.sc));
+// Per-block counts of the active cells (read-out, first pass).
+__global__ void __launch_bounds__(THREADS) k_readout_count(const Model m, Bufs b) {
+    DevScalars* sc = b.sc;
+    const long long ncell = min(*(volatile long long*)&sc->N, m.cap);
+    const unsigned short* om = b.om[*(volatile int*)&sc->gen];
+    long long c0, c1;
+    block_chunk(ncell, c0, c1);
+    int cnt = 0;
+    for (long long c = c0 + threadIdx.x; c < c1; c += blockDim.x) cnt += !is_halo(om, c);
+    const long long t = block_count(cnt);
+    if (threadIdx.x == 0) b.blk[blockIdx.x] = t;
 }
 
 __global__ void k_moments_clear(DevScalars* sc) {

@@ -8,8 +8,8 @@
 // step's scalars (dt, normalisation, maximum) itself from the same per-block
 // partials, so the scalars need no extra barrier; block 0 writes them back.
 //
-// Barriers per step: grow (+ boundary faces, FP64: + waves) | link | (FP64:
-// faces |) update; a prune adds mark | scatter | count | compact | relink.
+// Barriers per step: grow (FP64: + waves) | halo | link | (FP64: faces |)
+// update; a prune adds mark | scatter | status | compact | relink.
 #pragma once
 
 #include "gbees_kernels.cuh"
@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_persistent(const Model m, Bufs b
     unsigned long long maxrate = *(volatile unsigned long long*)&sc->maxrate_bits;
     double w = *(volatile double*)&sc->w;
     double last_dt = *(volatile double*)&sc->dt;
-    long long nsteps = 0, nupd = 0, fb = 0;
+    long long nsteps = 0, nupd = 0;
     // every block has read the state before anyone changes it
     if (done || *(volatile int*)&sc->error || !grid_barrier(sc)) return;
     // phase timing by block 0 (cycles between the barriers it passes)
@@ -61,21 +61,33 @@ __global__ void __launch_bounds__(THREADS, 1) k_persistent(const Model m, Bufs b
     };
 
     for (long long it = 0; it < max_steps && !done; ++it) {
-        // grow (appends to sc->N); FP64: the waves of the existing cells alongside
-        grow_body<N, T>(m, b, v);
+        // grow (appends active cells to sc->N, activates halo cells); FP64: the
+        // waves of the existing entries alongside
+        const double rg = grow_body<N, T>(m, b, v);
         if constexpr (sizeof(T) == 8) waves_body<N, DYN>(m, b, v, v.N_prev);
-        boundary_body<N, DYN, T>(m, b, v, v.N_prev);
         if (!grid_barrier(sc)) return;
         mark(0);
-        v.N = min(*(volatile long long*)&sc->N, m.cap);
-        // link the new cells; their CFL rates
+        // halo cells around the newly active cells (appended after sc->N, which
+        // stays put until the link phase)
+        const long long n_ins = min(*(volatile long long*)&sc->N, m.cap);
+        const long long n_active = *(volatile long long*)&sc->NA;
+        halo_body<N, T>(m, b, v, v.N_prev, n_ins, *(volatile long long*)&sc->n_act);
+        if (!grid_barrier(sc)) return;
+        v.N = min(n_ins + *(volatile long long*)&sc->n_halo, m.cap);
+        // link the new entries; CFL rates of the new active cells
         {
-            const double r = link_body<N>(m, b, v.N_prev, v.N, v.g);
+            const double r = fmax(rg, link_body<N>(m, b, v.N_prev, v.N, v.g));
             long long zero[NDIG] = {0, 0, 0, 0, 0, 0};
             block_partial(b.part, zero, -INFINITY, r);
         }
+        if (blockIdx.x == 0 && threadIdx.x == 0) sc->N = v.N;  // read again only after the next grow
         if (!grid_barrier(sc)) return;
         mark(1);
+        // everyone has read the halo and activation counts: reset them
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            sc->n_halo = 0;
+            sc->n_act = 0;
+        }
         {
             Combined cr = combine_partials(b.part, gridDim.x);
             maxrate = max(maxrate, cr.rate_bits);
@@ -108,12 +120,12 @@ __global__ void __launch_bounds__(THREADS, 1) k_persistent(const Model m, Bufs b
         double mx = -INFINITY;
         int err = 0;
         if constexpr (sizeof(T) == 8) {
-            fb += faces_body<N, DYN>(m, b, v);
+            faces_body<N, DYN>(m, b, v);
             if (!grid_barrier(sc)) return;
             mark(2);
             apply_body<N>(m, b, v, d, mx, err);
         } else {
-            fb += gather_faces_body<N, DYN, T>(m, b, v, d, mx, err);
+            gather_faces_body<N, DYN, T>(m, b, v, d, mx, err);
         }
         if (err) set_error(sc, ST_EDEGENERATE);
         block_partial(b.part, d, mx, 0.0);
@@ -138,7 +150,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_persistent(const Model m, Bufs b
         done = st.last;
         step += 1;
         nsteps += 1;
-        nupd += v.N;
+        nupd += n_active;
         v.pb ^= 1;
         v.N_prev = v.N;
         mark(5);
@@ -148,16 +160,19 @@ __global__ void __launch_bounds__(THREADS, 1) k_persistent(const Model m, Bufs b
             if (!grid_barrier(sc)) return;
             prune_scatter_body<N, T>(m, b, v);
             if (!grid_barrier(sc)) return;
-            prune_count_body(m, b, v);
+            prune_count_body<N>(m, b, v);
             if (!grid_barrier(sc)) return;
-            long long base, total;
-            block_offset_total(b, base, total);
-            if (blockIdx.x == 0 && threadIdx.x == 0) sc->N = total;  // before the next grow appends
+            const Survivors sv = block_offsets(b);
+            const long long total = sv.total_a + sv.total_g;
+            if (blockIdx.x == 0 && threadIdx.x == 0) {  // before the next grow appends
+                sc->N = total;
+                sc->NA = sv.total_a;
+            }
             {
                 long long dp[NDIG] = {0, 0, 0, 0, 0, 0};
                 double mxp = -INFINITY, rmax = 0.0;
                 int errp = 0;
-                prune_compact_body<N, T>(m, b, v, base, dp, mxp, rmax, errp);
+                prune_compact_body<N, T>(m, b, v, sv, dp, mxp, rmax, errp);
                 if (errp) set_error(sc, ST_EDEGENERATE);
                 block_partial(b.part, dp, mxp, rmax);
             }
@@ -170,7 +185,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_persistent(const Model m, Bufs b
             w = ss.w;
             v.scale = ss.scale;
             v.maxq = ss.maxq;
-            const int bad = ss.bad || total == 0;
+            const int bad = ss.bad || sv.total_a == 0;
             __syncthreads();
             if (bad) {
                 set_error(sc, ST_EDEGENERATE);
@@ -201,7 +216,6 @@ __global__ void __launch_bounds__(THREADS, 1) k_persistent(const Model m, Bufs b
         sc->updates_call += nupd;
         sc->prune_now = 0;
     }
-    if (fb) atomicAdd((unsigned long long*)&sc->lookups_fallback, (unsigned long long)fb);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         for (int q = 0; q < 8; ++q) sc->phase_cycles[q] += pc[q];
         sc->phase_steps += nsteps;

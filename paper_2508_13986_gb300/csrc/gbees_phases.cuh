@@ -6,12 +6,18 @@
 // grid barrier's fences make plain loads see the other blocks' writes.
 //
 //   grow       directional grow of the significant cells (Sec. 3.3, Algorithm 2)
-//   link       neighbour links, outward mask and CFL rate of the new cells (Sec. 4.1)
-//   waves      FP64: per-cell velocities u_d and entering waves G_d
+//   halo       the missing face neighbours of the newly active cells, as halo cells
+//   link       neighbour links, outward mask and CFL rate of the new entries (Sec. 4.1)
+//   waves      FP64: per-entry velocities u_d and entering waves G_d
 //   faces      FP64: one flux per face (Eq. 7 + Algorithm 1 gathered + HR term)
 //   apply      FP64: P -= sum_j dt/h_j (F_hi - F_lo), normalised, reduced
 //   gather     single-pass update (any precision), normalised, reduced
-//   prune      mark S, mark D(S), count, compact, relink and rehash (Algorithm 3)
+//   prune      mark S, mark D(S), status, compact, relink and rehash (Algorithm 3)
+//
+// The pool holds the active cells and, as halo cells with p = 0, every face
+// neighbour of an active cell that is not active (a missing cell of the method:
+// p = 0, not updated). With links between all pool entries, every cell of the
+// update stencil is reached through links and the update needs no hashtable.
 #pragma once
 
 #include "gbees_device.cuh"
@@ -20,8 +26,8 @@ namespace gbees {
 
 // What a phase needs to know about the step in progress.
 struct StepView {
-    long long N;       // active cells (clamped to the capacity)
-    long long N_prev;  // cells before this step's grow
+    long long N;       // pool entries (clamped to the capacity)
+    long long N_prev;  // pool entries before this step's grow
     int pb, g;         // current value buffer and key/link buffer
     double maxq;       // max stored value (threshold p* = thr_rel * maxq)
     double scale;      // 1 / w of the previous normalisation
@@ -86,8 +92,9 @@ __device__ __forceinline__ unsigned outward_mask(const Model& m, const int* I) {
     return msk;
 }
 
-// Index of cell c + s1 e_j + s2 e_d (j != d) through the links, -2 when both
-// intermediate cells are missing (the links cannot tell).
+// Index of cell c + s1 e_j + s2 e_d (j != d) through the links, -1 when it is
+// not in the pool. For an active cell c the face neighbour c + s1 e_j is in the
+// pool, so its link decides; -2 only when both intermediate cells are missing.
 __device__ __forceinline__ int edge_by_links(const int* link, long long cap, const int* L, int j, int s1,
                                              int d, int s2) {
     int a = L[2 * j + s1];
@@ -115,39 +122,74 @@ __device__ __forceinline__ void table_insert_new(const Model& m, const Bufs& b, 
 
 // ------------------------------------------------------------------ grow
 
-// Claim cell I if absent and append it with p = 0 (its links, outward mask and
-// rate are set by the link phase).
+// Entry e is a halo cell: make it active. True for the one thread that does.
+__device__ __forceinline__ bool activate(unsigned short* om, long long e) {
+    unsigned short old = *(volatile unsigned short*)&om[e];
+    while (old & OM_GHOST) {
+        const unsigned short prev = atomicCAS(&om[e], old, (unsigned short)(old & ~OM_GHOST));
+        if (prev == old) return true;
+        old = prev;
+    }
+    return false;
+}
+
+// Active cells keep one layer away from the edge of the key range, so that
+// their face neighbours (halo cells) have keys.
+template <int N>
+__device__ __forceinline__ bool interior(const Model& m, const int* I) {
+    const long long bias = 1ll << (m.key_bits - 1);
+    const long long top = (1ll << m.key_bits) - 2;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        const long long u = (long long)I[k] + bias;
+        if (u < 1 || u > top) return false;
+    }
+    return true;
+}
+
+// Claim the key of cell I and append it to the pool at base + (*counter)++
+// with p = 0 and the given flags. Returns the new index, or -1 when the key is
+// present already (or on an error, which is recorded).
 template <int N, typename T>
-__device__ __forceinline__ void grow_insert(const Model& m, const Bufs& b, int g, int pb, const int* I) {
+__device__ __forceinline__ long long insert_cell(const Model& m, const Bufs& b, const StepView& v, const int* I,
+                                                 unsigned short flags, long long* counter, long long base) {
     DevScalars* sc = b.sc;
     unsigned long long k;
     if (!pack_key<N>(m, I, k)) {
         set_error(sc, ST_EKEYRANGE);
-        return;
+        return -1;
     }
     unsigned long long slot;
-    int r = table_claim(m, b.table, k, &slot);
+    const int r = table_claim(m, b.table, k, &slot);
     if (r < 0) {
         set_error(sc, ST_ETABLE);
-        return;
+        return -1;
     }
-    if (r == 0) return;
-    long long c = warp_aggregated_add(&sc->N);
+    if (r == 0) return -1;
+    const long long c = base + warp_aggregated_add(counter);
     if (c >= m.cap) {
         set_error(sc, ST_ECAPACITY);
-        return;
+        return -1;
     }
     b.table[slot].val = c;
-    b.slot[g][c] = (unsigned int)slot;
-    b.key[g][c] = k;
-    static_cast<T*>(b.q[pb])[c] = (T)0;
+    b.slot[v.g][c] = (unsigned int)slot;
+    b.key[v.g][c] = k;
+    static_cast<T*>(b.q[v.pb])[c] = (T)0;
+    b.om[v.g][c] = flags;
+    return c;
 }
 
-// Directional grow (Sec. 3.3): every significant cell inserts the missing cells
-// of its downwind set. A cell whose downwind set was found complete since the
-// last prune is skipped.
+// Directional grow (Sec. 3.3): every significant cell makes its downwind set
+// active. A face neighbour of an active cell is always in the pool; an edge
+// neighbour c + s1 e_j + s2 e_l is found through the link of the face
+// neighbour c + s1 e_j. A halo cell found there becomes active (listed in map
+// for the halo phase); a missing one is inserted as active. A cell whose
+// downwind set was made active since the last prune is skipped. Returns the
+// largest CFL rate of the halo cells this thread activated (inserted cells get
+// theirs in the link phase).
 template <int N, typename T>
-__device__ __forceinline__ void grow_body(const Model& m, const Bufs& b, const StepView& v) {
+__device__ __forceinline__ double grow_body(const Model& m, const Bufs& b, const StepView& v) {
+    DevScalars* sc = b.sc;
     const long long ncell = v.N_prev;
     const double pstar = m.thr_rel * v.maxq;
     const T* Q = static_cast<const T*>(b.q[v.pb]);
@@ -155,12 +197,28 @@ __device__ __forceinline__ void grow_body(const Model& m, const Bufs& b, const S
     const int* link = b.link[v.g];
     unsigned short* om = b.om[v.g];
     const long long cap = m.cap;
+    double rmax = 0.0;
+    auto make_active = [&](long long e) {
+        if (!(om[e] & OM_GHOST) || !activate(om, e)) return;
+        warp_aggregated_add(&sc->NA);
+        b.map[warp_aggregated_add(&sc->n_act)] = (int)e;
+        int J[N];
+        unpack_key<N>(m, key[e], J);
+        rmax = fmax(rmax, cfl_rate64<N>(m, J));
+    };
+    auto insert_active = [&](const int* J) {
+        if (!interior<N>(m, J)) {
+            set_error(sc, ST_EKEYRANGE);
+            return;
+        }
+        if (insert_cell<N, T>(m, b, v, J, 0, &sc->N, 0) >= 0) warp_aggregated_add(&sc->NA);
+    };
     for (WarpRuns r(ncell); r.next();) {
         const long long c = r.c;
         if (c >= ncell) continue;
         if (!((double)Q[c] > pstar)) continue;
         const unsigned f = om[c];
-        if (f & OM_COMPLETE) continue;
+        if (f & (OM_COMPLETE | OM_GHOST)) continue;
         const unsigned out = f & 0xfffu;
         if (out) {
             int I[N];
@@ -170,12 +228,16 @@ __device__ __forceinline__ void grow_body(const Model& m, const Bufs& b, const S
             for (int d = 0; d < 2 * N; ++d) L[d] = link[(long long)d * cap + c];
 #pragma unroll
             for (int d = 0; d < 2 * N; ++d) {
-                if (!((out >> d) & 1u) || L[d] >= 0) continue;
-                int J[N];
+                if (!((out >> d) & 1u)) continue;
+                if (L[d] >= 0) {
+                    make_active(L[d]);
+                } else {
+                    int J[N];
 #pragma unroll
-                for (int k = 0; k < N; ++k) J[k] = I[k];
-                J[d >> 1] += (d & 1) ? 1 : -1;
-                grow_insert<N, T>(m, b, v.g, v.pb, J);
+                    for (int k = 0; k < N; ++k) J[k] = I[k];
+                    J[d >> 1] += (d & 1) ? 1 : -1;
+                    insert_active(J);
+                }
             }
 #pragma unroll
             for (int d1 = 0; d1 < 2 * N; ++d1) {
@@ -183,26 +245,83 @@ __device__ __forceinline__ void grow_body(const Model& m, const Bufs& b, const S
 #pragma unroll
                 for (int d2 = 0; d2 < 2 * N; ++d2) {
                     if ((d2 >> 1) <= (d1 >> 1) || !((out >> d2) & 1u)) continue;
-                    int e = edge_by_links(link, cap, L, d1 >> 1, d1 & 1, d2 >> 1, d2 & 1);
-                    if (e >= 0) continue;
-                    int J[N];
+                    const int e = edge_by_links(link, cap, L, d1 >> 1, d1 & 1, d2 >> 1, d2 & 1);
+                    if (e >= 0) {
+                        make_active(e);
+                    } else {
+                        int J[N];
 #pragma unroll
-                    for (int k = 0; k < N; ++k) J[k] = I[k];
-                    J[d1 >> 1] += (d1 & 1) ? 1 : -1;
-                    J[d2 >> 1] += (d2 & 1) ? 1 : -1;
-                    grow_insert<N, T>(m, b, v.g, v.pb, J);
+                        for (int k = 0; k < N; ++k) J[k] = I[k];
+                        J[d1 >> 1] += (d1 & 1) ? 1 : -1;
+                        J[d2 >> 1] += (d2 & 1) ? 1 : -1;
+                        insert_active(J);
+                    }
                 }
             }
         }
         om[c] = (unsigned short)(f | OM_COMPLETE);
     }
+    return rmax;
+}
+
+// ------------------------------------------------------------------ halo
+
+// The face neighbours of the cells made active by this step's grow that are
+// not in the pool are appended as halo cells at base + n_halo. Work items
+// (cell, face) over the inserted cells [lo, hi), which have no links yet (each
+// neighbour is claimed, the claim finds the present ones), and over the nact
+// activated halo cells listed in map (only their neighbours without a link).
+template <int N, typename T>
+__device__ __forceinline__ void halo_body(const Model& m, const Bufs& b, const StepView& v, long long lo, long long hi,
+                                          long long nact) {
+    const unsigned long long* key = b.key[v.g];
+    const int* link = b.link[v.g];
+    const long long cap = m.cap;
+    const long long ni = hi - lo;
+    const long long items = (ni + nact) * 2 * N;
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nth = (long long)gridDim.x * blockDim.x;
+    for (long long it = tid; it < items; it += nth) {
+        const long long q = it / (2 * N);
+        const int d = (int)(it - q * 2 * N);
+        long long x;
+        if (q < ni) {
+            x = lo + q;
+        } else {
+            x = b.map[q - ni];
+            if (link[(long long)d * cap + x] >= 0) continue;
+        }
+        int I[N];
+        unpack_key<N>(m, key[x], I);
+        I[d >> 1] += (d & 1) ? 1 : -1;
+        insert_cell<N, T>(m, b, v, I, OM_GHOST, &b.sc->n_halo, hi);
+    }
 }
 
 // ------------------------------------------------------------------ link
 
-// Cells [lo, hi) are new: look up their 2n face neighbours (one probe per
+// Outward masks of the new entries [lo, hi) (added to the flags their inserter
+// wrote) and the largest CFL rate among the active ones.
+template <int N>
+__device__ __forceinline__ double link_masks(const Model& m, const Bufs& b, long long lo, long long hi, int g) {
+    const unsigned long long* key = b.key[g];
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nth = (long long)gridDim.x * blockDim.x;
+    double rmax = 0.0;
+    for (long long c = lo + tid; c < hi; c += nth) {
+        int I[N];
+        unpack_key<N>(m, key[c], I);
+        const unsigned short f = b.om[g][c];
+        b.om[g][c] = (unsigned short)(f | outward_mask<N>(m, I));
+        if (!(f & OM_GHOST)) rmax = fmax(rmax, cfl_rate64<N>(m, I));
+    }
+    return rmax;
+}
+
+// Entries [lo, hi) are new: look up their 2n face neighbours (one probe per
 // thread and direction), write the reverse links into the neighbours, and set
-// their outward masks; returns this thread's largest CFL rate among them.
+// their outward masks; returns this thread's largest CFL rate among the active
+// ones.
 template <int N>
 __device__ __forceinline__ double link_body(const Model& m, const Bufs& b, long long lo, long long hi, int g) {
     const unsigned long long* key = b.key[g];
@@ -223,14 +342,7 @@ __device__ __forceinline__ double link_body(const Model& m, const Bufs& b, long 
         link[(long long)dir * cap + c] = nb;
         if (nb >= 0) link[(long long)(2 * j + (1 - s)) * cap + nb] = (int)c;
     }
-    double rmax = 0.0;
-    for (long long c = lo + tid; c < hi; c += nth) {
-        int I[N];
-        unpack_key<N>(m, key[c], I);
-        b.om[g][c] = (unsigned short)outward_mask<N>(m, I);
-        rmax = fmax(rmax, cfl_rate64<N>(m, I));
-    }
-    return rmax;
+    return link_masks<N>(m, b, lo, hi, g);
 }
 
 // Cooperative variant: W lanes probe W consecutive slots together.
@@ -257,80 +369,22 @@ __device__ __forceinline__ double link_body_tile(const Model& m, const Bufs& b, 
             if (nb >= 0) link[(long long)(2 * j + (1 - s)) * cap + nb] = (int)c;
         }
     }
-    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long nth = (long long)gridDim.x * blockDim.x;
-    double rmax = 0.0;
-    for (long long c = lo + tid; c < hi; c += nth) {
-        int I[N];
-        unpack_key<N>(m, key[c], I);
-        b.om[g][c] = (unsigned short)outward_mask<N>(m, I);
-        rmax = fmax(rmax, cfl_rate64<N>(m, I));
-    }
-    return rmax;
+    return link_masks<N>(m, b, lo, hi, g);
 }
 
 // ------------------------------------------------------------------ FP64 three-pass update
-
-// Index of c + s1 e_j + s2 e_d (j != d, s = 0 down, 1 up) through the links,
-// falling back to the hashtable when both intermediate cells are missing.
-template <int N>
-__device__ __forceinline__ int edge_index(const Model& m, const Bufs& b, const int* link, long long cap,
-                                          const int* L, const int* I, int j, int s1, int d, int s2, long long& fb) {
-    int a = L[2 * j + s1];
-    if (a >= 0) return __ldcg(link + (long long)(2 * d + s2) * cap + a);
-    int c2 = L[2 * d + s2];
-    if (c2 >= 0) return __ldcg(link + (long long)(2 * j + s1) * cap + c2);
-    int J[N];
-#pragma unroll
-    for (int k = 0; k < N; ++k) J[k] = I[k];
-    J[j] += s1 ? 1 : -1;
-    J[d] += s2 ? 1 : -1;
-    unsigned long long kk;
-    ++fb;
-    return pack_key<N>(m, J, kk) ? table_find(m, b.table, kk) : -1;
-}
-
-// Index of c + 2 s e_j.
-template <int N>
-__device__ __forceinline__ int second_index(const Model& m, const Bufs& b, const int* link,
-                                            long long cap, const int* L, const int* I, int j, int s, long long& fb) {
-    int a = L[2 * j + s];
-    if (a >= 0) return __ldcg(link + (long long)(2 * j + s) * cap + a);
-    int J[N];
-#pragma unroll
-    for (int k = 0; k < N; ++k) J[k] = I[k];
-    J[j] += s ? 2 : -2;
-    unsigned long long kk;
-    ++fb;
-    return pack_key<N>(m, J, kk) ? table_find(m, b.table, kk) : -1;
-}
 
 template <typename T>
 __device__ __forceinline__ T q_or_zero(const T* Q, int i) {
     return i >= 0 ? Q[i] : (T)0;
 }
 
-// sum_{d != j} dt/(2 h_d) G_d(Y) for the missing cell Y = c + s e_j (P_Y = 0).
-template <int N, int DYN, typename T>
-__device__ __forceinline__ T waves_of_missing(const Model& m, const Bufs& b, const T* Q,
-                                              const int* link, long long cap, const int* L, const int* I,
-                                              const T* xc, const T* h, const T* ch, int j, int s, long long& fb) {
-    T S = (T)0;
-#pragma unroll
-    for (int d = 0; d < N; ++d) {
-        if (d == j) continue;
-        const T Pm = q_or_zero<T>(Q, edge_index<N>(m, b, link, cap, L, I, j, s, d, 0, fb));
-        const T Pp = q_or_zero<T>(Q, edge_index<N>(m, b, link, cap, L, I, j, s, d, 1, fb));
-        const T ul = vel_at<N, DYN, T>(m, xc, h, j, s ? 1 : -1, d, -1);
-        const T uh = vel_at<N, DYN, T>(m, xc, h, j, s ? 1 : -1, d, +1);
-        S += ch[d] * (fmax(ul, (T)0) * ((T)0 - Pm) + fmin(uh, (T)0) * Pp);
-    }
-    return S;
-}
+__device__ __forceinline__ bool is_halo(const unsigned short* om, long long i) { return (om[i] & OM_GHOST) != 0; }
 
-// Pass 1, one work item per (cell, dimension d) of the cells [0, ncell): the
-// lower-face velocity u_d and the entering wave G_d of the cell. New cells (of
-// this step's grow) are left out: with P = 0 their waves are formed on the spot.
+// Pass 1, one work item per (entry, dimension d) of the entries [0, ncell)
+// (active and halo): the lower-face velocity u_d and the entering wave G_d.
+// Entries added by this step's grow and halo phases are left out: their waves
+// are formed on the spot (waves_of).
 template <int N, int DYN>
 __device__ __forceinline__ void waves_body(const Model& m, const Bufs& b, const StepView& v, long long ncell) {
     const double* Q = static_cast<const double*>(b.q[v.pb]);
@@ -366,27 +420,21 @@ __device__ __forceinline__ void waves_body(const Model& m, const Bufs& b, const 
     }
 }
 
-// sum_{d != j} dt/(2 h_d) G_d(Y) for Y = c + s e_j (s = -1, 0, +1) formed on the
-// spot: y is Y's index (-1 when Y is missing, then P_Y = 0 and its transverse
-// neighbours are found through c's links). Used for missing and new cells.
+// sum_{d != j} dt/(2 h_d) G_d(Y) for the pool entry y = Y = c + s e_j (s = -1
+// or 0; xc is the centre of c), formed on the spot from Y's links; 0 when Y is
+// not in the pool (a cell without a key: it and its neighbours have p = 0).
 template <int N, int DYN>
-__device__ __forceinline__ double waves_here(const Model& m, const Bufs& b, const double* Q, const int* link,
-                                             long long cap, const int* L, const int* I, const double* xc,
-                                             const double* h, const double* ch, int j, int s, long long y,
-                                             long long& fb) {
-    const double PY = y >= 0 ? Q[y] : 0.0;
+__device__ __forceinline__ double waves_of(const Model& m, const double* Q, const int* link, long long cap,
+                                           long long y, const double* xc, const double* h, const double* ch, int j,
+                                           int s) {
+    if (y < 0) return 0.0;
+    const double PY = Q[y];
     double S = 0.0;
 #pragma unroll
     for (int d = 0; d < N; ++d) {
         if (d == j) continue;
-        double Pm, Pp;
-        if (y >= 0) {
-            Pm = q_or_zero<double>(Q, link[(long long)(2 * d) * cap + y]);
-            Pp = q_or_zero<double>(Q, link[(long long)(2 * d + 1) * cap + y]);
-        } else {
-            Pm = q_or_zero<double>(Q, edge_index<N>(m, b, link, cap, L, I, j, s > 0, d, 0, fb));
-            Pp = q_or_zero<double>(Q, edge_index<N>(m, b, link, cap, L, I, j, s > 0, d, 1, fb));
-        }
+        const double Pm = q_or_zero<double>(Q, link[(long long)(2 * d) * cap + y]);
+        const double Pp = q_or_zero<double>(Q, link[(long long)(2 * d + 1) * cap + y]);
         const double ul = vel_at<N, DYN, double>(m, xc, h, s ? j : -1, s, d, -1);
         const double uh = vel_at<N, DYN, double>(m, xc, h, s ? j : -1, s, d, +1);
         S += ch[d] * (fmax(ul, 0.0) * (PY - Pm) + fmin(uh, 0.0) * (Pp - PY));
@@ -394,81 +442,19 @@ __device__ __forceinline__ double waves_here(const Model& m, const Bufs& b, cons
     return S;
 }
 
-// Boundary faces, one item per (cell c, face f = 2j + s) of the cells [0, ncell)
-// whose neighbour across f is missing; run before grow (with it), so that a
-// neighbour that grow creates (P = 0, like a missing cell) has the same waves.
-// Writes bu (face velocity) and, when the missing neighbour is upwind of the
-// face, bt (its transverse waves over 2 h_d) and bp (the value two cells away).
-template <int N, int DYN, typename T>
-__device__ __forceinline__ void boundary_body(const Model& m, const Bufs& b, const StepView& v, long long ncell) {
-    const T* Q = static_cast<const T*>(b.q[v.pb]);
-    const unsigned long long* key = b.key[v.g];
-    const int* link = b.link[v.g];
-    const long long cap = m.cap;
-    T* bu = static_cast<T*>(b.bu);
-    T* bt = static_cast<T*>(b.bt);
-    T* bp = static_cast<T*>(b.bp);
-    T h[N], x0[N], i2h[N];
-#pragma unroll
-    for (int k = 0; k < N; ++k) {
-        h[k] = sizeof(T) == 4 ? (T)m.hf[k] : (T)m.h[k];
-        x0[k] = sizeof(T) == 4 ? (T)m.x0f[k] : (T)m.x0[k];
-        i2h[k] = (T)m.inv_2h[k];
-    }
-    long long fb = 0;
-    const long long items = ncell * 2 * N;
-    // grow runs concurrently: only cells below ncell count, anything it creates
-    // (or a slot it has claimed but not yet filled, value -1) is P = 0
-    auto qold = [&](int i) -> T { return (i >= 0 && i < ncell) ? Q[i] : (T)0; };
-    for (WarpRuns wr(items); wr.next();) {
-        const long long it = wr.c;
-        if (it >= items) continue;
-        const long long c = it / (2 * N);
-        const int f = (int)(it - c * 2 * N);
-        if (link[(long long)f * cap + c] >= 0) continue;
-        const int j = f >> 1, s = f & 1;
-        int I[N];
-        unpack_key<N>(m, key[c], I);
-        T xc[N];
-#pragma unroll
-        for (int k = 0; k < N; ++k) xc[k] = x0[k] + (T)I[k] * h[k];
-        T u = (T)0;
-#pragma unroll
-        for (int d = 0; d < N; ++d)
-            if (d == j) u = vel_at<N, DYN, T>(m, xc, h, -1, 0, d, s ? +1 : -1);
-        bu[(long long)f * cap + c] = u;
-        if (s ? !(u < (T)0) : !(u > (T)0)) continue;  // the missing neighbour is not upwind
-        int L[2 * N];
-#pragma unroll
-        for (int d = 0; d < 2 * N; ++d) L[d] = link[(long long)d * cap + c];
-        const int sgn = s ? 1 : -1;
-        T S = (T)0;
-#pragma unroll
-        for (int d = 0; d < N; ++d) {
-            if (d == j) continue;
-            const T Pm = qold(edge_index<N>(m, b, link, cap, L, I, j, s, d, 0, fb));
-            const T Pp = qold(edge_index<N>(m, b, link, cap, L, I, j, s, d, 1, fb));
-            const T ul = vel_at<N, DYN, T>(m, xc, h, j, sgn, d, -1);
-            const T uh = vel_at<N, DYN, T>(m, xc, h, j, sgn, d, +1);
-            S += i2h[d] * (fmax(ul, (T)0) * ((T)0 - Pm) + fmin(uh, (T)0) * Pp);
-        }
-        bt[(long long)f * cap + c] = S;
-        bp[(long long)f * cap + c] = qold(second_index<N>(m, b, link, cap, L, I, j, s, fb));
-    }
-    if (fb) atomicAdd((unsigned long long*)&b.sc->lookups_fallback, (unsigned long long)fb);
-}
-
-// Pass 2, one work item per (cell c, dimension j): the flux through the lower
-// j-face of c, and through its upper j-face when the upper neighbour is missing
-// (Eq. 7, the gathered corrections of Algorithm 1, the limited HR term).
-// Returns the fallback lookups.
+// Pass 2, one work item per (entry c, dimension j): the flux through the lower
+// j-face of c (Eq. 7, the gathered corrections of Algorithm 1, the limited HR
+// term), for every face with an active cell on at least one side. The upper
+// face of an active cell is the lower face of its upper neighbour, which is in
+// the pool (active or halo).
 template <int N, int DYN>
-__device__ __forceinline__ long long faces_body(const Model& m, const Bufs& b, const StepView& v) {
+__device__ __forceinline__ void faces_body(const Model& m, const Bufs& b, const StepView& v) {
     const long long ncell = v.N;
     const long long nold = v.N_prev;
     const double* Q = static_cast<const double*>(b.q[v.pb]);
     const unsigned long long* key = b.key[v.g];
     const int* link = b.link[v.g];
+    const unsigned short* om = b.om[v.g];
     const double* wu = b.wv_u;
     const double* wg = b.wv_g;
     const long long cap = m.cap;
@@ -476,7 +462,6 @@ __device__ __forceinline__ long long faces_body(const Model& m, const Bufs& b, c
     double h[N];
 #pragma unroll
     for (int k = 0; k < N; ++k) h[k] = m.h[k];
-    long long fb = 0;
     const long long items = ncell * N;
     for (WarpRuns wr(items); wr.next();) {
         const long long it = wr.c;
@@ -484,109 +469,64 @@ __device__ __forceinline__ long long faces_body(const Model& m, const Bufs& b, c
         const long long c = it / N;
         const int j = (int)(it - c * N);
         const int Llo = link[(long long)(2 * j) * cap + c];
-        const int Lhi = link[(long long)(2 * j + 1) * cap + c];
+        if (is_halo(om, c) && (Llo < 0 || is_halo(om, Llo))) continue;  // no active cell on this face
         const double P0 = Q[c];
         const double PL = q_or_zero<double>(Q, Llo);
         const double dthj = v.dth[j];
-        int L[2 * N];
         int I[N];
         double xc[N];
         bool have_pos = false;
         auto pos = [&]() {
             if (!have_pos) {
-#pragma unroll
-                for (int d = 0; d < 2 * N; ++d) L[d] = link[(long long)d * cap + c];
                 unpack_key<N>(m, key[c], I);
 #pragma unroll
                 for (int k = 0; k < N; ++k) xc[k] = m.x0[k] + (double)I[k] * h[k];
                 have_pos = true;
             }
         };
-        auto face_u = [&](int side) -> double {  // velocity at the lower (0) or upper (1) j-face of c
+        double u = 0.0;
+        if (c < nold) {
+            u = wu[(long long)j * cap + c];
+        } else {
             pos();
-            double u = 0.0;
 #pragma unroll
             for (int dd = 0; dd < N; ++dd)
-                if (dd == j) u = vel_at<N, DYN, double>(m, xc, h, -1, 0, dd, side ? +1 : -1);
-            return u;
-        };
-        const bool old_cell = c < nold;
-        const double* bt = static_cast<const double*>(b.bt);
-        const double* bp = static_cast<const double*>(b.bp);
-        const double* bu = static_cast<const double*>(b.bu);
-        // transverse sum of the upwind cell Y = c + s e_j with index y; a missing or
-        // new neighbour of an old cell has its sum precomputed (boundary_body)
-        auto trans = [&](int s, long long y) -> double {
+                if (dd == j) u = vel_at<N, DYN, double>(m, xc, h, -1, 0, dd, -1);
+        }
+        double f = 0.0;
+        if (u != 0.0) {
+            f = fmax(u, 0.0) * PL + fmin(u, 0.0) * P0;  // Eq. 7
+            // transverse sum of the cell upwind of the face
+            const long long y = u > 0.0 ? (long long)Llo : c;
+            double S = 0.0;
             if (y >= 0 && y < nold) {
-                double S = 0.0;
 #pragma unroll
                 for (int d = 0; d < N; ++d)
                     if (d != j) S += v.ch[d] * wg[(long long)d * cap + y];
-                return S;
+            } else {
+                pos();
+                S = waves_of<N, DYN>(m, Q, link, cap, y, xc, h, v.ch, j, u > 0.0 ? -1 : 0);
             }
-            if (old_cell && s != 0) {
-                const int f = 2 * j + (s > 0);
-                return v.dt * bt[(long long)f * cap + c];
-            }
-            pos();
-            return waves_here<N, DYN>(m, b, Q, link, cap, L, I, xc, h, v.ch, j, s, y, fb);
-        };
-        // value at c + 2 s e_j (limiter)
-        auto second = [&](int s) -> double {
-            const int Lm = s > 0 ? Lhi : Llo;
-            if (Lm >= 0) return q_or_zero<double>(Q, link[(long long)(2 * j + (s > 0)) * cap + Lm]);
-            if (old_cell) return bp[(long long)(2 * j + (s > 0)) * cap + c];
-            pos();
-            return q_or_zero<double>(Q, second_index<N>(m, b, link, cap, L, I, j, s > 0, fb));
-        };
-        {  // lower face (c, j)
-            const double u = old_cell ? wu[(long long)j * cap + c] : face_u(0);
-            double f = 0.0;
-            if (u != 0.0) {
-                f = fmax(u, 0.0) * PL + fmin(u, 0.0) * P0;  // Eq. 7
-                const double S = u > 0.0 ? trans(-1, (long long)Llo) : trans(0, c);
-                f -= u * S;  // Algorithm 1, gathered
-                const double W = P0 - PL;
-                if (lim != LIM_NONE && W != 0.0) {
-                    double Wup;
-                    if (u > 0.0) {
-                        Wup = PL - second(-1);
-                    } else {
-                        Wup = q_or_zero<double>(Q, Lhi) - P0;
-                    }
-                    const double au = fabs(u);
-                    f += 0.5 * au * (1.0 - dthj * au) * limited_wave<double>(lim, W, Wup);
+            f -= u * S;  // Algorithm 1, gathered
+            const double W = P0 - PL;
+            if (lim != LIM_NONE && W != 0.0) {
+                double Wup;
+                if (u > 0.0) {
+                    Wup = PL - q_or_zero<double>(Q, Llo >= 0 ? link[(long long)(2 * j) * cap + Llo] : -1);
+                } else {
+                    Wup = q_or_zero<double>(Q, link[(long long)(2 * j + 1) * cap + c]) - P0;
                 }
+                const double au = fabs(u);
+                f += 0.5 * au * (1.0 - dthj * au) * limited_wave<double>(lim, W, Wup);
             }
-            b.fl[(long long)j * cap + c] = f;
         }
-        if (Lhi < 0) {  // upper face (c + e_j, j): nobody else owns it
-            const double u = old_cell ? bu[(long long)(2 * j + 1) * cap + c] : face_u(1);
-            double f = 0.0;
-            if (u != 0.0) {
-                f = fmax(u, 0.0) * P0;  // PR = 0
-                const double S = u > 0.0 ? trans(0, c) : trans(+1, -1);
-                f -= u * S;
-                const double W = 0.0 - P0;
-                if (lim != LIM_NONE && W != 0.0) {
-                    double Wup;
-                    if (u > 0.0) {
-                        Wup = P0 - PL;
-                    } else {
-                        Wup = second(+1) - 0.0;
-                    }
-                    const double au = fabs(u);
-                    f += 0.5 * au * (1.0 - dthj * au) * limited_wave<double>(lim, W, Wup);
-                }
-            }
-            b.fu[(long long)j * cap + c] = f;
-        }
+        b.fl[(long long)j * cap + c] = f;
     }
-    return fb;
 }
 
-// Pass 3: the conservative update with the previous normalisation applied;
-// adds this thread's new values to its digits and maximum.
+// Pass 3: the conservative update of the active cells with the previous
+// normalisation applied (halo cells stay 0); adds this thread's new values to
+// its digits and maximum.
 template <int N>
 __device__ __forceinline__ void apply_body(const Model& m, const Bufs& b, const StepView& v, long long (&dacc)[NDIG],
                                            double& mx, int& err) {
@@ -594,18 +534,22 @@ __device__ __forceinline__ void apply_body(const Model& m, const Bufs& b, const 
     const double* Q = static_cast<const double*>(b.q[v.pb]);
     double* Qn = static_cast<double*>(b.q[v.pb ^ 1]);
     const int* link = b.link[v.g];
+    const unsigned short* om = b.om[v.g];
     const double* fl = b.fl;
-    const double* fu = b.fu;
     const long long cap = m.cap;
     const double scale = v.scale;
     for (WarpRuns wr(ncell); wr.next();) {
         const long long c = wr.c;
         if (c >= ncell) continue;
+        if (is_halo(om, c)) {
+            Qn[c] = 0.0;
+            continue;
+        }
         double upd = 0.0;
 #pragma unroll
         for (int j = 0; j < N; ++j) {
             const int up = link[(long long)(2 * j + 1) * cap + c];
-            const double Fhi = up >= 0 ? fl[(long long)j * cap + up] : fu[(long long)j * cap + c];
+            const double Fhi = up >= 0 ? fl[(long long)j * cap + up] : 0.0;
             upd += v.dth[j] * (Fhi - fl[(long long)j * cap + c]);
         }
         const double qn = (Q[c] - upd) * scale;
@@ -615,138 +559,28 @@ __device__ __forceinline__ void apply_body(const Model& m, const Bufs& b, const 
     }
 }
 
-// ------------------------------------------------------------------ single-pass gather update
+// ------------------------------------------------------------------ single-pass update, one lane per face
 
-// Every cell computes its 2n face fluxes from its own neighbourhood. The
+// Every active cell computes its 2n face fluxes from its own neighbourhood. The
 // corrections that Algorithm 1 scatters onto face (X, j) add up to
 //   -u_j(X) sum_{d != j} dt/(2 h_d) G_d(Y),  Y the cell upwind of the face,
 //   G_d(Y) = max(u_d(Y), 0) (P_Y - P_{Y-e_d}) + min(u_d(Y+e_d), 0) (P_{Y+e_d} - P_Y),
 // so each cell needs its face neighbours, the transverse neighbours of each
-// upwind face neighbour, and one cell two steps away per dimension (limiter).
-template <int N, int DYN, typename T>
-__device__ __forceinline__ long long gather_body(const Model& m, const Bufs& b, const StepView& v,
-                                                 long long (&dacc)[NDIG], double& mx, int& err) {
-    const long long ncell = v.N;
-    const T* Q = static_cast<const T*>(b.q[v.pb]);
-    T* Qn = static_cast<T*>(b.q[v.pb ^ 1]);
-    const unsigned long long* key = b.key[v.g];
-    const int* link = b.link[v.g];
-    const long long cap = m.cap;
-    const int lim = m.limiter;
-    const T scale = (T)v.scale;
-    T h[N], dth[N], ch[N];
-#pragma unroll
-    for (int j = 0; j < N; ++j) {
-        h[j] = (T)m.h[j];
-        dth[j] = (T)v.dth[j];
-        ch[j] = (T)v.ch[j];
-    }
-    long long fb = 0;
-    for (WarpRuns wr(ncell); wr.next();) {
-        const long long c = wr.c;
-        if (c >= ncell) continue;
-        int I[N];
-        unpack_key<N>(m, key[c], I);
-        int L[2 * N];
-#pragma unroll
-        for (int d = 0; d < 2 * N; ++d) L[d] = link[(long long)d * cap + c];
-        const T P0 = Q[c];
-        T Pn[2 * N];
-#pragma unroll
-        for (int d = 0; d < 2 * N; ++d) Pn[d] = q_or_zero<T>(Q, L[d]);
-        T xc[N];
-#pragma unroll
-        for (int k = 0; k < N; ++k) xc[k] = (T)m.x0[k] + (T)I[k] * h[k];
-        T ulo[N], uhi[N];
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-            ulo[j] = vel_at<N, DYN, T>(m, xc, h, -1, 0, j, -1);
-            uhi[j] = vel_at<N, DYN, T>(m, xc, h, -1, 0, j, +1);
-        }
-        T Gc[N];
-#pragma unroll
-        for (int d = 0; d < N; ++d)
-            Gc[d] = fmax(ulo[d], (T)0) * (P0 - Pn[2 * d]) + fmin(uhi[d], (T)0) * (Pn[2 * d + 1] - P0);
-        // sum_{d != j} dt/(2 h_d) G_d(c + s e_j), the neighbour possibly missing
-        auto trans_nb = [&](int j, int sj) -> T {
-            const T PY = Pn[2 * j + sj];
-            const int sgn = sj ? 1 : -1;
-            T S = (T)0;
-#pragma unroll
-            for (int d = 0; d < N; ++d) {
-                if (d == j) continue;
-                const T Pm = q_or_zero<T>(Q, edge_index<N>(m, b, link, cap, L, I, j, sj, d, 0, fb));
-                const T Pp = q_or_zero<T>(Q, edge_index<N>(m, b, link, cap, L, I, j, sj, d, 1, fb));
-                const T ul = vel_at<N, DYN, T>(m, xc, h, j, sgn, d, -1);
-                const T uh = vel_at<N, DYN, T>(m, xc, h, j, sgn, d, +1);
-                S += ch[d] * (fmax(ul, (T)0) * (PY - Pm) + fmin(uh, (T)0) * (Pp - PY));
-            }
-            return S;
-        };
-        T upd = (T)0;
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-            T F[2];
-#pragma unroll
-            for (int side = 0; side < 2; ++side) {
-                const T u = side ? uhi[j] : ulo[j];
-                const T PL = side ? P0 : Pn[2 * j];
-                const T PR = side ? Pn[2 * j + 1] : P0;
-                T f = (T)0;
-                if (u != (T)0) {
-                    f = fmax(u, (T)0) * PL + fmin(u, (T)0) * PR;  // Eq. 7
-                    const bool upwind_is_c = side ? (u > (T)0) : (u < (T)0);
-                    T S;
-                    if (upwind_is_c) {
-                        S = (T)0;
-#pragma unroll
-                        for (int d = 0; d < N; ++d)
-                            if (d != j) S += ch[d] * Gc[d];
-                    } else {
-                        S = trans_nb(j, side);
-                    }
-                    f -= u * S;  // Algorithm 1
-                    const T W = PR - PL;
-                    if (lim != LIM_NONE && W != (T)0) {
-                        T Wup;
-                        if (u > (T)0)
-                            Wup = side ? (P0 - Pn[2 * j])
-                                       : (Pn[2 * j] - q_or_zero<T>(Q, second_index<N>(m, b, link, cap, L, I, j, 0, fb)));
-                        else
-                            Wup = side ? (q_or_zero<T>(Q, second_index<N>(m, b, link, cap, L, I, j, 1, fb)) - Pn[2 * j + 1])
-                                       : (Pn[2 * j + 1] - P0);
-                        const T au = fabs(u);
-                        f += (T)0.5 * au * ((T)1 - dth[j] * au) * limited_wave<T>(lim, W, Wup);
-                    }
-                }
-                F[side] = f;
-            }
-            upd += dth[j] * (F[1] - F[0]);
-        }
-        const T qn = (P0 - upd) * scale;
-        Qn[c] = qn;
-        acc_add(dacc, (double)qn, err);
-        mx = fmax(mx, (double)qn);
-    }
-    return fb;
-}
-
-// ------------------------------------------------------------------ single-pass update, one lane per face
-
-// The same update as gather_body with the 2n faces of a cell spread over a
+// upwind face neighbour (through that neighbour's links), and one cell two
+// steps away per dimension (limiter). The 2n faces of a cell are spread over a
 // group of G lanes (G = 8 for n <= 4, 16 for n = 5, 6; lane 2j + s owns the
-// lower (s = 0) or upper (s = 1) j-face). The cell's own waves and the update
-// are combined with shuffles inside the group, so each lane walks one face's
-// neighbourhood: 2n times more independent work than one lane per cell.
+// lower (s = 0) or upper (s = 1) j-face); the cell's own waves and the update
+// are combined with shuffles inside the group.
 template <int N, int DYN, typename T>
-__device__ __forceinline__ long long gather_faces_body(const Model& m, const Bufs& b, const StepView& v,
-                                                       long long (&dacc)[NDIG], double& mx, int& err) {
+__device__ __forceinline__ void gather_faces_body(const Model& m, const Bufs& b, const StepView& v,
+                                                  long long (&dacc)[NDIG], double& mx, int& err) {
     constexpr int G = (2 * N <= 8) ? 8 : 16;
     const long long ncell = v.N;
     const T* Q = static_cast<const T*>(b.q[v.pb]);
     T* Qn = static_cast<T*>(b.q[v.pb ^ 1]);
     const unsigned long long* key = b.key[v.g];
     const int* link = b.link[v.g];
+    const unsigned short* om = b.om[v.g];
     const long long cap = m.cap;
     const int lim = m.limiter;
     const T scale = (T)v.scale;
@@ -759,7 +593,6 @@ __device__ __forceinline__ long long gather_faces_body(const Model& m, const Buf
         dthT[k] = (T)v.dth[k];
     }
     T tmax = -INFINITY;
-    long long fb = 0;
     const long long items = ncell * G;
     const unsigned full = 0xffffffffu;
     for (WarpRuns wr(items); wr.next();) {
@@ -768,15 +601,16 @@ __device__ __forceinline__ long long gather_faces_body(const Model& m, const Buf
         const long long c = it / G;
         const int l = (int)(it % G);
         const bool cell_ok = c < ncell;
-        const bool face_ok = cell_ok && l < 2 * N;
+        const bool active = cell_ok && !is_halo(om, c);
+        const bool face_ok = active && l < 2 * N;
         const int j = face_ok ? (l >> 1) : 0;
         const int side = l & 1;
         T P0 = (T)0, Pn = (T)0, u = (T)0;
         int Ls = -1;
-        int I[N];
         T xc[N];
-        if (cell_ok) {
+        if (active) {
             P0 = Q[c];
+            int I[N];
             unpack_key<N>(m, key[c], I);
 #pragma unroll
             for (int k = 0; k < N; ++k) xc[k] = x0[k] + (T)I[k] * h[k];
@@ -813,28 +647,16 @@ __device__ __forceinline__ long long gather_faces_body(const Model& m, const Buf
             if (u != (T)0) {
                 f = fmax(u, (T)0) * PL + fmin(u, (T)0) * PR;  // Eq. 7
                 const bool upwind_is_c = side ? (u > (T)0) : (u < (T)0);
-                T S;
+                T S = (T)0;
                 if (upwind_is_c) {
                     S = tot - chj * Gj;
-                } else if (Ls < 0 && c < v.N_prev) {  // missing neighbour: precomputed waves
-                    S = (T)v.dt * static_cast<const T*>(b.bt)[(long long)(2 * j + side) * cap + c];
-                } else {  // the neighbour across this face (possibly new or missing)
-                    int L[2 * N];
-#pragma unroll
-                    for (int d = 0; d < 2 * N; ++d) L[d] = link[(long long)d * cap + c];
+                } else if (Ls >= 0) {  // through the links of the neighbour across this face
                     const int sgn = side ? 1 : -1;
-                    S = (T)0;
 #pragma unroll
                     for (int d = 0; d < N; ++d) {
                         if (d == j) continue;
-                        T Pm, Pp;
-                        if (Ls >= 0) {
-                            Pm = q_or_zero<T>(Q, link[(long long)(2 * d) * cap + Ls]);
-                            Pp = q_or_zero<T>(Q, link[(long long)(2 * d + 1) * cap + Ls]);
-                        } else {
-                            Pm = q_or_zero<T>(Q, edge_index<N>(m, b, link, cap, L, I, j, side, d, 0, fb));
-                            Pp = q_or_zero<T>(Q, edge_index<N>(m, b, link, cap, L, I, j, side, d, 1, fb));
-                        }
+                        const T Pm = q_or_zero<T>(Q, link[(long long)(2 * d) * cap + Ls]);
+                        const T Pp = q_or_zero<T>(Q, link[(long long)(2 * d + 1) * cap + Ls]);
                         const T ul = vel_at<N, DYN, T>(m, xc, h, j, sgn, d, -1);
                         const T uh = vel_at<N, DYN, T>(m, xc, h, j, sgn, d, +1);
                         S += chT[d] * (fmax(ul, (T)0) * (Pn - Pm) + fmin(uh, (T)0) * (Pp - Pn));
@@ -843,18 +665,11 @@ __device__ __forceinline__ long long gather_faces_body(const Model& m, const Buf
                 f -= u * S;  // Algorithm 1
                 const T W = PR - PL;
                 if (lim != LIM_NONE && W != (T)0) {
-                    T Wup;
                     // value two cells away across this face
-                    auto second = [&]() -> T {
-                        if (Ls >= 0) return q_or_zero<T>(Q, link[(long long)(2 * j + side) * cap + Ls]);
-                        if (c < v.N_prev) return static_cast<const T*>(b.bp)[(long long)(2 * j + side) * cap + c];
-                        int L[2 * N];
-#pragma unroll
-                        for (int d = 0; d < 2 * N; ++d) L[d] = link[(long long)d * cap + c];
-                        return q_or_zero<T>(Q, second_index<N>(m, b, link, cap, L, I, j, side, fb));
-                    };
-                    if (u > (T)0) Wup = side ? (P0 - Plo) : (Plo - second());
-                    else Wup = side ? (second() - Phi) : (Phi - P0);
+                    const T P2 = Ls >= 0 ? q_or_zero<T>(Q, link[(long long)(2 * j + side) * cap + Ls]) : (T)0;
+                    T Wup;
+                    if (u > (T)0) Wup = side ? (P0 - Plo) : (Plo - P2);
+                    else Wup = side ? (P2 - Phi) : (Phi - P0);
                     const T au = fabs(u);
                     f += (T)0.5 * au * ((T)1 - dthj * au) * limited_wave<T>(lim, W, Wup);
                 }
@@ -864,44 +679,48 @@ __device__ __forceinline__ long long gather_faces_body(const Model& m, const Buf
 #pragma unroll
         for (int off = G / 2; off > 0; off >>= 1) contrib += __shfl_xor_sync(full, contrib, off, G);
         if (cell_ok && l == 0) {
-            const T qn = (P0 - contrib) * scale;
-            Qn[c] = qn;
-            acc_add(dacc, qn, err);
-            tmax = fmax(tmax, qn);
+            if (active) {
+                const T qn = (P0 - contrib) * scale;
+                Qn[c] = qn;
+                acc_add(dacc, qn, err);
+                tmax = fmax(tmax, qn);
+            } else {
+                Qn[c] = (T)0;
+            }
         }
     }
     if (tmax > -INFINITY) mx = fmax(mx, (double)tmax);
-    return fb;
 }
 
 // ------------------------------------------------------------------ prune
 
-// keep[c] = (p_c > p*): the significant cells S.
+// keep[c] = (p_c > p*) for the active cells: the significant cells S.
 template <typename T>
 __device__ __forceinline__ void prune_mark_body(const Model& m, const Bufs& b, const StepView& v) {
     const double pstar = m.thr_rel * v.maxq;
     const T* Q = static_cast<const T*>(b.q[v.pb]);
+    const unsigned short* om = b.om[v.g];
     for (WarpRuns r(v.N); r.next();) {
         const long long c = r.c;
-        if (c < v.N) b.keep[c] = (double)Q[c] > pstar;
+        if (c < v.N) b.keep[c] = !is_halo(om, c) && (double)Q[c] > pstar;
     }
 }
 
-// keep[D(S)] = 1: each significant cell marks the existing cells of its
-// downwind set (Sec. 3.3, Fig. 3).
+// keep[D(S)] = 1: each significant cell marks the pool entries of its
+// downwind set (Sec. 3.3, Fig. 3); only the active ones among them are kept.
 template <int N, typename T>
 __device__ __forceinline__ void prune_scatter_body(const Model& m, const Bufs& b, const StepView& v) {
     const double pstar = m.thr_rel * v.maxq;
     const T* Q = static_cast<const T*>(b.q[v.pb]);
-    const unsigned long long* key = b.key[v.g];
     const int* link = b.link[v.g];
     const unsigned short* om = b.om[v.g];
     const long long cap = m.cap;
     for (WarpRuns r(v.N); r.next();) {
         const long long c = r.c;
         if (c >= v.N) continue;
-        if (!((double)Q[c] > pstar)) continue;
-        const unsigned out = om[c] & 0xfffu;
+        const unsigned f = om[c];
+        if ((f & OM_GHOST) || !((double)Q[c] > pstar)) continue;
+        const unsigned out = f & 0xfffu;
         if (!out) continue;
         int L[2 * N];
 #pragma unroll
@@ -915,15 +734,7 @@ __device__ __forceinline__ void prune_scatter_body(const Model& m, const Bufs& b
 #pragma unroll
             for (int d2 = 0; d2 < 2 * N; ++d2) {
                 if ((d2 >> 1) <= (d1 >> 1) || !((out >> d2) & 1u)) continue;
-                int e = edge_by_links(link, cap, L, d1 >> 1, d1 & 1, d2 >> 1, d2 & 1);
-                if (e == -2) {
-                    int I[N];
-                    unpack_key<N>(m, key[c], I);
-                    I[d1 >> 1] += (d1 & 1) ? 1 : -1;
-                    I[d2 >> 1] += (d2 & 1) ? 1 : -1;
-                    unsigned long long kk;
-                    e = pack_key<N>(m, I, kk) ? table_find(m, b.table, kk) : -1;
-                }
+                const int e = edge_by_links(link, cap, L, d1 >> 1, d1 & 1, d2 >> 1, d2 & 1);
                 if (e >= 0) b.keep[e] = 1;
             }
         }
@@ -938,65 +749,102 @@ __device__ __forceinline__ void block_chunk(long long total, long long& c0, long
     c1 = min(total, c0 + per);
 }
 
-// This block's count of kept cells into blk[blockIdx.x]; the table slots of
-// the current cells are emptied for the rehash (the table holds nothing else).
-__device__ __forceinline__ void prune_count_body(const Model& m, const Bufs& b, const StepView& v) {
-    long long c0, c1;
-    block_chunk(v.N, c0, c1);
-    int cnt = 0;
-    for (long long c = c0 + threadIdx.x; c < c1; c += blockDim.x) cnt += b.keep[c] != 0;
+// Sum of a per-thread count over the block (every thread gets it).
+__device__ __forceinline__ long long block_count(int cnt) {
+    __shared__ long long s[WARPS];
     for (int off = 16; off > 0; off >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, off);
-    __shared__ int s[WARPS];
     if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = cnt;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        long long t = 0;
-        for (int w = 0; w < WARPS; ++w) t += s[w];
-        b.blk[blockIdx.x] = t;
-    }
+    long long t = 0;
+    for (int w = 0; w < WARPS; ++w) t += s[w];
     __syncthreads();
+    return t;
+}
+
+// Status of every entry into map: 1 active and kept, 2 halo of a kept cell
+// (not kept, with a kept face neighbour), 0 dropped. The block's counts of
+// both go to blk and blk2; the table slots of the current entries are emptied
+// for the rehash (the table holds nothing else).
+template <int N>
+__device__ __forceinline__ void prune_count_body(const Model& m, const Bufs& b, const StepView& v) {
+    const int* link = b.link[v.g];
+    const unsigned short* om = b.om[v.g];
+    const long long cap = m.cap;
+    long long c0, c1;
+    block_chunk(v.N, c0, c1);
+    int na = 0, ng = 0;
+    for (long long c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+        int st = 0;
+        if (b.keep[c] && !is_halo(om, c)) {
+            st = 1;
+        } else {
+#pragma unroll
+            for (int d = 0; d < 2 * N; ++d) {
+                const int l = link[(long long)d * cap + c];
+                if (l >= 0 && b.keep[l] && !is_halo(om, l)) st = 2;
+            }
+        }
+        b.map[c] = st;
+        na += st == 1;
+        ng += st == 2;
+    }
+    const long long ta = block_count(na);
+    const long long tg = block_count(ng);
+    if (threadIdx.x == 0) {
+        b.blk[blockIdx.x] = ta;
+        b.blk2[blockIdx.x] = tg;
+    }
     const unsigned int* slots = b.slot[v.g];
     for (long long c = c0 + threadIdx.x; c < c1; c += blockDim.x)
         reinterpret_cast<ulonglong2*>(b.table)[slots[c]] = make_ulonglong2(EMPTY_KEY, ~0ull);
 }
 
-// Offset of this block's survivors (sum of the counts of the blocks before it)
-// and the total, read by every block from blk (same values everywhere).
-__device__ __forceinline__ void block_offset_total(const Bufs& b, long long& offset, long long& total) {
-    __shared__ long long s_off[WARPS], s_tot[WARPS];
-    long long o = 0, t = 0;
+// Offsets of this block's survivors in the new pool (active cells first, then
+// halo cells) and the totals, read by every block from blk and blk2.
+struct Survivors {
+    long long base_a, base_g, total_a, total_g;
+};
+__device__ __forceinline__ Survivors block_offsets(const Bufs& b) {
+    __shared__ long long s[4][WARPS];
+    long long v[4] = {0, 0, 0, 0};  // offset a, total a, offset g, total g
     for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
-        long long v = __ldcg(&b.blk[i]);
-        t += v;
-        if (i < (int)blockIdx.x) o += v;
+        const long long a = __ldcg(&b.blk[i]);
+        const long long g = __ldcg(&b.blk2[i]);
+        v[1] += a;
+        v[3] += g;
+        if (i < (int)blockIdx.x) {
+            v[0] += a;
+            v[2] += g;
+        }
     }
-    for (int off = 16; off > 0; off >>= 1) {
-        o += __shfl_down_sync(0xffffffffu, o, off);
-        t += __shfl_down_sync(0xffffffffu, t, off);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        s_off[threadIdx.x >> 5] = o;
-        s_tot[threadIdx.x >> 5] = t;
-    }
-    __syncthreads();
-    o = 0;
-    t = 0;
-    for (int w = 0; w < WARPS; ++w) {
-        o += s_off[w];
-        t += s_tot[w];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
+        if ((threadIdx.x & 31) == 0) s[k][threadIdx.x >> 5] = v[k];
     }
     __syncthreads();
-    offset = o;
-    total = t;
+    long long t[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        for (int w = 0; w < WARPS; ++w) t[k] += s[k][w];
+    __syncthreads();
+    Survivors r;
+    r.base_a = t[0];
+    r.total_a = t[1];
+    r.base_g = t[1] + t[2];
+    r.total_g = t[3];
+    return r;
 }
 
-// Stream compaction of the kept cells in storage order into the other buffer
-// set, starting at `base`; map[c] = new index or -1. The values are rescaled by
-// an exact power of two that brings the maximum into [1, 2) (their ratios do
-// not change, and the exact sum stays in its window even after a very unlikely
-// measurement). Adds the survivors' digits, maximum and CFL rates.
+// Stream compaction of the survivors in storage order into the other buffer
+// set: the kept active cells at [0, total_a), the halo cells after them;
+// map[c] = new index or -1. Values of active cells are rescaled by an exact
+// power of two that brings the maximum into [1, 2) (their ratios do not
+// change, and the exact sum stays in its window even after a very unlikely
+// measurement); halo cells hold 0. Adds the active cells' digits, maximum and
+// CFL rates.
 template <int N, typename T>
-__device__ __forceinline__ void prune_compact_body(const Model& m, const Bufs& b, const StepView& v, long long base,
+__device__ __forceinline__ void prune_compact_body(const Model& m, const Bufs& b, const StepView& v, Survivors sv,
                                                    long long (&d)[NDIG], double& mx, double& rmax, int& err) {
     const T* Q = static_cast<const T*>(b.q[v.pb]);
     T* Qo = static_cast<T*>(b.q[v.pb ^ 1]);
@@ -1006,32 +854,41 @@ __device__ __forceinline__ void prune_compact_body(const Model& m, const Bufs& b
     unsigned short* omo = b.om[v.g ^ 1];
     const double mq = v.maxq;
     const double s2 = (mq > 0.0 && isfinite(mq)) ? ldexp(1.0, -ilogb(mq)) : 1.0;
+    long long ba = sv.base_a, bg = sv.base_g;
     long long c0, c1;
     block_chunk(v.N, c0, c1);
     for (long long t0 = c0; t0 < c1; t0 += blockDim.x) {
-        long long c = t0 + threadIdx.x;
-        int f = (c < c1) ? (b.keep[c] != 0) : 0;
-        int total;
-        int pos = block_exclusive_scan(f, total);
+        const long long c = t0 + threadIdx.x;
+        const int st = (c < c1) ? b.map[c] : 0;
+        int na, ng;
+        const int pa = block_exclusive_scan(st == 1, na);
+        const int pg = block_exclusive_scan(st == 2, ng);
         if (c < c1) {
-            if (f) {
-                long long nc = base + pos;
-                unsigned long long k = key[c];
-                T val = (T)((double)Q[c] * s2);
+            const unsigned long long k = key[c];
+            if (st == 1) {
+                const long long nc = ba + pa;
+                const T val = (T)((double)Q[c] * s2);
                 keyo[nc] = k;
                 Qo[nc] = val;
-                omo[nc] = (unsigned short)(om[c] & ~OM_COMPLETE);
+                omo[nc] = (unsigned short)(om[c] & 0xfffu);
                 b.map[c] = (int)nc;
                 acc_add(d, (double)val, err);
                 mx = fmax(mx, (double)val);
                 int I[N];
                 unpack_key<N>(m, k, I);
                 rmax = fmax(rmax, cfl_rate64<N>(m, I));
+            } else if (st == 2) {
+                const long long nc = bg + pg;
+                keyo[nc] = k;
+                Qo[nc] = (T)0;
+                omo[nc] = (unsigned short)((om[c] & 0xfffu) | OM_GHOST);
+                b.map[c] = (int)nc;
             } else {
                 b.map[c] = -1;
             }
         }
-        base += total;
+        ba += na;
+        bg += ng;
     }
 }
 

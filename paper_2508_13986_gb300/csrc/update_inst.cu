@@ -23,22 +23,23 @@ using Real = double;
 using Real = float;
 #endif
 
-// pre: the kernels before the link phase; post: after it (all take (Model, Bufs)).
+// pre: the kernels before the link phase (grow, halo); post: after it (all
+// take (Model, Bufs)).
 template <int N, int DYN>
 static void kernels_of(Kernels* k) {
     k->persist = (void*)k_persistent<N, DYN, Real>;
 #if GBEES_PREC == 64
     k->pre[0] = (void*)k_grow_waves<N, DYN>;
-    k->npre = 1;
     k->post[0] = (void*)k_faces<N, DYN>;
     k->post[1] = (void*)k_apply<N>;
     k->npost = 2;
 #else
-    k->pre[0] = (void*)k_grow_boundary<N, DYN, Real>;
-    k->npre = 1;
+    k->pre[0] = (void*)k_grow<N, Real>;
     k->post[0] = (void*)k_ctu<N, DYN, Real>;
     k->npost = 1;
 #endif
+    k->pre[1] = (void*)k_halo<N, Real, 1>;
+    k->npre = 2;
 }
 
 #define GBEES_JOIN2(a, b) a##b

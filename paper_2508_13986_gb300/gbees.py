@@ -56,6 +56,7 @@ class gbees_stats(ctypes.Structure):
         ("total_steps", ctypes.c_int64),
         ("n_cells", ctypes.c_int64),
         ("norm", ctypes.c_double),
+        ("n_pool", ctypes.c_int64),
     ]
 
 
@@ -227,10 +228,11 @@ class Stats:
     total_steps: int
     n_cells: int
     norm: float
+    n_pool: int
 
     @classmethod
     def of(cls, s: gbees_stats) -> "Stats":
-        return cls(s.steps, s.cell_updates, s.t, s.last_dt, s.total_steps, s.n_cells, s.norm)
+        return cls(s.steps, s.cell_updates, s.t, s.last_dt, s.total_steps, s.n_cells, s.norm, s.n_pool)
 
 
 def make_config(n: int, dynamics: int, params: Sequence[float], h: Sequence[float], x0: Sequence[float],

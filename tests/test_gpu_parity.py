@@ -86,7 +86,7 @@ def test_lorenz63_fp32_store(prec):
 
 def test_lorenz96_6d_h05_short_fp64():
     w = W.lorenz96(h=0.5, t_end=0.06, prune_interval=2)
-    g, o = make_pair(w, max_cells=1 << 19)
+    g, o = make_pair(w, max_cells=1 << 20)
     g.init_gaussian(w.mean, w.cov)
     o.init_gaussian(w.mean, w.cov)
     assert_fp64_parity(g, o, w)
@@ -108,7 +108,8 @@ def test_random_sets_linear_dynamics_fp64(n, lim):
     x0 = rng.standard_normal(n)
     w = W.Workload(name="rand", n=n, dynamics=W.DYN_LINEAR, params=tuple(A.reshape(-1)) + tuple(b), h=tuple(h),
                    mean=tuple(x0), cov=np.eye(n), thr_rel=0.05, cfl=0.8, t_end=0.0, prune_interval=2, limiter=lim)
-    g, o = make_pair(w, max_cells=1 << 18)
+    # sparse sets in high dimension: the halo (missing face neighbours) outnumbers the active cells
+    g, o = make_pair(w, max_cells=1 << 20)
     g.init_cells(idx, p)
     o.init_cells(idx, p)
     for k in range(1, 4):
@@ -167,8 +168,11 @@ def test_edge_cases():
     # a new grid clears the poisoned state
     g.init_gaussian(w.mean, w.cov)
     assert g.status == 0
-    # capacity overflow on growth
-    small = gbees.grid_for_workload(w, max_cells=7000)
+    # capacity overflow on growth: room for the initial cells and their halo only
+    g.init_gaussian(w.mean, w.cov)
+    pool0 = g.stats().n_pool
+    assert pool0 > g.count()
+    small = gbees.grid_for_workload(w, max_cells=pool0 + 16)
     small.init_gaussian(w.mean, w.cov)
     with pytest.raises(gbees.GbeesError) as e:
         small.propagate(0.5)
@@ -180,10 +184,14 @@ def test_edge_cases():
     with pytest.raises(gbees.GbeesError) as e:
         tiny.init_gaussian(w.mean, w.cov)
     assert e.value.status == gbees.GBEES_ECAPACITY
-    # key range (21 bits per dimension for n = 3): growth across the edge of the range
+    # key range (21 bits per dimension for n = 3; active cells one layer inside it):
+    # growth across the edge of the range
     cfg = gbees.make_config(3, gbees.GBEES_DYN_CONSTANT, (1.0, 0.0, 0.0), [1.0] * 3, [0.0] * 3, max_cells=64)
     edge = gbees.Grid(cfg)
-    edge.init_cells(np.array([[2 ** 20 - 1, 0, 0]], dtype=np.int32), np.array([1.0]))
+    with pytest.raises(gbees.GbeesError) as e:
+        edge.init_cells(np.array([[2 ** 20 - 1, 0, 0]], dtype=np.int32), np.array([1.0]))
+    assert e.value.status == gbees.GBEES_EKEYRANGE
+    edge.init_cells(np.array([[2 ** 20 - 2, 0, 0]], dtype=np.int32), np.array([1.0]))
     with pytest.raises(gbees.GbeesError) as e:
         edge.propagate(0.5)
     assert e.value.status == gbees.GBEES_EKEYRANGE
