@@ -259,8 +259,7 @@ def time_precision(args, w, precision, dev, rank, world):
         traffic = rec["bytes_per_cell"] * prof_updates / launches_upd
     tot_ms = sum(prof["ms"].values())
     phase_share = {k: (v / tot_ms if tot_ms > 0 else 0.0) for k, v in prof["ms"].items()}
-    kernels = ("k_ctu (single-pass gather)" if precision == "f32"
-               else "k_waves + k_faces + k_apply (three-pass FP64 update)")
+    kernels = "k_faces + k_apply (flux and conservative update)"
     return {
         "value": upd_sum / (ms_max / 1e3),
         "ms_per_step": ms_max / args.steps,

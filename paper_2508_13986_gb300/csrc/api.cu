@@ -157,17 +157,17 @@ bool make_layout(const gbees_config* c, Layout* L) {
     L->part = take(sizeof(Partial) * GRID_MAX);
     for (int g = 0; g < 2; ++g) L->key[g] = take(8 * cap);
     for (int g = 0; g < 2; ++g) L->q[g] = take(S * cap);
-    for (int g = 0; g < 2; ++g) L->link[g] = take((size_t)4 * 2 * c->n * cap);
+    for (int g = 0; g < 2; ++g) L->link[g] = take((size_t)4 * lrow_of(c->n) * cap);
     for (int g = 0; g < 2; ++g) L->om[g] = take(2 * cap);
     for (int g = 0; g < 2; ++g) L->slot[g] = take(4 * cap);
     L->keep = take(cap);
     L->map = take(4 * cap);
     L->table = take(sizeof(Slot) * slots);
-    // scratch of the three-pass FP64 update
-    const size_t fp64 = c->precision == GBEES_FP64 ? (size_t)8 * c->n * cap : 0;
-    L->wv_u = take(fp64);
-    L->wv_g = take(fp64);
-    L->fl = take(fp64);
+    // scratch of the three-pass update, storage type
+    const size_t rows = S * (size_t)wrow_of(c->n) * cap;
+    L->wv_u = take(rows);
+    L->wv_g = take(rows);
+    L->fl = take(rows);
     L->total = off;
     L->slots = slots;
     return true;
@@ -222,9 +222,9 @@ void bind_context(gbees_ctx* ctx, const gbees_config* cfg, const Layout& L, void
     b.keep = (unsigned char*)(base + L.keep);
     b.map = (int*)(base + L.map);
     b.table = (Slot*)(base + L.table);
-    b.wv_u = (double*)(base + L.wv_u);
-    b.wv_g = (double*)(base + L.wv_g);
-    b.fl = (double*)(base + L.fl);
+    b.wv_u = (void*)(base + L.wv_u);
+    b.wv_g = (void*)(base + L.wv_g);
+    b.fl = (void*)(base + L.fl);
 }
 
 void set_err(gbees_ctx* ctx, int st, const std::string& msg) {

@@ -137,9 +137,10 @@ struct alignas(64) Partial {
 // every face neighbour of an active cell that is not active itself is kept as
 // a halo cell (p = 0, never updated, never counted), so that all cells of the
 // update stencil (face neighbours, their face neighbours, the second
-// neighbours) are reached through links. link[g] holds 2n arrays of cap int32:
-// entry (2j + s) * cap + c is the index of the neighbour of entry c one step
-// down (s = 0) or up (s = 1) in dimension j, or -1 when it is not in the pool.
+// neighbours) are reached through links. link[g] holds one row of LROW int32
+// per entry: entry c * LROW + 2j + s is the index of the neighbour of entry c
+// one step down (s = 0) or up (s = 1) in dimension j, or -1 when it is not in
+// the pool.
 //
 // om[g][c]: bits 0..2n-1 are the outward directions of cell c (bit 2j+1: the
 // flow leaves through the upper j-face, bit 2j: through the lower j-face),
@@ -147,9 +148,9 @@ struct alignas(64) Partial {
 // halo cell; bit 15 marks an active cell whose downwind set is known to be
 // active (cleared by every prune).
 //
-// FP64 update scratch (n arrays of cap doubles each): wv_u[j] lower-face
-// velocity, wv_g[d] d-direction wave entering the cell, fl[j] flux through the
-// lower j-face.
+// Update scratch (one row of WROW values of the storage type per entry):
+// wv_u[c, j] lower-face velocity, wv_g[c, d] d-direction wave entering the
+// cell, fl[c, j] flux through the lower j-face.
 struct Bufs {
     unsigned long long* key[2];
     void* q[2];
@@ -162,11 +163,22 @@ struct Bufs {
     DevScalars* sc;
     long long* blk;  // per-block counts (active cells)
     long long* blk2; // per-block counts (halo cells)
-    double* wv_u;
-    double* wv_g;
-    double* fl;
+    void* wv_u;  // update scratch in the storage type
+    void* wv_g;
+    void* fl;
     Partial* part;   // GRID_MAX per-block partials
 };
+
+// Rows of the per-entry arrays (cell-major, so that the links or the FP64
+// scratch of one entry share one or two 32-byte sectors): LROW<N> int32 per
+// link row (2n rounded up to a power of two), WROW<N> doubles per scratch row
+// (n rounded up to a power of two).
+template <int N>
+constexpr int LROW = (2 * N <= 2) ? 2 : (2 * N <= 4) ? 4 : (2 * N <= 8) ? 8 : 16;
+template <int N>
+constexpr int WROW = (N <= 1) ? 1 : (N <= 2) ? 2 : (N <= 4) ? 4 : 8;
+__host__ __device__ constexpr int lrow_of(int n) { return (2 * n <= 2) ? 2 : (2 * n <= 4) ? 4 : (2 * n <= 8) ? 8 : 16; }
+__host__ __device__ constexpr int wrow_of(int n) { return (n <= 1) ? 1 : (n <= 2) ? 2 : (n <= 4) ? 4 : 8; }
 
 constexpr unsigned short OM_COMPLETE = 0x8000;
 constexpr unsigned short OM_GHOST = 0x4000;

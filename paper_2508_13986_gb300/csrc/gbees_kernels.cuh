@@ -208,13 +208,6 @@ __device__ __forceinline__ void grow_rates(DevScalars* sc, double r) {
     if (threadIdx.x == 0 && r > 0.0) atomicMax(&sc->maxrate_bits, (unsigned long long)__double_as_longlong(r));
 }
 
-template <int N, typename T>
-__global__ void __launch_bounds__(THREADS) k_grow(const Model m, Bufs b) {
-    DevScalars* sc = b.sc;
-    if (*(volatile int*)&sc->done | *(volatile int*)&sc->error) return;
-    grow_rates(sc, grow_body<N, T>(m, b, view_of(m, sc)));
-}
-
 // Halo cells around the cells that grow made active (inserted ones: [N_prev, N)
 // at entry; activated ones: the n_act entries listed in map). With STEP == 0
 // (initial grid) it runs whatever the done flag says. The last block appends
@@ -262,27 +255,27 @@ __device__ __forceinline__ void finish_step(const Model& m, DevScalars* sc, cons
     sc->ticket = 0;
 }
 
-// FP64 step, first phase: grow, and the waves of the entries that existed
+// First phase of a step: grow, and the waves of the entries that existed
 // before it (a cell that grow or halo adds has p = 0, like a missing one, so
 // the waves of the old entries do not change).
-template <int N, int DYN>
+template <int N, int DYN, typename T>
 __global__ void __launch_bounds__(THREADS) k_grow_waves(const Model m, Bufs b) {
     DevScalars* sc = b.sc;
     if (*(volatile int*)&sc->done | *(volatile int*)&sc->error) return;
     const StepView v = view_of(m, sc);
-    const double r = grow_body<N, double>(m, b, v);
-    waves_body<N, DYN>(m, b, v, v.N_prev);
+    const double r = grow_body<N, T>(m, b, v);
+    waves_body<N, DYN, T>(m, b, v, v.N_prev);
     grow_rates(sc, r);
 }
 
-template <int N, int DYN>
+template <int N, int DYN, typename T>
 __global__ void __launch_bounds__(THREADS) k_faces(const Model m, Bufs b) {
     DevScalars* sc = b.sc;
     if (*(volatile int*)&sc->done | *(volatile int*)&sc->error) return;
-    faces_body<N, DYN>(m, b, view_of(m, sc));
+    faces_body<N, DYN, T>(m, b, view_of(m, sc));
 }
 
-template <int N>
+template <int N, typename T>
 __global__ void __launch_bounds__(THREADS) k_apply(const Model m, Bufs b) {
     DevScalars* sc = b.sc;
     if (*(volatile int*)&sc->done | *(volatile int*)&sc->error) return;
@@ -290,24 +283,7 @@ __global__ void __launch_bounds__(THREADS) k_apply(const Model m, Bufs b) {
     long long d[NDIG] = {0, 0, 0, 0, 0, 0};
     double mx = -INFINITY;
     int err = 0;
-    apply_body<N>(m, b, v, d, mx, err);
-    if (err) set_error(sc, ST_EDEGENERATE);
-    block_partial(b.part, d, mx, 0.0);
-    if (last_block(sc)) {
-        Combined cs = combine_partials(b.part, gridDim.x);
-        if (threadIdx.x == 0) finish_step(m, sc, cs, v.pb);
-    }
-}
-
-template <int N, int DYN, typename T>
-__global__ void __launch_bounds__(THREADS) k_ctu(const Model m, Bufs b) {
-    DevScalars* sc = b.sc;
-    if (*(volatile int*)&sc->done | *(volatile int*)&sc->error) return;
-    const StepView v = view_of(m, sc);
-    long long d[NDIG] = {0, 0, 0, 0, 0, 0};
-    double mx = -INFINITY;
-    int err = 0;
-    gather_faces_body<N, DYN, T>(m, b, v, d, mx, err);
+    apply_body<N, T>(m, b, v, d, mx, err);
     if (err) set_error(sc, ST_EDEGENERATE);
     block_partial(b.part, d, mx, 0.0);
     if (last_block(sc)) {

@@ -8,8 +8,8 @@
 // step's scalars (dt, normalisation, maximum) itself from the same per-block
 // partials, so the scalars need no extra barrier; block 0 writes them back.
 //
-// Barriers per step: grow (FP64: + waves) | halo | link | (FP64: faces |)
-// update; a prune adds mark | scatter | status | compact | relink.
+// Barriers per step: grow + waves | halo | link | faces | apply; a prune adds
+// mark | scatter | status | compact | relink.
 #pragma once
 
 #include "gbees_kernels.cuh"
@@ -61,10 +61,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_persistent(const Model m, Bufs b
     };
 
     for (long long it = 0; it < max_steps && !done; ++it) {
-        // grow (appends active cells to sc->N, activates halo cells); FP64: the
+        // grow (appends active cells to sc->N, activates halo cells) and the
         // waves of the existing entries alongside
         const double rg = grow_body<N, T>(m, b, v);
-        if constexpr (sizeof(T) == 8) waves_body<N, DYN>(m, b, v, v.N_prev);
+        waves_body<N, DYN, T>(m, b, v, v.N_prev);
         if (!grid_barrier(sc)) return;
         mark(0);
         // halo cells around the newly active cells (appended after sc->N, which
@@ -119,14 +119,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_persistent(const Model m, Bufs b
         long long d[NDIG] = {0, 0, 0, 0, 0, 0};
         double mx = -INFINITY;
         int err = 0;
-        if constexpr (sizeof(T) == 8) {
-            faces_body<N, DYN>(m, b, v);
-            if (!grid_barrier(sc)) return;
-            mark(2);
-            apply_body<N>(m, b, v, d, mx, err);
-        } else {
-            gather_faces_body<N, DYN, T>(m, b, v, d, mx, err);
-        }
+        faces_body<N, DYN, T>(m, b, v);
+        if (!grid_barrier(sc)) return;
+        mark(2);
+        apply_body<N, T>(m, b, v, d, mx, err);
         if (err) set_error(sc, ST_EDEGENERATE);
         block_partial(b.part, d, mx, 0.0);
         if (!grid_barrier(sc)) return;

@@ -92,16 +92,37 @@ __device__ __forceinline__ unsigned outward_mask(const Model& m, const int* I) {
     return msk;
 }
 
-// Index of cell c + s1 e_j + s2 e_d (j != d) through the links, -1 when it is
-// not in the pool. For an active cell c the face neighbour c + s1 e_j is in the
-// pool, so its link decides; -2 only when both intermediate cells are missing.
-__device__ __forceinline__ int edge_by_links(const int* link, long long cap, const int* L, int j, int s1,
-                                             int d, int s2) {
+// Index of cell c + s1 e_j + s2 e_d (j != d) through the links (L: the link
+// row of c), -1 when it is not in the pool. For an active cell c the face
+// neighbour c + s1 e_j is in the pool, so its link decides; -2 only when both
+// intermediate cells are missing.
+template <int N>
+__device__ __forceinline__ int edge_by_links(const int* link, const int* L, int j, int s1, int d, int s2) {
     int a = L[2 * j + s1];
-    if (a >= 0) return __ldcg(link + (long long)(2 * d + s2) * cap + a);
+    if (a >= 0) return __ldcg(link + (long long)a * LROW<N> + 2 * d + s2);
     int b = L[2 * d + s2];
-    if (b >= 0) return __ldcg(link + (long long)(2 * j + s1) * cap + b);
+    if (b >= 0) return __ldcg(link + (long long)b * LROW<N> + 2 * j + s1);
     return -2;
+}
+
+// The 2n links of entry c (one row, loaded as 16-byte vectors where it can).
+template <int N>
+__device__ __forceinline__ void load_links(const int* link, long long c, int* L) {
+    const int* row = link + c * LROW<N>;
+    if constexpr (LROW<N> >= 4) {
+#pragma unroll
+        for (int q = 0; q < (2 * N + 3) / 4; ++q) {
+            const int4 v = *reinterpret_cast<const int4*>(row + 4 * q);
+            if (4 * q + 0 < 2 * N) L[4 * q + 0] = v.x;
+            if (4 * q + 1 < 2 * N) L[4 * q + 1] = v.y;
+            if (4 * q + 2 < 2 * N) L[4 * q + 2] = v.z;
+            if (4 * q + 3 < 2 * N) L[4 * q + 3] = v.w;
+        }
+    } else {
+        const int2 v = *reinterpret_cast<const int2*>(row);
+        L[0] = v.x;
+        L[1] = v.y;
+    }
 }
 
 // Insert cell c (key k) into the table; the key must be new. slots[c]
@@ -184,11 +205,16 @@ __device__ __forceinline__ long long insert_cell(const Model& m, const Bufs& b, 
 // neighbour c + s1 e_j + s2 e_l is found through the link of the face
 // neighbour c + s1 e_j. A halo cell found there becomes active (listed in map
 // for the halo phase); a missing one is inserted as active. A cell whose
-// downwind set was made active since the last prune is skipped. Returns the
-// largest CFL rate of the halo cells this thread activated (inserted cells get
-// theirs in the link phase).
+// downwind set was made active since the last prune is skipped.
+//
+// The candidates of a cell (2n faces, 4 C(n,2) edges, those that are not
+// downwind skipped at once) are independent chains of dependent loads and
+// atomics; the (cell, candidate) pairs of the qualifying cells of a warp are
+// spread over its lanes. Returns the largest CFL rate of the halo cells this
+// thread activated (inserted cells get theirs in the link phase).
 template <int N, typename T>
 __device__ __forceinline__ double grow_body(const Model& m, const Bufs& b, const StepView& v) {
+    constexpr int K = 2 * N + 2 * N * (N - 1);  // candidates per cell
     DevScalars* sc = b.sc;
     const long long ncell = v.N_prev;
     const double pstar = m.thr_rel * v.maxq;
@@ -197,6 +223,9 @@ __device__ __forceinline__ double grow_body(const Model& m, const Bufs& b, const
     const int* link = b.link[v.g];
     unsigned short* om = b.om[v.g];
     const long long cap = m.cap;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __shared__ long long s_cell[WARPS][32];
+    __shared__ unsigned s_out[WARPS][32];
     double rmax = 0.0;
     auto make_active = [&](long long e) {
         if (!(om[e] & OM_GHOST) || !activate(om, e)) return;
@@ -213,53 +242,65 @@ __device__ __forceinline__ double grow_body(const Model& m, const Bufs& b, const
         }
         if (insert_cell<N, T>(m, b, v, J, 0, &sc->N, 0) >= 0) warp_aggregated_add(&sc->NA);
     };
+    // candidate k of cell cc with downwind directions out
+    auto candidate = [&](long long cc, unsigned out, int k) {
+        int d1, d2 = -1;
+        if (k < 2 * N) {
+            d1 = k;
+        } else {
+            const int e = k - 2 * N;
+            int rem = e >> 2, j = 0;
+            while (rem >= N - 1 - j) {
+                rem -= N - 1 - j;
+                ++j;
+            }
+            d1 = 2 * j + (e & 1);
+            d2 = 2 * (j + 1 + rem) + ((e >> 1) & 1);
+        }
+        if (!((out >> d1) & 1u) || (d2 >= 0 && !((out >> d2) & 1u))) return;
+        const int a = link[(long long)cc * LROW<N> + d1];
+        long long e;
+        if (d2 < 0) {
+            e = a;
+        } else if (a >= 0) {
+            e = link[(long long)a * LROW<N> + d2];
+        } else {
+            const int a2 = link[(long long)cc * LROW<N> + d2];
+            e = a2 >= 0 ? link[(long long)a2 * LROW<N> + d1] : -1;
+        }
+        if (e >= 0) {
+            make_active(e);
+            return;
+        }
+        int J[N];
+        unpack_key<N>(m, key[cc], J);
+        J[d1 >> 1] += (d1 & 1) ? 1 : -1;
+        if (d2 >= 0) J[d2 >> 1] += (d2 & 1) ? 1 : -1;
+        insert_active(J);
+    };
     for (WarpRuns r(ncell); r.next();) {
         const long long c = r.c;
-        if (c >= ncell) continue;
-        if (!((double)Q[c] > pstar)) continue;
-        const unsigned f = om[c];
-        if (f & (OM_COMPLETE | OM_GHOST)) continue;
-        const unsigned out = f & 0xfffu;
-        if (out) {
-            int I[N];
-            unpack_key<N>(m, key[c], I);
-            int L[2 * N];
-#pragma unroll
-            for (int d = 0; d < 2 * N; ++d) L[d] = link[(long long)d * cap + c];
-#pragma unroll
-            for (int d = 0; d < 2 * N; ++d) {
-                if (!((out >> d) & 1u)) continue;
-                if (L[d] >= 0) {
-                    make_active(L[d]);
-                } else {
-                    int J[N];
-#pragma unroll
-                    for (int k = 0; k < N; ++k) J[k] = I[k];
-                    J[d >> 1] += (d & 1) ? 1 : -1;
-                    insert_active(J);
-                }
-            }
-#pragma unroll
-            for (int d1 = 0; d1 < 2 * N; ++d1) {
-                if (!((out >> d1) & 1u)) continue;
-#pragma unroll
-                for (int d2 = 0; d2 < 2 * N; ++d2) {
-                    if ((d2 >> 1) <= (d1 >> 1) || !((out >> d2) & 1u)) continue;
-                    const int e = edge_by_links(link, cap, L, d1 >> 1, d1 & 1, d2 >> 1, d2 & 1);
-                    if (e >= 0) {
-                        make_active(e);
-                    } else {
-                        int J[N];
-#pragma unroll
-                        for (int k = 0; k < N; ++k) J[k] = I[k];
-                        J[d1 >> 1] += (d1 & 1) ? 1 : -1;
-                        J[d2 >> 1] += (d2 & 1) ? 1 : -1;
-                        insert_active(J);
-                    }
-                }
-            }
+        unsigned f = 0;
+        bool q = false;
+        if (c < ncell && (double)Q[c] > pstar) {
+            f = om[c];
+            q = !(f & (OM_COMPLETE | OM_GHOST)) && (f & 0xfffu);
         }
-        om[c] = (unsigned short)(f | OM_COMPLETE);
+        const unsigned qm = __ballot_sync(0xffffffffu, q);
+        if (!qm) continue;
+        if (q) {
+            const int pos = __popc(qm & ((1u << lane) - 1u));
+            s_cell[wid][pos] = c;
+            s_out[wid][pos] = f & 0xfffu;
+        }
+        __syncwarp();
+        const int pairs = __popc(qm) * K;
+        for (int t = lane; t < pairs; t += 32) {
+            const int rank = t / K;
+            candidate(s_cell[wid][rank], s_out[wid][rank], t - rank * K);
+        }
+        __syncwarp();
+        if (q) om[c] = (unsigned short)(f | OM_COMPLETE);
     }
     return rmax;
 }
@@ -289,7 +330,7 @@ __device__ __forceinline__ void halo_body(const Model& m, const Bufs& b, const S
             x = lo + q;
         } else {
             x = b.map[q - ni];
-            if (link[(long long)d * cap + x] >= 0) continue;
+            if (link[(long long)x * LROW<N> + d] >= 0) continue;
         }
         int I[N];
         unpack_key<N>(m, key[x], I);
@@ -339,8 +380,8 @@ __device__ __forceinline__ double link_body(const Model& m, const Bufs& b, long 
         I[j] += s ? 1 : -1;
         unsigned long long k;
         int nb = pack_key<N>(m, I, k) ? table_find(m, b.table, k) : -1;
-        link[(long long)dir * cap + c] = nb;
-        if (nb >= 0) link[(long long)(2 * j + (1 - s)) * cap + nb] = (int)c;
+        link[(long long)c * LROW<N> + dir] = nb;
+        if (nb >= 0) link[(long long)nb * LROW<N> + (2 * j + (1 - s))] = (int)c;
     }
     return link_masks<N>(m, b, lo, hi, g);
 }
@@ -365,14 +406,14 @@ __device__ __forceinline__ double link_body_tile(const Model& m, const Bufs& b, 
         unsigned long long k;
         int nb = pack_key<N>(m, I, k) ? table_find_tile<W>(m, b.table, k, tile) : -1;
         if (tile.thread_rank() == 0) {
-            link[(long long)dir * cap + c] = nb;
-            if (nb >= 0) link[(long long)(2 * j + (1 - s)) * cap + nb] = (int)c;
+            link[(long long)c * LROW<N> + dir] = nb;
+            if (nb >= 0) link[(long long)nb * LROW<N> + (2 * j + (1 - s))] = (int)c;
         }
     }
     return link_masks<N>(m, b, lo, hi, g);
 }
 
-// ------------------------------------------------------------------ FP64 three-pass update
+// ------------------------------------------------------------------ three-pass update
 
 template <typename T>
 __device__ __forceinline__ T q_or_zero(const T* Q, int i) {
@@ -381,20 +422,42 @@ __device__ __forceinline__ T q_or_zero(const T* Q, int i) {
 
 __device__ __forceinline__ bool is_halo(const unsigned short* om, long long i) { return (om[i] & OM_GHOST) != 0; }
 
+// Cell widths, origin and step coefficients in the arithmetic type T (float
+// copies for the FP32 mode, so that nothing converts per use).
+template <int N, typename T>
+struct Geo {
+    T h[N], x0[N], ch[N], dth[N];
+    __device__ __forceinline__ Geo(const Model& m, const StepView& v) {
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            h[k] = sizeof(T) == 4 ? (T)m.hf[k] : (T)m.h[k];
+            x0[k] = sizeof(T) == 4 ? (T)m.x0f[k] : (T)m.x0[k];
+            ch[k] = (T)v.ch[k];
+            dth[k] = (T)v.dth[k];
+        }
+    }
+    __device__ __forceinline__ void centre(const int* I, T* xc) const {
+#pragma unroll
+        for (int k = 0; k < N; ++k) xc[k] = x0[k] + (T)I[k] * h[k];
+    }
+};
+
 // Pass 1, one work item per (entry, dimension d) of the entries [0, ncell)
-// (active and halo): the lower-face velocity u_d and the entering wave G_d.
-// Entries added by this step's grow and halo phases are left out: their waves
-// are formed on the spot (waves_of).
-template <int N, int DYN>
+// (active and halo): the lower-face velocity u_d and the entering wave
+//   G_d = max(u_d, 0) (P - P_{-e_d}) + min(u_{d, upper}, 0) (P_{+e_d} - P).
+// Entries added by this step's grow and halo phases are left out: they have
+// p = 0, and their waves are formed on the spot (waves_of). Runs beside grow:
+// a cell that grow or halo adds has p = 0 like the missing cell it replaces,
+// so these waves do not change.
+template <int N, int DYN, typename T>
 __device__ __forceinline__ void waves_body(const Model& m, const Bufs& b, const StepView& v, long long ncell) {
-    const double* Q = static_cast<const double*>(b.q[v.pb]);
+    const T* Q = static_cast<const T*>(b.q[v.pb]);
     const unsigned long long* key = b.key[v.g];
     const int* link = b.link[v.g];
-    const long long cap = m.cap;
+    T* wu = static_cast<T*>(b.wv_u);
+    T* wg = static_cast<T*>(b.wv_g);
+    const Geo<N, T> geo(m, v);
     const long long items = ncell * N;
-    double h[N];
-#pragma unroll
-    for (int k = 0; k < N; ++k) h[k] = m.h[k];
     for (WarpRuns wr(items); wr.next();) {
         const long long it = wr.c;
         if (it >= items) continue;
@@ -402,292 +465,165 @@ __device__ __forceinline__ void waves_body(const Model& m, const Bufs& b, const 
         const int d = (int)(it - c * N);
         int I[N];
         unpack_key<N>(m, key[c], I);
-        const double P0 = Q[c];
-        const double Pm = q_or_zero<double>(Q, link[(long long)(2 * d) * cap + c]);
-        const double Pp = q_or_zero<double>(Q, link[(long long)(2 * d + 1) * cap + c]);
-        double xc[N];
-#pragma unroll
-        for (int k = 0; k < N; ++k) xc[k] = m.x0[k] + (double)I[k] * h[k];
-        double ul = 0.0, uh = 0.0;
+        const T P0 = Q[c];
+        const T Pm = q_or_zero<T>(Q, link[c * LROW<N> + 2 * d]);
+        const T Pp = q_or_zero<T>(Q, link[c * LROW<N> + 2 * d + 1]);
+        T xc[N];
+        geo.centre(I, xc);
+        T ul = (T)0, uh = (T)0;
 #pragma unroll
         for (int dd = 0; dd < N; ++dd)
             if (dd == d) {
-                ul = vel_at<N, DYN, double>(m, xc, h, -1, 0, dd, -1);
-                uh = vel_at<N, DYN, double>(m, xc, h, -1, 0, dd, +1);
+                ul = vel_at<N, DYN, T>(m, xc, geo.h, -1, 0, dd, -1);
+                uh = vel_at<N, DYN, T>(m, xc, geo.h, -1, 0, dd, +1);
             }
-        b.wv_u[(long long)d * cap + c] = ul;
-        b.wv_g[(long long)d * cap + c] = fmax(ul, 0.0) * (P0 - Pm) + fmin(uh, 0.0) * (Pp - P0);
+        wu[c * WROW<N> + d] = ul;
+        wg[c * WROW<N> + d] = fmax(ul, (T)0) * (P0 - Pm) + fmin(uh, (T)0) * (Pp - P0);
     }
 }
 
 // sum_{d != j} dt/(2 h_d) G_d(Y) for the pool entry y = Y = c + s e_j (s = -1
 // or 0; xc is the centre of c), formed on the spot from Y's links; 0 when Y is
 // not in the pool (a cell without a key: it and its neighbours have p = 0).
-template <int N, int DYN>
-__device__ __forceinline__ double waves_of(const Model& m, const double* Q, const int* link, long long cap,
-                                           long long y, const double* xc, const double* h, const double* ch, int j,
-                                           int s) {
-    if (y < 0) return 0.0;
-    const double PY = Q[y];
-    double S = 0.0;
+template <int N, int DYN, typename T>
+__device__ __forceinline__ T waves_of(const Model& m, const T* Q, const int* link, long long y, const T* xc,
+                                      const Geo<N, T>& geo, int j, int s) {
+    if (y < 0) return (T)0;
+    const T PY = Q[y];
+    T S = (T)0;
 #pragma unroll
     for (int d = 0; d < N; ++d) {
         if (d == j) continue;
-        const double Pm = q_or_zero<double>(Q, link[(long long)(2 * d) * cap + y]);
-        const double Pp = q_or_zero<double>(Q, link[(long long)(2 * d + 1) * cap + y]);
-        const double ul = vel_at<N, DYN, double>(m, xc, h, s ? j : -1, s, d, -1);
-        const double uh = vel_at<N, DYN, double>(m, xc, h, s ? j : -1, s, d, +1);
-        S += ch[d] * (fmax(ul, 0.0) * (PY - Pm) + fmin(uh, 0.0) * (Pp - PY));
+        const T Pm = q_or_zero<T>(Q, link[y * LROW<N> + 2 * d]);
+        const T Pp = q_or_zero<T>(Q, link[y * LROW<N> + 2 * d + 1]);
+        const T ul = vel_at<N, DYN, T>(m, xc, geo.h, s ? j : -1, s, d, -1);
+        const T uh = vel_at<N, DYN, T>(m, xc, geo.h, s ? j : -1, s, d, +1);
+        S += geo.ch[d] * (fmax(ul, (T)0) * (PY - Pm) + fmin(uh, (T)0) * (Pp - PY));
     }
     return S;
 }
 
 // Pass 2, one work item per (entry c, dimension j): the flux through the lower
-// j-face of c (Eq. 7, the gathered corrections of Algorithm 1, the limited HR
-// term), for every face with an active cell on at least one side. The upper
-// face of an active cell is the lower face of its upper neighbour, which is in
-// the pool (active or halo).
-template <int N, int DYN>
+// j-face of c (Eq. 7, the corrections of Algorithm 1 gathered onto the face,
+// the limited HR term), for every face with an active cell on at least one
+// side. The corrections that Algorithm 1 scatters onto face (X, j) add up to
+//   -u_j(X) sum_{d != j} dt/(2 h_d) G_d(Y),  Y the cell upwind of the face.
+// The upper face of an active cell is the lower face of its upper neighbour,
+// which is in the pool (active or halo).
+template <int N, int DYN, typename T>
 __device__ __forceinline__ void faces_body(const Model& m, const Bufs& b, const StepView& v) {
     const long long ncell = v.N;
     const long long nold = v.N_prev;
-    const double* Q = static_cast<const double*>(b.q[v.pb]);
+    const T* Q = static_cast<const T*>(b.q[v.pb]);
     const unsigned long long* key = b.key[v.g];
     const int* link = b.link[v.g];
     const unsigned short* om = b.om[v.g];
-    const double* wu = b.wv_u;
-    const double* wg = b.wv_g;
-    const long long cap = m.cap;
+    const T* wu = static_cast<const T*>(b.wv_u);
+    const T* wg = static_cast<const T*>(b.wv_g);
+    T* fl = static_cast<T*>(b.fl);
     const int lim = m.limiter;
-    double h[N];
-#pragma unroll
-    for (int k = 0; k < N; ++k) h[k] = m.h[k];
+    const Geo<N, T> geo(m, v);
     const long long items = ncell * N;
     for (WarpRuns wr(items); wr.next();) {
         const long long it = wr.c;
         if (it >= items) continue;
         const long long c = it / N;
         const int j = (int)(it - c * N);
-        const int Llo = link[(long long)(2 * j) * cap + c];
+        const int Llo = link[c * LROW<N> + 2 * j];
         if (is_halo(om, c) && (Llo < 0 || is_halo(om, Llo))) continue;  // no active cell on this face
-        const double P0 = Q[c];
-        const double PL = q_or_zero<double>(Q, Llo);
-        const double dthj = v.dth[j];
-        int I[N];
-        double xc[N];
+        const T P0 = Q[c];
+        const T PL = q_or_zero<T>(Q, Llo);
+        T dthj = (T)0;
+#pragma unroll
+        for (int k = 0; k < N; ++k)
+            if (k == j) dthj = geo.dth[k];
+        T xc[N];
         bool have_pos = false;
         auto pos = [&]() {
             if (!have_pos) {
+                int I[N];
                 unpack_key<N>(m, key[c], I);
-#pragma unroll
-                for (int k = 0; k < N; ++k) xc[k] = m.x0[k] + (double)I[k] * h[k];
+                geo.centre(I, xc);
                 have_pos = true;
             }
         };
-        double u = 0.0;
+        T u = (T)0;
         if (c < nold) {
-            u = wu[(long long)j * cap + c];
+            u = wu[c * WROW<N> + j];
         } else {
             pos();
 #pragma unroll
             for (int dd = 0; dd < N; ++dd)
-                if (dd == j) u = vel_at<N, DYN, double>(m, xc, h, -1, 0, dd, -1);
+                if (dd == j) u = vel_at<N, DYN, T>(m, xc, geo.h, -1, 0, dd, -1);
         }
-        double f = 0.0;
-        if (u != 0.0) {
-            f = fmax(u, 0.0) * PL + fmin(u, 0.0) * P0;  // Eq. 7
+        T f = (T)0;
+        if (u != (T)0) {
+            f = fmax(u, (T)0) * PL + fmin(u, (T)0) * P0;  // Eq. 7
             // transverse sum of the cell upwind of the face
-            const long long y = u > 0.0 ? (long long)Llo : c;
-            double S = 0.0;
+            const long long y = u > (T)0 ? (long long)Llo : c;
+            T S = (T)0;
             if (y >= 0 && y < nold) {
 #pragma unroll
                 for (int d = 0; d < N; ++d)
-                    if (d != j) S += v.ch[d] * wg[(long long)d * cap + y];
+                    if (d != j) S += geo.ch[d] * wg[y * WROW<N> + d];
             } else {
                 pos();
-                S = waves_of<N, DYN>(m, Q, link, cap, y, xc, h, v.ch, j, u > 0.0 ? -1 : 0);
+                S = waves_of<N, DYN, T>(m, Q, link, y, xc, geo, j, u > (T)0 ? -1 : 0);
             }
             f -= u * S;  // Algorithm 1, gathered
-            const double W = P0 - PL;
-            if (lim != LIM_NONE && W != 0.0) {
-                double Wup;
-                if (u > 0.0) {
-                    Wup = PL - q_or_zero<double>(Q, Llo >= 0 ? link[(long long)(2 * j) * cap + Llo] : -1);
+            const T W = P0 - PL;
+            if (lim != LIM_NONE && W != (T)0) {
+                T Wup;
+                if (u > (T)0) {
+                    Wup = PL - q_or_zero<T>(Q, Llo >= 0 ? link[(long long)Llo * LROW<N> + 2 * j] : -1);
                 } else {
-                    Wup = q_or_zero<double>(Q, link[(long long)(2 * j + 1) * cap + c]) - P0;
+                    Wup = q_or_zero<T>(Q, link[c * LROW<N> + 2 * j + 1]) - P0;
                 }
-                const double au = fabs(u);
-                f += 0.5 * au * (1.0 - dthj * au) * limited_wave<double>(lim, W, Wup);
+                const T au = fabs(u);
+                f += (T)0.5 * au * ((T)1 - dthj * au) * limited_wave<T>(lim, W, Wup);
             }
         }
-        b.fl[(long long)j * cap + c] = f;
+        fl[c * WROW<N> + j] = f;
     }
 }
 
 // Pass 3: the conservative update of the active cells with the previous
 // normalisation applied (halo cells stay 0); adds this thread's new values to
 // its digits and maximum.
-template <int N>
+template <int N, typename T>
 __device__ __forceinline__ void apply_body(const Model& m, const Bufs& b, const StepView& v, long long (&dacc)[NDIG],
                                            double& mx, int& err) {
     const long long ncell = v.N;
-    const double* Q = static_cast<const double*>(b.q[v.pb]);
-    double* Qn = static_cast<double*>(b.q[v.pb ^ 1]);
+    const T* Q = static_cast<const T*>(b.q[v.pb]);
+    T* Qn = static_cast<T*>(b.q[v.pb ^ 1]);
     const int* link = b.link[v.g];
     const unsigned short* om = b.om[v.g];
-    const double* fl = b.fl;
-    const long long cap = m.cap;
-    const double scale = v.scale;
+    const T* fl = static_cast<const T*>(b.fl);
+    const T scale = (T)v.scale;
+    T dth[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) dth[k] = (T)v.dth[k];
+    T tmax = -INFINITY;
     for (WarpRuns wr(ncell); wr.next();) {
         const long long c = wr.c;
         if (c >= ncell) continue;
         if (is_halo(om, c)) {
-            Qn[c] = 0.0;
+            Qn[c] = (T)0;
             continue;
         }
-        double upd = 0.0;
+        int L[2 * N];
+        load_links<N>(link, c, L);
+        T upd = (T)0;
 #pragma unroll
         for (int j = 0; j < N; ++j) {
-            const int up = link[(long long)(2 * j + 1) * cap + c];
-            const double Fhi = up >= 0 ? fl[(long long)j * cap + up] : 0.0;
-            upd += v.dth[j] * (Fhi - fl[(long long)j * cap + c]);
+            const int up = L[2 * j + 1];
+            const T Fhi = up >= 0 ? fl[(long long)up * WROW<N> + j] : (T)0;
+            upd += dth[j] * (Fhi - fl[c * WROW<N> + j]);
         }
-        const double qn = (Q[c] - upd) * scale;
+        const T qn = (Q[c] - upd) * scale;
         Qn[c] = qn;
         acc_add(dacc, qn, err);
-        mx = fmax(mx, qn);
-    }
-}
-
-// ------------------------------------------------------------------ single-pass update, one lane per face
-
-// Every active cell computes its 2n face fluxes from its own neighbourhood. The
-// corrections that Algorithm 1 scatters onto face (X, j) add up to
-//   -u_j(X) sum_{d != j} dt/(2 h_d) G_d(Y),  Y the cell upwind of the face,
-//   G_d(Y) = max(u_d(Y), 0) (P_Y - P_{Y-e_d}) + min(u_d(Y+e_d), 0) (P_{Y+e_d} - P_Y),
-// so each cell needs its face neighbours, the transverse neighbours of each
-// upwind face neighbour (through that neighbour's links), and one cell two
-// steps away per dimension (limiter). The 2n faces of a cell are spread over a
-// group of G lanes (G = 8 for n <= 4, 16 for n = 5, 6; lane 2j + s owns the
-// lower (s = 0) or upper (s = 1) j-face); the cell's own waves and the update
-// are combined with shuffles inside the group.
-template <int N, int DYN, typename T>
-__device__ __forceinline__ void gather_faces_body(const Model& m, const Bufs& b, const StepView& v,
-                                                  long long (&dacc)[NDIG], double& mx, int& err) {
-    constexpr int G = (2 * N <= 8) ? 8 : 16;
-    const long long ncell = v.N;
-    const T* Q = static_cast<const T*>(b.q[v.pb]);
-    T* Qn = static_cast<T*>(b.q[v.pb ^ 1]);
-    const unsigned long long* key = b.key[v.g];
-    const int* link = b.link[v.g];
-    const unsigned short* om = b.om[v.g];
-    const long long cap = m.cap;
-    const int lim = m.limiter;
-    const T scale = (T)v.scale;
-    T h[N], x0[N], chT[N], dthT[N];
-#pragma unroll
-    for (int k = 0; k < N; ++k) {
-        h[k] = sizeof(T) == 4 ? (T)m.hf[k] : (T)m.h[k];
-        x0[k] = sizeof(T) == 4 ? (T)m.x0f[k] : (T)m.x0[k];
-        chT[k] = (T)v.ch[k];
-        dthT[k] = (T)v.dth[k];
-    }
-    T tmax = -INFINITY;
-    const long long items = ncell * G;
-    const unsigned full = 0xffffffffu;
-    for (WarpRuns wr(items); wr.next();) {
-        // every lane of the warp takes part in the shuffles below
-        const long long it = wr.c;
-        const long long c = it / G;
-        const int l = (int)(it % G);
-        const bool cell_ok = c < ncell;
-        const bool active = cell_ok && !is_halo(om, c);
-        const bool face_ok = active && l < 2 * N;
-        const int j = face_ok ? (l >> 1) : 0;
-        const int side = l & 1;
-        T P0 = (T)0, Pn = (T)0, u = (T)0;
-        int Ls = -1;
-        T xc[N];
-        if (active) {
-            P0 = Q[c];
-            int I[N];
-            unpack_key<N>(m, key[c], I);
-#pragma unroll
-            for (int k = 0; k < N; ++k) xc[k] = x0[k] + (T)I[k] * h[k];
-        }
-        if (face_ok) {
-            Ls = link[(long long)(2 * j + side) * cap + c];
-            Pn = q_or_zero<T>(Q, Ls);
-#pragma unroll
-            for (int d = 0; d < N; ++d)
-                if (d == j) u = vel_at<N, DYN, T>(m, xc, h, -1, 0, d, side ? +1 : -1);
-        }
-        // the partner lane holds the other face of the same dimension
-        const T u_o = __shfl_xor_sync(full, u, 1, G);
-        const T Pn_o = __shfl_xor_sync(full, Pn, 1, G);
-        const T ulo = side ? u_o : u, uhi = side ? u : u_o;
-        const T Plo = side ? Pn_o : Pn, Phi = side ? Pn : Pn_o;
-        // G_j(c), the j-waves entering c; and sum over d of dt/(2 h_d) G_d(c)
-        const T Gj = face_ok ? fmax(ulo, (T)0) * (P0 - Plo) + fmin(uhi, (T)0) * (Phi - P0) : (T)0;
-        T chj = (T)0, dthj = (T)0;
-#pragma unroll
-        for (int k = 0; k < N; ++k)
-            if (k == j && face_ok) {
-                chj = chT[k];
-                dthj = dthT[k];
-            }
-        T tot = (side == 0) ? chj * Gj : (T)0;
-#pragma unroll
-        for (int off = G / 2; off > 0; off >>= 1) tot += __shfl_xor_sync(full, tot, off, G);
-        T contrib = (T)0;
-        if (face_ok) {
-            const T PL = side ? P0 : Pn;
-            const T PR = side ? Pn : P0;
-            T f = (T)0;
-            if (u != (T)0) {
-                f = fmax(u, (T)0) * PL + fmin(u, (T)0) * PR;  // Eq. 7
-                const bool upwind_is_c = side ? (u > (T)0) : (u < (T)0);
-                T S = (T)0;
-                if (upwind_is_c) {
-                    S = tot - chj * Gj;
-                } else if (Ls >= 0) {  // through the links of the neighbour across this face
-                    const int sgn = side ? 1 : -1;
-#pragma unroll
-                    for (int d = 0; d < N; ++d) {
-                        if (d == j) continue;
-                        const T Pm = q_or_zero<T>(Q, link[(long long)(2 * d) * cap + Ls]);
-                        const T Pp = q_or_zero<T>(Q, link[(long long)(2 * d + 1) * cap + Ls]);
-                        const T ul = vel_at<N, DYN, T>(m, xc, h, j, sgn, d, -1);
-                        const T uh = vel_at<N, DYN, T>(m, xc, h, j, sgn, d, +1);
-                        S += chT[d] * (fmax(ul, (T)0) * (Pn - Pm) + fmin(uh, (T)0) * (Pp - Pn));
-                    }
-                }
-                f -= u * S;  // Algorithm 1
-                const T W = PR - PL;
-                if (lim != LIM_NONE && W != (T)0) {
-                    // value two cells away across this face
-                    const T P2 = Ls >= 0 ? q_or_zero<T>(Q, link[(long long)(2 * j + side) * cap + Ls]) : (T)0;
-                    T Wup;
-                    if (u > (T)0) Wup = side ? (P0 - Plo) : (Plo - P2);
-                    else Wup = side ? (P2 - Phi) : (Phi - P0);
-                    const T au = fabs(u);
-                    f += (T)0.5 * au * ((T)1 - dthj * au) * limited_wave<T>(lim, W, Wup);
-                }
-            }
-            contrib = (side ? (T)1 : (T)-1) * dthj * f;
-        }
-#pragma unroll
-        for (int off = G / 2; off > 0; off >>= 1) contrib += __shfl_xor_sync(full, contrib, off, G);
-        if (cell_ok && l == 0) {
-            if (active) {
-                const T qn = (P0 - contrib) * scale;
-                Qn[c] = qn;
-                acc_add(dacc, qn, err);
-                tmax = fmax(tmax, qn);
-            } else {
-                Qn[c] = (T)0;
-            }
-        }
+        tmax = fmax(tmax, qn);
     }
     if (tmax > -INFINITY) mx = fmax(mx, (double)tmax);
 }
@@ -723,8 +659,7 @@ __device__ __forceinline__ void prune_scatter_body(const Model& m, const Bufs& b
         const unsigned out = f & 0xfffu;
         if (!out) continue;
         int L[2 * N];
-#pragma unroll
-        for (int d = 0; d < 2 * N; ++d) L[d] = link[(long long)d * cap + c];
+        load_links<N>(link, c, L);
 #pragma unroll
         for (int d = 0; d < 2 * N; ++d)
             if (((out >> d) & 1u) && L[d] >= 0) b.keep[L[d]] = 1;
@@ -734,7 +669,7 @@ __device__ __forceinline__ void prune_scatter_body(const Model& m, const Bufs& b
 #pragma unroll
             for (int d2 = 0; d2 < 2 * N; ++d2) {
                 if ((d2 >> 1) <= (d1 >> 1) || !((out >> d2) & 1u)) continue;
-                const int e = edge_by_links(link, cap, L, d1 >> 1, d1 & 1, d2 >> 1, d2 & 1);
+                const int e = edge_by_links<N>(link, L, d1 >> 1, d1 & 1, d2 >> 1, d2 & 1);
                 if (e >= 0) b.keep[e] = 1;
             }
         }
@@ -778,11 +713,11 @@ __device__ __forceinline__ void prune_count_body(const Model& m, const Bufs& b, 
         if (b.keep[c] && !is_halo(om, c)) {
             st = 1;
         } else {
+            int L[2 * N];
+            load_links<N>(link, c, L);
 #pragma unroll
-            for (int d = 0; d < 2 * N; ++d) {
-                const int l = link[(long long)d * cap + c];
-                if (l >= 0 && b.keep[l] && !is_halo(om, l)) st = 2;
-            }
+            for (int d = 0; d < 2 * N; ++d)
+                if (L[d] >= 0 && b.keep[L[d]] && !is_halo(om, L[d])) st = 2;
         }
         b.map[c] = st;
         na += st == 1;
@@ -904,11 +839,10 @@ __device__ __forceinline__ void prune_relink_body(const Model& m, const Bufs& b,
         if (c >= v.N) continue;
         const int nc = b.map[c];
         if (nc < 0) continue;
+        int L[2 * N];
+        load_links<N>(link, c, L);
 #pragma unroll
-        for (int d = 0; d < 2 * N; ++d) {
-            int l = link[(long long)d * cap + c];
-            linko[(long long)d * cap + nc] = l >= 0 ? b.map[l] : -1;
-        }
+        for (int d = 0; d < 2 * N; ++d) linko[(long long)nc * LROW<N> + d] = L[d] >= 0 ? b.map[L[d]] : -1;
         table_insert_new(m, b, keyo[nc], nc, b.slot[v.g ^ 1]);
     }
 }

@@ -2,7 +2,7 @@
 // kernel for one precision and one family of drift models. The build compiles
 // this file once per (GBEES_PREC, GBEES_FAMILY) pair so that the instantiations
 // compile in parallel:
-//   GBEES_PREC   64 (three-pass FP64 update) or 32 (single-pass gather, FP32)
+//   GBEES_PREC   64 (FP64) or 32 (FP32 storage and fluxes)
 //   GBEES_FAMILY 0 Lorenz '63 (both forms), 1 Lorenz '96 (n = 4..6),
 //                2 linear n = 1..3, 3 linear n = 4..6, 4 constant n = 1..3,
 //                5 constant n = 4..6
@@ -28,18 +28,12 @@ using Real = float;
 template <int N, int DYN>
 static void kernels_of(Kernels* k) {
     k->persist = (void*)k_persistent<N, DYN, Real>;
-#if GBEES_PREC == 64
-    k->pre[0] = (void*)k_grow_waves<N, DYN>;
-    k->post[0] = (void*)k_faces<N, DYN>;
-    k->post[1] = (void*)k_apply<N>;
-    k->npost = 2;
-#else
-    k->pre[0] = (void*)k_grow<N, Real>;
-    k->post[0] = (void*)k_ctu<N, DYN, Real>;
-    k->npost = 1;
-#endif
+    k->pre[0] = (void*)k_grow_waves<N, DYN, Real>;
     k->pre[1] = (void*)k_halo<N, Real, 1>;
     k->npre = 2;
+    k->post[0] = (void*)k_faces<N, DYN, Real>;
+    k->post[1] = (void*)k_apply<N, Real>;
+    k->npost = 2;
 }
 
 #define GBEES_JOIN2(a, b) a##b
