@@ -35,11 +35,13 @@ sys.path.insert(0, ROOT)
 METRIC = "cell-updates/s"
 DEFAULT_WORKLOAD = "lorenz63_h0.25"
 
-# DRAM traffic of one update-kernel launch per cell, from an ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum divided by the cells the launch
-# updated); valid only while the kernel source has the recorded hash.
+# DRAM traffic per cell update of the roofline kernel, from an ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum of the launch divided by the
+# cell updates it made), keyed by workload/precision; valid only while the
+# device sources have the recorded hash (null otherwise).
 TRAFFIC_BYTES_PER_CELL = {}
-CTU_SOURCE = os.path.join(ROOT, "paper_2508_13986_gb300", "csrc", "gbees_ctu.cuh")
+DEVICE_SOURCES = [os.path.join(ROOT, "paper_2508_13986_gb300", "csrc", f)
+                  for f in ("gbees_device.cuh", "gbees_phases.cuh", "gbees_kernels.cuh", "gbees_persistent.cuh")]
 
 
 def parse():
@@ -51,9 +53,12 @@ def parse():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--precision", choices=["f64", "f32"], default="f64")
     ap.add_argument("--no-secondary", action="store_true", help="skip the other precision's line")
-    ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
+    ap.add_argument("--cpu-budget", type=float, default=12.0,
+                    help="seconds of oracle work for cpu_baseline (0: skip, for grids the oracle cannot initialise quickly)")
     ap.add_argument("--max-cells", type=int, default=1 << 22)
     ap.add_argument("--launch-mode", choices=["auto", "persistent", "graph", "direct"], default="auto")
+    ap.add_argument("--t-end", type=float, default=None,
+                    help="stop the workload at this time (large-grid runs); the default is its own t_end")
     return ap.parse_args()
 
 
@@ -154,11 +159,13 @@ def run_workload(grid, w, with_readout=False):
 
 
 def bytes_per_update(n: int, precision: str) -> int:
-    """Algorithmic HBM bytes of the update kernel per cell: the packed key (8),
-    the cell's own value read and the new value written (2 S) and its 2n
-    neighbour links (8 n); neighbour values are L2 hits in key order."""
+    """Algorithmic HBM bytes of one cell update (one active cell advanced one
+    step, grow included): the update pass reads the packed key (8), the value
+    (S) and the 2n int32 links (8 n) and writes the new value (S); the grow
+    scan reads the value and the links again (S + 8 n). Neighbour values are
+    L2 hits. B = 8 + 3 S + 16 n."""
     S = 8 if precision == "f64" else 4
-    return 8 + 2 * S + 8 * n
+    return 8 + 3 * S + 16 * n
 
 
 def load_peaks():
@@ -171,9 +178,12 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
-def ctu_source_hash() -> str:
-    with open(CTU_SOURCE, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+def device_source_hash() -> str:
+    h = hashlib.sha256()
+    for path in DEVICE_SOURCES:
+        with open(path, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def time_precision(args, w, precision, dev, rank, world):
@@ -249,17 +259,32 @@ def time_precision(args, w, precision, dev, rank, world):
 
     peak_gbs, peak_src = load_peaks()
     bpc = bytes_per_update(w.n, precision)
-    upd_ms = prof["ms"]["update"]
-    achieved = bpc * prof_updates / (upd_ms / 1e3) / 1e9 if upd_ms > 0 else None
-    launches_upd = max(prof["timed"]["update"], 1)
+    # the dominant kernel of the timed region: the persistent step-loop kernel
+    # when the launch mode used it (its launches are event-timed inside the
+    # library on its stream), otherwise the slowest per-cell step kernel of the
+    # profiled pass (one launch per kernel, events around each)
+    if pt["persist_launches"] and pt["persist_updates"] >= 0.5 * total_updates:
+        kernel = "k_persistent (whole step loop, one cooperative launch per propagate segment)"
+        timing = "CUDA events around every persistent launch on the library stream, timed region"
+        launches_k = pt["persist_launches"]
+        units = pt["persist_updates"]
+        avg_us = pt["persist_ms"] * 1e3 / max(launches_k, 1)
+    else:
+        per_cell = {k: prof["ms"][k] for k in ("grow", "faces", "apply")}
+        top = max(per_cell, key=per_cell.get)
+        kernel = {"grow": "k_grow_waves", "faces": "k_faces", "apply": "k_apply"}[top]
+        timing = "CUDA events around each launch of that kernel in a profiled pass of the same runs"
+        launches_k = max(prof["timed"][top], 1)
+        units = prof_updates
+        avg_us = per_cell[top] * 1e3 / launches_k
+    units_per_launch = units / max(launches_k, 1)
+    achieved = bpc * units_per_launch / (avg_us * 1e-6) / 1e9 if avg_us > 0 else None
     traffic = None
-    key = f"{w.name}/{precision}"
-    rec = TRAFFIC_BYTES_PER_CELL.get(key)
-    if rec and rec.get("src") == ctu_source_hash():
-        traffic = rec["bytes_per_cell"] * prof_updates / launches_upd
+    rec = TRAFFIC_BYTES_PER_CELL.get(f"{w.name}/{precision}")
+    if rec and rec.get("src") == device_source_hash():
+        traffic = rec["bytes_per_cell"] * units_per_launch
     tot_ms = sum(prof["ms"].values())
     phase_share = {k: (v / tot_ms if tot_ms > 0 else 0.0) for k, v in prof["ms"].items()}
-    kernels = "k_faces + k_apply (flux and conservative update)"
     return {
         "value": upd_sum / (ms_max / 1e3),
         "ms_per_step": ms_max / args.steps,
@@ -270,22 +295,21 @@ def time_precision(args, w, precision, dev, rank, world):
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_max / args.steps},
         "roofline": {
             "bound": "hbm",
-            "kernel": kernels,
-            "timing": "CUDA events around each update phase in a profiled pass of the same runs",
+            "kernel": kernel,
+            "timing": timing,
             "achieved": achieved,
             "peak": peak_gbs,
             "peak_source": peak_src,
             "unit": "GB/s",
             "frac": (achieved / peak_gbs) if achieved else None,
             "traffic": traffic,
-            "algorithmic_bytes_per_cell": bpc,
-            "cells_per_launch": prof_updates / launches_upd,
-            "avg_launch_us": upd_ms * 1e3 / launches_upd,
+            "algorithmic_bytes_per_cell_update": bpc,
+            "cell_updates_per_launch": units_per_launch,
+            "avg_launch_us": avg_us,
         },
-        "phase_share": phase_share,
+        "profiled_phase_share": phase_share,
         "persistent_us_per_step": persist_split,
         "gpu_launches": launches,
-        "fallback_lookups": prof["fallback_lookups"],
         "clocks": clk,
     }
 
@@ -351,13 +375,15 @@ def main_ours(args):
 
         dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
     w = workloads.config(args.workload)
+    if args.t_end is not None:
+        w = w.with_(t_end=args.t_end, measurements=[m for m in w.measurements if m.t < args.t_end])
     main = time_precision(args, w, args.precision, local, rank, world)
     other = None
     if not args.no_secondary:
         other_prec = "f32" if args.precision == "f64" else "f64"
         other = time_precision(args, w, other_prec, local, rank, world)
     if rank == 0:
-        cpu = cpu_baseline(w, args.cpu_budget) if world == 1 else None
+        cpu = cpu_baseline(w, args.cpu_budget) if (world == 1 and args.cpu_budget > 0) else None
         line = {
             "metric": METRIC,
             "value": main["value"],
@@ -371,7 +397,7 @@ def main_ours(args):
             "vs_baseline": None,
             "dtype": args.precision,
             "data": "synthetic",
-            "config": {"workload": args.workload, "parallelism": f"replicas{world}",
+            "config": {"workload": args.workload, "t_end": w.t_end, "parallelism": f"replicas{world}",
                        "step": "one whole run: init + propagate/correct to t_end",
                        "l2": "flushed between timed runs (256 MiB write)",
                        "launch_mode": args.launch_mode,
@@ -383,16 +409,15 @@ def main_ours(args):
             "cpu_baseline": cpu,
             "gpu_launches": main["gpu_launches"],
             "clocks": main["clocks"],
-            "phase_share": main["phase_share"],
+            "profiled_phase_share": main["profiled_phase_share"],
             "persistent_us_per_step": main["persistent_us_per_step"],
-            "fallback_lookups": main["fallback_lookups"],
         }
         if other is not None:
             line["other_precision"] = {
                 "dtype": "f32" if args.precision == "f64" else "f64",
                 "value": other["value"], "ms_per_step": other["ms_per_step"], "e2e": other["e2e"],
                 "roofline": other["roofline"], "gpu_launches": other["gpu_launches"], "clocks": other["clocks"],
-                "phase_share": other["phase_share"],
+                "profiled_phase_share": other["profiled_phase_share"],
                 "persistent_us_per_step": other["persistent_us_per_step"]}
         print(json.dumps(line))
     if world > 1:

@@ -191,27 +191,34 @@ int gbees_get_stats(gbees_ctx* ctx, gbees_stats* stats);
  * and its duration is added up; launches counts every kernel the library
  * issues, enabled or not. Phases: */
 enum {
-    GBEES_PHASE_GROW = 0,    /* directional grow (Sec. 3.3) */
-    GBEES_PHASE_LINK = 1,    /* neighbour links of the new cells (Sec. 4.1) */
-    GBEES_PHASE_UPDATE = 2,  /* DCU + CTU + high-resolution update (Eq. 7, Algorithm 1) */
-    GBEES_PHASE_PRUNE = 3,   /* mark, scan, compaction, relink and rehash (Algorithm 3) */
-    GBEES_PHASE_CORRECT = 4, /* Bayesian update (Eq. 4) */
-    GBEES_PHASE_OTHER = 5,   /* init, read-out, moments */
-    GBEES_NPHASES = 6
+    GBEES_PHASE_GROW = 0,    /* directional grow (Sec. 3.3) with the waves of the existing entries */
+    GBEES_PHASE_HALO = 1,    /* halo cells around the newly active cells */
+    GBEES_PHASE_LINK = 2,    /* neighbour links of the new entries, CFL step (Sec. 4.1, Eq. 8) */
+    GBEES_PHASE_FACES = 3,   /* face fluxes: DCU + CTU + high-resolution term (Eq. 7, Algorithm 1) */
+    GBEES_PHASE_APPLY = 4,   /* conservative update, normalisation partials */
+    GBEES_PHASE_PRUNE = 5,   /* mark, scan, compaction, relink and rehash (Algorithm 3) */
+    GBEES_PHASE_CORRECT = 6, /* Bayesian update (Eq. 4) */
+    GBEES_PHASE_OTHER = 7,   /* init, read-out, moments */
+    GBEES_NPHASES = 8
 };
 typedef struct {
     int64_t launches[GBEES_NPHASES]; /* kernel launches per phase since the last reset */
     double ms[GBEES_NPHASES];        /* summed event time per phase (while enabled) */
     int64_t timed[GBEES_NPHASES];    /* launches that were timed */
     int64_t total_launches;          /* all kernel launches since the last reset */
-    int64_t fallback_lookups;        /* edge and second-neighbour lookups that needed the hashtable */
+    int64_t fallback_lookups;        /* hashtable lookups of the flux update (0: every stencil cell is linked) */
     /* persistent kernel (GBEES_LAUNCH_PERSISTENT / AUTO): microseconds that its
      * block 0 spent per phase, measured with the SM clock between grid
-     * barriers -- grow (FP64: with the waves), link, faces (FP64), update
-     * (apply or single-pass), prune, step scalars -- and the steps covered
-     * (accumulated since the last init, not reset by reset) */
-    double persist_us[6];
+     * barriers -- grow, halo, link, faces, apply, prune, step scalars, unused --
+     * and the steps covered (accumulated since the last init, not reset by
+     * reset) */
+    double persist_us[8];
     int64_t persist_steps;
+    /* every persistent launch bracketed by CUDA events (always, not only while
+     * enabled): summed device time, launches, and the cell updates they made */
+    double persist_ms;
+    int64_t persist_launches;
+    int64_t persist_updates;
 } gbees_profile;
 
 /* enable != 0 turns event timing on; reset != 0 zeroes the counters. */

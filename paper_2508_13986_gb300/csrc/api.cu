@@ -75,7 +75,11 @@ struct gbees_ctx {
     bool kern_ok = false;
     int persist_grid = 0;
     long long persist_max_cells = 1ll << 18;
+    // device time of every persistent launch (always measured: few launches)
+    cudaEvent_t pev[2] = {nullptr, nullptr};
     ~gbees_ctx() {
+        for (auto e : pev)
+            if (e) cudaEventDestroy(e);
         if (gexec) cudaGraphExecDestroy(gexec);
         if (graph) cudaGraphDestroy(graph);
         for (auto& p : pending) {
@@ -419,8 +423,12 @@ void launch_readout(gbees_ctx* ctx, int* d_idx, double* d_p) {
 void launch_step(gbees_ctx* ctx) {
     resolve_update_kernels(ctx);
     {
-        Phase ph(ctx, GBEES_PHASE_GROW, ctx->kern.npre);
-        launch_list(ctx, ctx->kern.pre, ctx->kern.npre);
+        Phase ph(ctx, GBEES_PHASE_GROW, 1);
+        launch_list(ctx, ctx->kern.pre, 1);
+    }
+    {
+        Phase ph(ctx, GBEES_PHASE_HALO, 1);
+        launch_list(ctx, ctx->kern.pre + 1, 1);
     }
     {
         Phase ph(ctx, GBEES_PHASE_LINK, 1);
@@ -429,8 +437,12 @@ void launch_step(gbees_ctx* ctx) {
             launch_link<N>(ctx, 1);
         });
     }
-    Phase ph(ctx, GBEES_PHASE_UPDATE, ctx->kern.npost);
-    launch_list(ctx, ctx->kern.post, ctx->kern.npost);
+    {
+        Phase ph(ctx, GBEES_PHASE_FACES, 1);
+        launch_list(ctx, ctx->kern.post, 1);
+    }
+    Phase ph(ctx, GBEES_PHASE_APPLY, 1);
+    launch_list(ctx, ctx->kern.post + 1, 1);
 }
 
 // ---- the step loop as a CUDA graph
@@ -649,7 +661,7 @@ int gbees_profile_read(gbees_ctx* ctx, gbees_profile* out) {
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
         const double per_us = khz > 0 ? khz / 1e3 : 1.0;
-        for (int q = 0; q < 6; ++q) out->persist_us[q] = hs.phase_cycles[q] / per_us;
+        for (int q = 0; q < 8; ++q) out->persist_us[q] = hs.phase_cycles[q] / per_us;
         out->persist_steps = hs.phase_steps;
     }
     cudaGetLastError();
@@ -821,16 +833,27 @@ int gbees_propagate(gbees_ctx* ctx, double t_end, gbees_stats* stats) {
     if (persist_ok) {
         bool used = false;
         const long long limit = mode == GBEES_LAUNCH_PERSISTENT ? (1ll << 62) : ctx->persist_max_cells;
+        for (auto& e : ctx->pev)
+            if (!e && !cuda_ok(ctx, cudaEventCreate(&e), "propagate")) return ctx->status;
         while (!ctx->hs.done && ctx->hs.N <= limit) {
             used = true;
             const long long before = ctx->hs.steps_call;
+            const long long upd_before = ctx->hs.updates_call;
             long long max_steps = kPersistSteps;
             void* args[] = {&ctx->m, &ctx->b, &max_steps};
+            cudaEventRecord(ctx->pev[0], s);
             if (!cuda_ok(ctx, cudaLaunchCooperativeKernel(ctx->kern.persist, dim3(ctx->persist_grid), dim3(THREADS), args, 0, s),
                          "propagate"))
                 return ctx->status;
+            cudaEventRecord(ctx->pev[1], s);
             ctx->prof.total_launches += 1;
             if (!sync_scalars(ctx, "propagate")) return ctx->status;
+            float ms = 0.0f;
+            if (cudaEventElapsedTime(&ms, ctx->pev[0], ctx->pev[1]) == cudaSuccess) {
+                ctx->prof.persist_ms += ms;
+                ctx->prof.persist_launches += 1;
+                ctx->prof.persist_updates += ctx->hs.updates_call - upd_before;
+            }
             if (!ctx->hs.done && ctx->hs.steps_call == before) {
                 set_err(ctx, GBEES_ETIMEOUT, "propagate: a persistent launch made no progress");
                 return ctx->status;

@@ -73,6 +73,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_persistent(const Model m, Bufs b
         const long long n_active = *(volatile long long*)&sc->NA;
         halo_body<N, T>(m, b, v, v.N_prev, n_ins, *(volatile long long*)&sc->n_act);
         if (!grid_barrier(sc)) return;
+        mark(1);
         v.N = min(n_ins + *(volatile long long*)&sc->n_halo, m.cap);
         // link the new entries; CFL rates of the new active cells
         {
@@ -82,7 +83,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_persistent(const Model m, Bufs b
         }
         if (blockIdx.x == 0 && threadIdx.x == 0) sc->N = v.N;  // read again only after the next grow
         if (!grid_barrier(sc)) return;
-        mark(1);
+        mark(2);
         // everyone has read the halo and activation counts: reset them
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             sc->n_halo = 0;
@@ -114,19 +115,19 @@ __global__ void __launch_bounds__(THREADS, 1) k_persistent(const Model m, Bufs b
             set_error(sc, ST_EDEGENERATE);
             return;
         }
-        mark(5);
+        mark(6);
         // flux update
         long long d[NDIG] = {0, 0, 0, 0, 0, 0};
         double mx = -INFINITY;
         int err = 0;
         faces_body<N, DYN, T>(m, b, v);
         if (!grid_barrier(sc)) return;
-        mark(2);
+        mark(3);
         apply_body<N, T>(m, b, v, d, mx, err);
         if (err) set_error(sc, ST_EDEGENERATE);
         block_partial(b.part, d, mx, 0.0);
         if (!grid_barrier(sc)) return;
-        mark(3);
+        mark(4);
         {
             Combined cs = combine_partials(b.part, gridDim.x);
             if (threadIdx.x == 0) normalisation(m, cs, ss);
@@ -149,7 +150,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_persistent(const Model m, Bufs b
         nupd += n_active;
         v.pb ^= 1;
         v.N_prev = v.N;
-        mark(5);
+        mark(6);
         // prune (Algorithm 3) every prune_interval steps
         if (m.prune_interval > 0 && step % m.prune_interval == 0) {
             prune_mark_body<T>(m, b, v);
@@ -188,7 +189,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_persistent(const Model m, Bufs b
                 return;
             }
             maxrate = cp.rate_bits;
-            mark(4);
+            mark(5);
             v.N = total;
             v.N_prev = total;
             v.g ^= 1;

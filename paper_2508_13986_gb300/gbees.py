@@ -60,8 +60,9 @@ class gbees_stats(ctypes.Structure):
     ]
 
 
-GBEES_NPHASES = 6
-PHASE_NAMES = ("grow", "link", "update", "prune", "correct", "other")
+GBEES_NPHASES = 8
+PHASE_NAMES = ("grow", "halo", "link", "faces", "apply", "prune", "correct", "other")
+PERSIST_NAMES = ("grow", "halo", "link", "faces", "apply", "prune", "scalars")
 
 
 class gbees_profile(ctypes.Structure):
@@ -71,8 +72,11 @@ class gbees_profile(ctypes.Structure):
         ("timed", ctypes.c_int64 * GBEES_NPHASES),
         ("total_launches", ctypes.c_int64),
         ("fallback_lookups", ctypes.c_int64),
-        ("persist_us", ctypes.c_double * 6),
+        ("persist_us", ctypes.c_double * 8),
         ("persist_steps", ctypes.c_int64),
+        ("persist_ms", ctypes.c_double),
+        ("persist_launches", ctypes.c_int64),
+        ("persist_updates", ctypes.c_int64),
     ]
 
 
@@ -351,9 +355,11 @@ class Grid:
             "timed": {k: int(pr.timed[i]) for i, k in enumerate(PHASE_NAMES)},
             "total_launches": int(pr.total_launches),
             "fallback_lookups": int(pr.fallback_lookups),
-            "persist_us": {k: float(pr.persist_us[i]) for i, k in
-                           enumerate(("grow", "link", "faces", "update", "prune", "scalars"))},
+            "persist_us": {k: float(pr.persist_us[i]) for i, k in enumerate(PERSIST_NAMES)},
             "persist_steps": int(pr.persist_steps),
+            "persist_ms": float(pr.persist_ms),
+            "persist_launches": int(pr.persist_launches),
+            "persist_updates": int(pr.persist_updates),
         }
 
     _prof_on = False
