@@ -314,6 +314,120 @@ def time_precision(args, w, precision, dev, rank, world):
     }
 
 
+def batch_capacity(w) -> int:
+    """Pool capacity of one batched grid: room for the initial set growing
+    six-fold with its halo (a power of two, 2^15..2^22)."""
+    from paper_2508_13986_gb300 import workloads
+
+    want = 6.0 * workloads.initial_cells_estimate(w) + 4096
+    cap = 1 << 15
+    while cap < want and cap < (1 << 22):
+        cap <<= 1
+    return cap
+
+
+def time_batch(args, ws, precision, dev, rank, world):
+    """Many independent grids per step: the initial Gaussians of all grids and
+    one batched propagation of all of them to their own end times."""
+    import torch
+
+    from paper_2508_13986_gb300 import gbees
+
+    prec = gbees.GBEES_FP64 if precision == "f64" else gbees.GBEES_FP32
+    grids = [gbees.grid_for_workload(w, precision=prec, max_cells=batch_capacity(w), device=f"cuda:{dev}")
+             for w in ws]
+    stream = grids[0].stream
+    t_ends = [w.t_end for w in ws]
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=f"cuda:{dev}")
+
+    def run(with_readout=False):
+        for g, w in zip(grids, ws):
+            g.init_gaussian(w.mean, w.cov)
+        st = gbees.propagate_batch(grids, t_ends)
+        h2d = sum(8 * w.n + 8 * w.n * w.n for w in ws) + 8 * len(ws)
+        d2h = 0
+        if with_readout:
+            for g in grids:
+                idx, p = g.read_cells(sorted_=False)
+                mean, cov = g.moments()
+                d2h += idx.nbytes + p.nbytes + mean.nbytes + cov.nbytes
+        return (sum(x.cell_updates for x in st), sum(x.steps for x in st), max(x.n_pool for x in st), h2d, d2h)
+
+    for _ in range(args.warmup):
+        run()
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    grids[0].profile(enable=False, reset=True)
+    clocks = ClockSampler(dev)
+    clocks.start()
+    total_ms = total_updates = total_steps = peak = 0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        u, nst, pk, _, _ = run()
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        total_updates += u
+        total_steps += nst
+        peak = max(peak, pk)
+    clk = clocks.stop()
+    pt = grids[0].profile()
+    launches = sum(g.profile()["total_launches"] for g in grids)
+    e2e_ms = e2e_updates = 0
+    h2d = d2h = 0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        u, _, _, h2d, d2h = run(with_readout=True)
+        torch.cuda.synchronize(dev)
+        e2e_ms += (time.perf_counter() - t0) * 1e3
+        e2e_updates += u
+    for g in grids:
+        g.close()
+    ms_max = reduce_max(total_ms, world)
+    upd_sum = reduce_sum(total_updates, world)
+    e2e_max = reduce_max(e2e_ms, world)
+    e2e_sum = reduce_sum(e2e_updates, world)
+    peak_gbs, peak_src = load_peaks()
+    bpc = bytes_per_update(ws[0].n, precision)
+    launches_k = max(pt["persist_launches"], 1)
+    avg_us = pt["persist_ms"] * 1e3 / launches_k
+    units_per_launch = pt["persist_updates"] / launches_k
+    achieved = bpc * units_per_launch / (avg_us * 1e-6) / 1e9 if avg_us > 0 else None
+    return {
+        "value": upd_sum / (ms_max / 1e3),
+        "ms_per_step": ms_max / args.steps,
+        "updates_per_step": total_updates / args.steps,
+        "time_steps_per_run": total_steps / args.steps,
+        "peak_cells": peak,
+        "e2e": {"value": e2e_sum / (e2e_max / 1e3), "unit": METRIC, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_max / args.steps},
+        "roofline": {
+            "bound": "hbm",
+            "kernel": "k_batch (one block per grid, all grids' step loops in one launch)",
+            "timing": "CUDA events around every batch launch on the library stream, timed region",
+            "achieved": achieved,
+            "peak": peak_gbs,
+            "peak_source": peak_src,
+            "unit": "GB/s",
+            "frac": (achieved / peak_gbs) if achieved else None,
+            "traffic": None,
+            "algorithmic_bytes_per_cell_update": bpc,
+            "cell_updates_per_launch": units_per_launch,
+            "avg_launch_us": avg_us,
+        },
+        "profiled_phase_share": None,
+        "persistent_us_per_step": None,
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+
+
 def cpu_baseline(w, budget_s):
     """The oracle as it stands, single-threaded, on the first part of the same
     workload until about budget_s seconds of work."""
@@ -374,14 +488,27 @@ def main_ours(args):
         import torch.distributed as dist
 
         dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
-    w = workloads.config(args.workload)
-    if args.t_end is not None:
-        w = w.with_(t_end=args.t_end, measurements=[m for m in w.measurements if m.t < args.t_end])
-    main = time_precision(args, w, args.precision, local, rank, world)
+    if args.workload.startswith("lorenz63_batch"):
+        count = int(args.workload[len("lorenz63_batch"):] or 256)
+        ws = workloads.lorenz63_batch(count=count)
+        if args.t_end is not None:
+            ws = [x.with_(t_end=min(x.t_end, args.t_end)) for x in ws]
+        w = ws[0]
+        cfg_extra = {"grids": count, "t_end": "per grid, uniform in [0.25, 1.0]" if args.t_end is None
+                     else f"per grid, uniform in [0.25, 1.0], capped at {args.t_end}",
+                     "grid_sizes": "ragged, 1.7e3-2.7e5 initial cells"}
+        timer = lambda prec: time_batch(args, ws, prec, local, rank, world)  # noqa: E731
+    else:
+        w = workloads.config(args.workload)
+        if args.t_end is not None:
+            w = w.with_(t_end=args.t_end, measurements=[m for m in w.measurements if m.t < args.t_end])
+        cfg_extra = {"t_end": w.t_end}
+        timer = lambda prec: time_precision(args, w, prec, local, rank, world)  # noqa: E731
+    main = timer(args.precision)
     other = None
     if not args.no_secondary:
         other_prec = "f32" if args.precision == "f64" else "f64"
-        other = time_precision(args, w, other_prec, local, rank, world)
+        other = timer(other_prec)
     if rank == 0:
         cpu = cpu_baseline(w, args.cpu_budget) if (world == 1 and args.cpu_budget > 0) else None
         line = {
@@ -397,7 +524,7 @@ def main_ours(args):
             "vs_baseline": None,
             "dtype": args.precision,
             "data": "synthetic",
-            "config": {"workload": args.workload, "t_end": w.t_end, "parallelism": f"replicas{world}",
+            "config": {"workload": args.workload, **cfg_extra, "parallelism": f"replicas{world}",
                        "step": "one whole run: init + propagate/correct to t_end",
                        "l2": "flushed between timed runs (256 MiB write)",
                        "launch_mode": args.launch_mode,

@@ -161,6 +161,23 @@ int gbees_init_cells(gbees_ctx* ctx, const int32_t* idx, const double* p, int64_
  * NULL. t_end <= t takes no step. */
 int gbees_propagate(gbees_ctx* ctx, double t_end, gbees_stats* stats);
 
+/* Many independent grids in one launch (batched propagation). ctxs: count
+ * contexts with a grid each, all with the dimension, dynamics and precision of
+ * ctxs[0] and on the same device; t_end: count target times. One kernel runs
+ * on ctxs[0]'s stream with the same phases and arithmetic as gbees_propagate,
+ * so every grid ends bit-identical to its own gbees_propagate. When all grids
+ * fit on the GPU at once, each grid gets a team of thread blocks in proportion
+ * to its work (active cells x remaining time / h; cooperative launch, a
+ * barrier per team); otherwise each block takes the next grid from a queue
+ * and runs its whole step loop alone. d_scratch: device memory of
+ * gbees_batch_workspace_bytes(count) bytes, 256-byte aligned, owned by the
+ * caller. stats: NULL or count entries. Returns the first error of any grid
+ * (that grid's context is poisoned as by gbees_propagate), GBEES_EINVAL for
+ * mismatched contexts. The contexts must have no work in flight. */
+size_t gbees_batch_workspace_bytes(int32_t count);
+int gbees_batch_propagate(gbees_ctx* const* ctxs, int32_t count, const double* t_end, void* d_scratch,
+                          size_t scratch_bytes, gbees_stats* stats);
+
 /* Bayesian measurement update (Eq. 4) with the Gaussian likelihood
  * exp(-1/2 (y - x_H)^T R^{-1} (y - x_H)) of m measured components
  * x_H = (x[H_idx[0]], ..., x[H_idx[m-1]]) at the cell centres, followed by a
@@ -214,7 +231,8 @@ typedef struct {
      * reset) */
     double persist_us[8];
     int64_t persist_steps;
-    /* every persistent launch bracketed by CUDA events (always, not only while
+    /* every persistent launch (and every batch launch, counted on the batch's
+     * first context) bracketed by CUDA events (always, not only while
      * enabled): summed device time, launches, and the cell updates they made */
     double persist_ms;
     int64_t persist_launches;

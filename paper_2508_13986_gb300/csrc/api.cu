@@ -904,6 +904,191 @@ int gbees_propagate(gbees_ctx* ctx, double t_end, gbees_stats* stats) {
     return GBEES_OK;
 }
 
+// ---- many grids in one launch
+
+namespace {
+struct BatchLayout {
+    size_t next, slots, items, collect, total;
+};
+BatchLayout batch_layout(int32_t count) {
+    BatchLayout L;
+    L.next = 0;
+    L.slots = align_up(sizeof(unsigned int));
+    L.items = align_up(L.slots + sizeof(TeamSlot) * GRID_MAX);
+    L.collect = align_up(L.items + sizeof(BatchItem) * (size_t)count);
+    L.total = align_up(L.collect + sizeof(DevScalars) * (size_t)count);
+    return L;
+}
+constexpr long long kBatchSteps = 1ll << 20;  // steps per grid and launch at most
+constexpr int kMaxTeam = 32;                  // blocks per grid in a team launch at most
+
+// Team sizes of a team launch over G resident blocks: one block per grid plus
+// the rest in proportion to each grid's work (active cells x remaining time /
+// smallest cell width, the step count scaling as 1/h), at most kMaxTeam.
+std::vector<int> team_sizes(gbees_ctx* const* ctxs, int32_t count, const double* t_end, int G) {
+    std::vector<double> w((size_t)count, 0.0);
+    double W = 0.0;
+    for (int32_t i = 0; i < count; ++i) {
+        const gbees_ctx* c = ctxs[i];
+        double hmin = c->cfg.h[0];
+        for (int j = 1; j < c->cfg.n; ++j) hmin = std::min(hmin, c->cfg.h[j]);
+        const double rem = t_end[i] - c->hs.t;
+        w[i] = rem > 0.0 ? (double)std::max(1ll, c->hs.NA) * rem / hmin : 0.0;
+        W += w[i];
+    }
+    std::vector<int> k((size_t)count, 1);
+    if (W <= 0.0) return k;
+    int used = 0;
+    std::vector<double> rest((size_t)count, 0.0);
+    for (int32_t i = 0; i < count; ++i) {
+        const double ideal = w[i] / W * G;
+        k[i] = std::max(1, std::min(kMaxTeam, (int)std::floor(ideal)));
+        rest[i] = ideal - k[i];
+        used += k[i];
+    }
+    while (used > G) {  // the floor of 1 per grid overshot: shrink the largest teams
+        int j = (int)(std::max_element(k.begin(), k.end()) - k.begin());
+        if (k[j] <= 1) break;
+        --k[j];
+        --used;
+    }
+    while (used < G) {  // hand out the remainder by largest shortfall
+        int j = -1;
+        for (int32_t i = 0; i < count; ++i)
+            if (k[i] < kMaxTeam && (j < 0 || rest[i] > rest[j])) j = i;
+        if (j < 0 || rest[j] <= 0.0) break;
+        ++k[j];
+        rest[j] -= 1.0;
+        ++used;
+    }
+    return k;
+}
+}  // namespace
+
+size_t gbees_batch_workspace_bytes(int32_t count) { return count < 1 ? 0 : batch_layout(count).total; }
+
+int gbees_batch_propagate(gbees_ctx* const* ctxs, int32_t count, const double* t_end, void* d_scratch,
+                          size_t scratch_bytes, gbees_stats* stats) {
+    if (!ctxs || count < 1 || !t_end || !d_scratch) return GBEES_EINVAL;
+    const BatchLayout L = batch_layout(count);
+    if (scratch_bytes < L.total || ((uintptr_t)d_scratch % ALIGN) != 0) return GBEES_EINVAL;
+    gbees_ctx* c0 = ctxs[0];
+    for (int32_t i = 0; i < count; ++i) {
+        gbees_ctx* c = ctxs[i];
+        if (!c) return GBEES_EINVAL;
+        int st = guard(c, true);
+        if (st) return st;
+        if (!std::isfinite(t_end[i])) {
+            c->err = "t_end must be finite";
+            return GBEES_EINVAL;
+        }
+        if (c->cfg.n != c0->cfg.n || c->cfg.dynamics != c0->cfg.dynamics || c->cfg.precision != c0->cfg.precision) {
+            c->err = "batch: every grid needs the dimension, dynamics and precision of the first";
+            return GBEES_EINVAL;
+        }
+    }
+    resolve_update_kernels(c0);
+    if (!c0->kern_ok || !c0->kern.batch) {
+        set_err(c0, GBEES_EINVAL, "batch: no kernels for this model");
+        return c0->status;
+    }
+    cudaStream_t s = c0->stream;
+    char* base = (char*)d_scratch;
+    unsigned int* next = (unsigned int*)(base + L.next);
+    TeamSlot* slots = (TeamSlot*)(base + L.slots);
+    BatchItem* items = (BatchItem*)(base + L.items);
+    DevScalars* collect = (DevScalars*)(base + L.collect);
+    std::vector<BatchItem> h_items((size_t)count);
+    for (int32_t i = 0; i < count; ++i) {
+        std::memset(&h_items[i], 0, sizeof(BatchItem));
+        h_items[i].m = ctxs[i]->m;
+        h_items[i].b = ctxs[i]->b;
+        h_items[i].t_end = t_end[i];
+    }
+    if (!cuda_ok(c0, cudaMemcpyAsync(items, h_items.data(), sizeof(BatchItem) * count, cudaMemcpyHostToDevice, s),
+                 "batch_propagate"))
+        return c0->status;
+    k_batch_begin<<<(count + THREADS - 1) / THREADS, THREADS, 0, s>>>(items, count);
+    int dev = 0, sms = 0, per_sm = 0;
+    if (!cuda_ok(c0, cudaGetDevice(&dev), "batch_propagate") ||
+        !cuda_ok(c0, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "batch_propagate") ||
+        !cuda_ok(c0, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, c0->kern.batch, THREADS, 0),
+                 "batch_propagate"))
+        return c0->status;
+    int G = std::max(1, std::min(count, sms * std::max(per_sm, 1)));
+    // teams: every grid resident at once with blocks in proportion to its work
+    int per_sm_team = 0;
+    bool teams = c0->kern.batch_teams &&
+                 cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_team, c0->kern.batch_teams, THREADS, 0) ==
+                     cudaSuccess &&
+                 per_sm_team >= 1 && count <= std::min(GRID_MAX, sms * per_sm_team);
+    cudaGetLastError();
+    if (teams) {
+        const int Gt = std::min(GRID_MAX, sms * per_sm_team);
+        const std::vector<int> k = team_sizes(ctxs, count, t_end, Gt);
+        std::vector<TeamSlot> h_slots;
+        for (int32_t i = 0; i < count; ++i)
+            for (int j = 0; j < k[i]; ++j) h_slots.push_back(TeamSlot{(int)i, k[i], j});
+        G = (int)h_slots.size();
+        if (!cuda_ok(c0, cudaMemcpyAsync(slots, h_slots.data(), sizeof(TeamSlot) * G, cudaMemcpyHostToDevice, s),
+                     "batch_propagate"))
+            return c0->status;
+    }
+    std::vector<DevScalars> hs((size_t)count);
+    std::vector<long long> steps_before((size_t)count, -1), upd_before((size_t)count, 0);
+    long long max_steps = kBatchSteps;
+    for (auto& e : c0->pev)
+        if (!e && !cuda_ok(c0, cudaEventCreate(&e), "batch_propagate")) return c0->status;
+    for (int round = 0;; ++round) {
+        if (!cuda_ok(c0, cudaMemsetAsync(next, 0, sizeof(unsigned int), s), "batch_propagate")) return c0->status;
+        void* args[] = {&items, &count, &next, &max_steps};
+        void* targs[] = {&items, &slots, &max_steps};
+        cudaEventRecord(c0->pev[0], s);
+        const cudaError_t le = teams ? cudaLaunchCooperativeKernel(c0->kern.batch_teams, dim3(G), dim3(THREADS), targs, 0, s)
+                                     : cudaLaunchKernel(c0->kern.batch, dim3(G), dim3(THREADS), args, 0, s);
+        if (!cuda_ok(c0, le, "batch_propagate")) return c0->status;
+        cudaEventRecord(c0->pev[1], s);
+        k_batch_collect<<<std::min(1024, (count * (int)(sizeof(DevScalars) / 8) + THREADS - 1) / THREADS), THREADS, 0,
+                          s>>>(items, count, collect);
+        if (!cuda_ok(c0, cudaMemcpyAsync(hs.data(), collect, sizeof(DevScalars) * count, cudaMemcpyDeviceToHost, s),
+                     "batch_propagate") ||
+            !cuda_ok(c0, cudaStreamSynchronize(s), "batch_propagate"))
+            return c0->status;
+        c0->prof.total_launches += 3;
+        float ms = 0.0f;
+        long long upd = 0;
+        bool all_done = true, progress = false;
+        for (int32_t i = 0; i < count; ++i) {
+            if (!hs[i].done && !hs[i].error) all_done = false;
+            if (hs[i].steps_call != steps_before[i]) progress = true;
+            steps_before[i] = hs[i].steps_call;
+            upd += hs[i].updates_call - upd_before[i];
+            upd_before[i] = hs[i].updates_call;
+        }
+        if (cudaEventElapsedTime(&ms, c0->pev[0], c0->pev[1]) == cudaSuccess) {
+            c0->prof.persist_ms += ms;
+            c0->prof.persist_launches += 1;
+            c0->prof.persist_updates += upd;
+        }
+        if (all_done) break;
+        if (!progress) {
+            set_err(c0, GBEES_ETIMEOUT, "batch_propagate: a launch made no progress");
+            return c0->status;
+        }
+    }
+    int first_err = GBEES_OK;
+    for (int32_t i = 0; i < count; ++i) {
+        gbees_ctx* c = ctxs[i];
+        c->hs = hs[i];
+        if (c->hs.error) {
+            set_err(c, c->hs.error, std::string("batch_propagate: ") + status_text(c->hs.error));
+            if (first_err == GBEES_OK) first_err = c->status;
+        }
+        if (stats) fill_stats(c, stats + i);
+    }
+    return first_err;
+}
+
 int gbees_correct_gaussian(gbees_ctx* ctx, const double* y, const double* R, const int32_t* H_idx, int32_t m) {
     int st = guard(ctx, true);
     if (st) return st;

@@ -191,6 +191,22 @@ struct Kernels {
     void* post[3];
     int npost;
     void* persist;
+    void* batch;
+    void* batch_teams;
+};
+
+// One grid of a batched propagation (k_batch): its model, its buffers (in its
+// own workspace) and the time to propagate it to.
+struct BatchItem {
+    Model m;
+    Bufs b;
+    double t_end;
+};
+
+// Block of a team launch (k_batch_teams): the grid it works on (-1: none), the
+// team's size and this block's index in the team.
+struct TeamSlot {
+    int item, nb, bi;
 };
 
 
@@ -198,15 +214,18 @@ struct Kernels {
 // ------------------------------------------------------------------ cell iteration
 // Cells are handed out in runs of 32 consecutive cells (one warp, coalesced),
 // consecutive runs to consecutive blocks, so that a small grid still spreads
-// over every SM. Usage:
-//   for (WarpRuns r(ncell); r.next();) { const long long c = r.c; if (c >= ncell) continue; ... }
+// over every SM. The blocks that share the work of one grid are nb blocks of
+// index bi (the whole launch, or one block when a launch runs many grids).
+// Usage:
+//   for (WarpRuns r(ncell, nb, bi); r.next();) { const long long c = r.c; if (c >= ncell) continue; ... }
 struct WarpRuns {
     long long k, step, n, c;
-    __device__ __forceinline__ explicit WarpRuns(long long ncell)
-        : k(blockIdx.x + (long long)gridDim.x * (threadIdx.x >> 5) - (long long)gridDim.x * (blockDim.x >> 5)),
-          step((long long)gridDim.x * (blockDim.x >> 5)),
+    __device__ __forceinline__ WarpRuns(long long ncell, int nb, int bi)
+        : k(bi + (long long)nb * (threadIdx.x >> 5) - (long long)nb * (blockDim.x >> 5)),
+          step((long long)nb * (blockDim.x >> 5)),
           n(ncell),
           c(0) {}
+    __device__ __forceinline__ explicit WarpRuns(long long ncell) : WarpRuns(ncell, gridDim.x, blockIdx.x) {}
     __device__ __forceinline__ bool next() {
         k += step;
         c = k * 32 + (threadIdx.x & 31);
@@ -684,7 +703,8 @@ __device__ __forceinline__ void finish_step(const Model& m, DevScalars* sc, long
 // Write this block's partial (exact digits, maximum value, maximum rate).
 // All threads of the block must call it; d, mx, rate are per thread. The
 // maxima are reduced as order-preserving integer keys (integer pipe).
-__device__ __forceinline__ void block_partial(Partial* part, long long (&d)[NDIG], double mx, double rate) {
+__device__ __forceinline__ void block_partial(Partial* part, long long (&d)[NDIG], double mx, double rate,
+                                              int bi) {
     __shared__ long long s_acc[WARPS][NDIG];
     __shared__ unsigned long long s_mx[WARPS], s_rt[WARPS];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -718,9 +738,12 @@ __device__ __forceinline__ void block_partial(Partial* part, long long (&d)[NDIG
         }
         p.maxq_ord = mm;
         p.rate_bits = rr;
-        part[blockIdx.x] = p;
+        part[bi] = p;
     }
     __syncthreads();
+}
+__device__ __forceinline__ void block_partial(Partial* part, long long (&d)[NDIG], double mx, double rate) {
+    block_partial(part, d, mx, rate, blockIdx.x);
 }
 
 // Combine the partials of blocks [0, nblk) in every thread of the calling
@@ -776,7 +799,10 @@ __device__ __forceinline__ Combined combine_partials(const Partial* part, int nb
 // bounded: it gives up when another block has set an error or after about
 // two seconds, sets ST_ETIMEOUT, and returns false; callers then leave.
 constexpr long long BARRIER_SPIN_LIMIT = 1ll << 26;
-__device__ __forceinline__ bool grid_barrier(DevScalars* sc) {
+// Barrier of the nb blocks that share the grid whose scalars are sc (the whole
+// launch, or a team of a batched launch); every block of the team must be
+// resident (cooperative launch). Bounded: gives up with ST_ETIMEOUT.
+__device__ __forceinline__ bool grid_barrier(DevScalars* sc, int nb) {
     __shared__ int s_ok;
     unsigned int* bar = &sc->bar_count;
     __syncthreads();
@@ -786,7 +812,7 @@ __device__ __forceinline__ bool grid_barrier(DevScalars* sc) {
         __threadfence();
         const unsigned int arrived = atomicAdd(bar, 1u);
         int ok = 1;
-        if (arrived == gridDim.x - 1) {
+        if (arrived == (unsigned int)nb - 1u) {
             *(volatile unsigned int*)bar = 0u;
             __threadfence();
             atomicAdd(&sc->bar_gen, 1u);

@@ -39,7 +39,8 @@ __global__ void __launch_bounds__(THREADS) k_link(const Model m, Bufs b, int ste
     if (*(volatile int*)&sc->error) return;
     if (step && *(volatile int*)&sc->done) return;
     const StepView v = view_of(m, sc);
-    const double r = (W == 1) ? link_body<N>(m, b, v.N_prev, v.N, v.g) : link_body_tile<N, W>(m, b, v.N_prev, v.N, v.g);
+    const double r = (W == 1) ? link_body<N>(m, b, v.N_prev, v.N, v.g, v.nb, v.bi)
+                              : link_body_tile<N, W>(m, b, v.N_prev, v.N, v.g, v.nb, v.bi);
     long long zero[NDIG] = {0, 0, 0, 0, 0, 0};
     block_partial(b.part, zero, -INFINITY, r);
     if (last_block(sc)) {
@@ -368,7 +369,7 @@ __global__ void __launch_bounds__(THREADS) k_prune_compact(const Model m, Bufs b
     DevScalars* sc = b.sc;
     if (!prune_due(sc)) return;
     const StepView v = view_of(m, sc);
-    const Survivors sv = block_offsets(b);
+    const Survivors sv = block_offsets(b, v.nb, v.bi);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         sc->N_new = sv.total_a + sv.total_g;
         sc->NA_new = sv.total_a;

@@ -17,6 +17,28 @@ __global__ void k_begin(DevScalars* sc, double t_target) {
 
 __global__ void k_finalise(const Model m, DevScalars* sc, int mode) { finalise_norm(m, sc, mode); }
 
+// Start a batched propagate call: k_begin for every grid of the batch.
+__global__ void k_batch_begin(const BatchItem* items, int count) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        DevScalars* sc = items[i].b.sc;
+        const double tt = items[i].t_end;
+        sc->t_target = tt;
+        sc->done = !(sc->t < tt) || sc->error != 0;
+        sc->steps_call = 0;
+        sc->updates_call = 0;
+    }
+}
+
+// Copy the scalars of every grid of a batch into one array (one read-back).
+__global__ void k_batch_collect(const BatchItem* items, int count, DevScalars* out) {
+    constexpr int W = sizeof(DevScalars) / 8;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < (long long)count * W;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(k / W), q = (int)(k % W);
+        reinterpret_cast<long long*>(out + i)[q] = __ldcg(reinterpret_cast<const long long*>(items[i].b.sc) + q);
+    }
+}
+
 // Control of the device-side step loop of a graph launch (a WHILE node whose
 // body is one step and an IF node around the prune): after the flux update of
 // a step, decide whether the prune runs and whether another step follows.

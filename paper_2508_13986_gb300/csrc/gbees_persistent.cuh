@@ -1,12 +1,19 @@
-// The whole step loop of a propagate call in one cooperative launch.
+// The whole step loop of a propagate call in one launch.
 //
-// For the grids of 10^4-10^5 cells of the Lorenz '63 workloads a time step is a
-// few microseconds of work split into dependent phases; kernel launches and
-// their drain would dominate. This kernel keeps one block per SM resident and
-// separates the phases by a bounded grid barrier (the cooperative-kernel
-// structure of Sec. 4, with GB300's block count). Every block computes the
-// step's scalars (dt, normalisation, maximum) itself from the same per-block
-// partials, so the scalars need no extra barrier; block 0 writes them back.
+// k_persistent: for the grids of 10^4-10^5 cells of the Lorenz '63 workloads a
+// time step is a few microseconds of work split into dependent phases; kernel
+// launches and their drain would dominate. This cooperative kernel keeps one
+// block per SM resident and separates the phases by a bounded grid barrier
+// (the cooperative-kernel structure of Sec. 4, with GB300's block count).
+//
+// k_batch: many independent grids in one launch. Each block takes a grid from
+// a queue and runs its whole step loop alone, the phases separated by block
+// barriers; blocks never wait on each other, so the launch needs no
+// co-residency and ragged grids balance over the SMs.
+//
+// Every block computes the step's scalars (dt, normalisation, maximum) itself
+// from the same per-block partials, so the scalars need no extra barrier;
+// block 0 of the grid writes them back.
 //
 // Barriers per step: grow + waves | halo | link | faces | apply; a prune adds
 // mark | scatter | status | compact | relink.
@@ -34,11 +41,23 @@ __device__ __forceinline__ void normalisation(const Model& m, const Combined& c,
     ss.maxq = c.maxq_ord ? ord_val(c.maxq_ord) : 0.0;
 }
 
+// Up to max_steps steps of the grid (m, b) by the nb blocks of index bi that
+// share it (the whole launch, a team of a batched launch, or one block): grid
+// barriers between the phases, block barriers when the block is alone.
 template <int N, int DYN, typename T>
-__global__ void __launch_bounds__(THREADS, 1) k_persistent(const Model m, Bufs b, long long max_steps) {
+__device__ __forceinline__ void step_loop(const Model& m, const Bufs& b, long long max_steps, int nb, int bi) {
     __shared__ StepShared ss;
     DevScalars* sc = b.sc;
+    auto barrier = [&]() -> bool {
+        if (nb == 1) {
+            __syncthreads();
+            return !*(volatile int*)&sc->error;
+        }
+        return grid_barrier(sc, nb);
+    };
     StepView v = view_of(m, sc);
+    v.nb = nb;
+    v.bi = bi;
     double t = *(volatile double*)&sc->t;
     const double tt = *(volatile double*)&sc->t_target;
     int done = *(volatile int*)&sc->done;
@@ -48,12 +67,12 @@ __global__ void __launch_bounds__(THREADS, 1) k_persistent(const Model m, Bufs b
     double last_dt = *(volatile double*)&sc->dt;
     long long nsteps = 0, nupd = 0;
     // every block has read the state before anyone changes it
-    if (done || *(volatile int*)&sc->error || !grid_barrier(sc)) return;
+    if (done || *(volatile int*)&sc->error || !barrier()) return;
     // phase timing by block 0 (cycles between the barriers it passes)
     long long pc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     long long t_mark = clock64();
     auto mark = [&](int ph) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (bi == 0 && threadIdx.x == 0) {
             const long long now = clock64();
             pc[ph] += now - t_mark;
             t_mark = now;
@@ -65,32 +84,32 @@ __global__ void __launch_bounds__(THREADS, 1) k_persistent(const Model m, Bufs b
         // waves of the existing entries alongside
         const double rg = grow_body<N, T>(m, b, v);
         waves_body<N, DYN, T>(m, b, v, v.N_prev);
-        if (!grid_barrier(sc)) return;
+        if (!barrier()) return;
         mark(0);
         // halo cells around the newly active cells (appended after sc->N, which
         // stays put until the link phase)
         const long long n_ins = min(*(volatile long long*)&sc->N, m.cap);
         const long long n_active = *(volatile long long*)&sc->NA;
         halo_body<N, T>(m, b, v, v.N_prev, n_ins, *(volatile long long*)&sc->n_act);
-        if (!grid_barrier(sc)) return;
+        if (!barrier()) return;
         mark(1);
         v.N = min(n_ins + *(volatile long long*)&sc->n_halo, m.cap);
         // link the new entries; CFL rates of the new active cells
         {
-            const double r = fmax(rg, link_body<N>(m, b, v.N_prev, v.N, v.g));
+            const double r = fmax(rg, link_body<N>(m, b, v.N_prev, v.N, v.g, nb, bi));
             long long zero[NDIG] = {0, 0, 0, 0, 0, 0};
-            block_partial(b.part, zero, -INFINITY, r);
+            block_partial(b.part, zero, -INFINITY, r, bi);
         }
-        if (blockIdx.x == 0 && threadIdx.x == 0) sc->N = v.N;  // read again only after the next grow
-        if (!grid_barrier(sc)) return;
+        if (bi == 0 && threadIdx.x == 0) sc->N = v.N;  // read again only after the next grow
+        if (!barrier()) return;
         mark(2);
         // everyone has read the halo and activation counts: reset them
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (bi == 0 && threadIdx.x == 0) {
             sc->n_halo = 0;
             sc->n_act = 0;
         }
         {
-            Combined cr = combine_partials(b.part, gridDim.x);
+            Combined cr = combine_partials(b.part, nb);
             maxrate = max(maxrate, cr.rate_bits);
         }
         if (threadIdx.x == 0) {
@@ -121,15 +140,15 @@ __global__ void __launch_bounds__(THREADS, 1) k_persistent(const Model m, Bufs b
         double mx = -INFINITY;
         int err = 0;
         faces_body<N, DYN, T>(m, b, v);
-        if (!grid_barrier(sc)) return;
+        if (!barrier()) return;
         mark(3);
         apply_body<N, T>(m, b, v, d, mx, err);
         if (err) set_error(sc, ST_EDEGENERATE);
-        block_partial(b.part, d, mx, 0.0);
-        if (!grid_barrier(sc)) return;
+        block_partial(b.part, d, mx, 0.0, bi);
+        if (!barrier()) return;
         mark(4);
         {
-            Combined cs = combine_partials(b.part, gridDim.x);
+            Combined cs = combine_partials(b.part, nb);
             if (threadIdx.x == 0) normalisation(m, cs, ss);
             __syncthreads();
             w = ss.w;
@@ -154,14 +173,14 @@ __global__ void __launch_bounds__(THREADS, 1) k_persistent(const Model m, Bufs b
         // prune (Algorithm 3) every prune_interval steps
         if (m.prune_interval > 0 && step % m.prune_interval == 0) {
             prune_mark_body<T>(m, b, v);
-            if (!grid_barrier(sc)) return;
+            if (!barrier()) return;
             prune_scatter_body<N, T>(m, b, v);
-            if (!grid_barrier(sc)) return;
+            if (!barrier()) return;
             prune_count_body<N>(m, b, v);
-            if (!grid_barrier(sc)) return;
-            const Survivors sv = block_offsets(b);
+            if (!barrier()) return;
+            const Survivors sv = block_offsets(b, v.nb, v.bi);
             const long long total = sv.total_a + sv.total_g;
-            if (blockIdx.x == 0 && threadIdx.x == 0) {  // before the next grow appends
+            if (bi == 0 && threadIdx.x == 0) {  // before the next grow appends
                 sc->N = total;
                 sc->NA = sv.total_a;
             }
@@ -171,12 +190,12 @@ __global__ void __launch_bounds__(THREADS, 1) k_persistent(const Model m, Bufs b
                 int errp = 0;
                 prune_compact_body<N, T>(m, b, v, sv, dp, mxp, rmax, errp);
                 if (errp) set_error(sc, ST_EDEGENERATE);
-                block_partial(b.part, dp, mxp, rmax);
+                block_partial(b.part, dp, mxp, rmax, bi);
             }
-            if (!grid_barrier(sc)) return;
+            if (!barrier()) return;
             prune_relink_body<N>(m, b, v);
-            if (!grid_barrier(sc)) return;
-            Combined cp = combine_partials(b.part, gridDim.x);
+            if (!barrier()) return;
+            Combined cp = combine_partials(b.part, nb);
             if (threadIdx.x == 0) normalisation(m, cp, ss);
             __syncthreads();
             w = ss.w;
@@ -196,7 +215,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_persistent(const Model m, Bufs b
             v.pb ^= 1;
         }
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (bi == 0 && threadIdx.x == 0) {
         sc->N = v.N;
         sc->N_prev = v.N_prev;
         sc->pbuf = v.pb;
@@ -213,10 +232,53 @@ __global__ void __launch_bounds__(THREADS, 1) k_persistent(const Model m, Bufs b
         sc->updates_call += nupd;
         sc->prune_now = 0;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (bi == 0 && threadIdx.x == 0) {
         for (int q = 0; q < 8; ++q) sc->phase_cycles[q] += pc[q];
         sc->phase_steps += nsteps;
     }
+}
+
+
+template <int N, int DYN, typename T>
+__global__ void __launch_bounds__(THREADS, 1) k_persistent(const Model m, Bufs b, long long max_steps) {
+    step_loop<N, DYN, T>(m, b, max_steps, gridDim.x, blockIdx.x);
+}
+
+// Resident blocks per SM of the batch kernels: the register cap (64) spills a
+// little, but four blocks keep four times the loads of one in flight, and the
+// phases are bound by dependent global loads (measured: 2.1x the throughput of
+// two blocks per SM on 256 Lorenz '63 grids).
+constexpr int BATCH_BLOCKS_PER_SM = 4;
+
+// k_batch: block after block takes the next grid of the queue (next counts the
+// grids handed out) and runs up to max_steps of its steps. A grid that is done
+// or in error returns at once, so a launch can be repeated until all are done.
+template <int N, int DYN, typename T>
+__global__ void __launch_bounds__(THREADS, BATCH_BLOCKS_PER_SM) k_batch(const BatchItem* items, int count, unsigned int* next,
+                                                  long long max_steps) {
+    __shared__ int s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(next, 1u);
+        __syncthreads();
+        const int i = s_item;
+        __syncthreads();
+        if (i >= count) return;
+        const Bufs b = items[i].b;
+        step_loop<N, DYN, T>(items[i].m, b, max_steps, 1, 0);
+        __syncthreads();
+    }
+}
+
+// k_batch_teams: a cooperative launch in which every grid has a team of
+// blocks (slots[blockIdx.x]) sized to its work, the team's phases separated by
+// a barrier on the grid's own scalars.
+template <int N, int DYN, typename T>
+__global__ void __launch_bounds__(THREADS, BATCH_BLOCKS_PER_SM) k_batch_teams(const BatchItem* items, const TeamSlot* slots,
+                                                        long long max_steps) {
+    const TeamSlot ts = slots[blockIdx.x];
+    if (ts.item < 0) return;
+    const Bufs b = items[ts.item].b;
+    step_loop<N, DYN, T>(items[ts.item].m, b, max_steps, ts.nb, ts.bi);
 }
 
 }  // namespace gbees

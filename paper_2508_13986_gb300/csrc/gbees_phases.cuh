@@ -34,6 +34,7 @@ struct StepView {
     double dth[MAXN];  // dt / h_j of this step
     double ch[MAXN];   // dt / (2 h_j)
     double dt;         // dt of this step
+    int nb, bi;        // the blocks that share this grid's work, and this block's index among them
 };
 
 __device__ __forceinline__ StepView view_of(const Model& m, DevScalars* sc) {
@@ -49,6 +50,8 @@ __device__ __forceinline__ StepView view_of(const Model& m, DevScalars* sc) {
         v.ch[j] = *(volatile double*)&sc->coef_ch[j];
     }
     v.dt = *(volatile double*)&sc->step_dt;
+    v.nb = gridDim.x;
+    v.bi = blockIdx.x;
     return v;
 }
 
@@ -278,7 +281,7 @@ __device__ __forceinline__ double grow_body(const Model& m, const Bufs& b, const
         if (d2 >= 0) J[d2 >> 1] += (d2 & 1) ? 1 : -1;
         insert_active(J);
     };
-    for (WarpRuns r(ncell); r.next();) {
+    for (WarpRuns r(ncell, v.nb, v.bi); r.next();) {
         const long long c = r.c;
         unsigned f = 0;
         bool q = false;
@@ -320,8 +323,8 @@ __device__ __forceinline__ void halo_body(const Model& m, const Bufs& b, const S
     const long long cap = m.cap;
     const long long ni = hi - lo;
     const long long items = (ni + nact) * 2 * N;
-    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long nth = (long long)gridDim.x * blockDim.x;
+    const long long tid = (long long)v.bi * blockDim.x + threadIdx.x;
+    const long long nth = (long long)v.nb * blockDim.x;
     for (long long it = tid; it < items; it += nth) {
         const long long q = it / (2 * N);
         const int d = (int)(it - q * 2 * N);
@@ -344,10 +347,11 @@ __device__ __forceinline__ void halo_body(const Model& m, const Bufs& b, const S
 // Outward masks of the new entries [lo, hi) (added to the flags their inserter
 // wrote) and the largest CFL rate among the active ones.
 template <int N>
-__device__ __forceinline__ double link_masks(const Model& m, const Bufs& b, long long lo, long long hi, int g) {
+__device__ __forceinline__ double link_masks(const Model& m, const Bufs& b, long long lo, long long hi, int g,
+                                              int nb, int bi) {
     const unsigned long long* key = b.key[g];
-    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long nth = (long long)gridDim.x * blockDim.x;
+    const long long tid = (long long)bi * blockDim.x + threadIdx.x;
+    const long long nth = (long long)nb * blockDim.x;
     double rmax = 0.0;
     for (long long c = lo + tid; c < hi; c += nth) {
         int I[N];
@@ -364,12 +368,13 @@ __device__ __forceinline__ double link_masks(const Model& m, const Bufs& b, long
 // their outward masks; returns this thread's largest CFL rate among the active
 // ones.
 template <int N>
-__device__ __forceinline__ double link_body(const Model& m, const Bufs& b, long long lo, long long hi, int g) {
+__device__ __forceinline__ double link_body(const Model& m, const Bufs& b, long long lo, long long hi, int g, int nb,
+                                             int bi) {
     const unsigned long long* key = b.key[g];
     int* link = b.link[g];
     const long long cap = m.cap;
-    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long nth = (long long)gridDim.x * blockDim.x;
+    const long long tid = (long long)bi * blockDim.x + threadIdx.x;
+    const long long nth = (long long)nb * blockDim.x;
     const long long work = (hi - lo) * 2 * N;
     for (long long wi = tid; wi < work; wi += nth) {
         const long long c = lo + wi / (2 * N);
@@ -383,18 +388,19 @@ __device__ __forceinline__ double link_body(const Model& m, const Bufs& b, long 
         link[(long long)c * LROW<N> + dir] = nb;
         if (nb >= 0) link[(long long)nb * LROW<N> + (2 * j + (1 - s))] = (int)c;
     }
-    return link_masks<N>(m, b, lo, hi, g);
+    return link_masks<N>(m, b, lo, hi, g, nb, bi);
 }
 
 // Cooperative variant: W lanes probe W consecutive slots together.
 template <int N, int W>
-__device__ __forceinline__ double link_body_tile(const Model& m, const Bufs& b, long long lo, long long hi, int g) {
+__device__ __forceinline__ double link_body_tile(const Model& m, const Bufs& b, long long lo, long long hi, int g,
+                                                  int nb, int bi) {
     const unsigned long long* key = b.key[g];
     int* link = b.link[g];
     const long long cap = m.cap;
     auto tile = cg::tiled_partition<W>(cg::this_thread_block());
-    const long long tiles = (long long)gridDim.x * (blockDim.x / W);
-    const long long tile_id = (long long)blockIdx.x * (blockDim.x / W) + threadIdx.x / W;
+    const long long tiles = (long long)nb * (blockDim.x / W);
+    const long long tile_id = (long long)bi * (blockDim.x / W) + threadIdx.x / W;
     const long long work = (hi - lo) * 2 * N;
     for (long long wi = tile_id; wi < work; wi += tiles) {
         const long long c = lo + wi / (2 * N);
@@ -410,7 +416,7 @@ __device__ __forceinline__ double link_body_tile(const Model& m, const Bufs& b, 
             if (nb >= 0) link[(long long)nb * LROW<N> + (2 * j + (1 - s))] = (int)c;
         }
     }
-    return link_masks<N>(m, b, lo, hi, g);
+    return link_masks<N>(m, b, lo, hi, g, nb, bi);
 }
 
 // ------------------------------------------------------------------ three-pass update
@@ -458,7 +464,7 @@ __device__ __forceinline__ void waves_body(const Model& m, const Bufs& b, const 
     T* wg = static_cast<T*>(b.wv_g);
     const Geo<N, T> geo(m, v);
     const long long items = ncell * N;
-    for (WarpRuns wr(items); wr.next();) {
+    for (WarpRuns wr(items, v.nb, v.bi); wr.next();) {
         const long long it = wr.c;
         if (it >= items) continue;
         const long long c = it / N;
@@ -524,7 +530,7 @@ __device__ __forceinline__ void faces_body(const Model& m, const Bufs& b, const 
     const int lim = m.limiter;
     const Geo<N, T> geo(m, v);
     const long long items = ncell * N;
-    for (WarpRuns wr(items); wr.next();) {
+    for (WarpRuns wr(items, v.nb, v.bi); wr.next();) {
         const long long it = wr.c;
         if (it >= items) continue;
         const long long c = it / N;
@@ -604,7 +610,7 @@ __device__ __forceinline__ void apply_body(const Model& m, const Bufs& b, const 
 #pragma unroll
     for (int k = 0; k < N; ++k) dth[k] = (T)v.dth[k];
     T tmax = -INFINITY;
-    for (WarpRuns wr(ncell); wr.next();) {
+    for (WarpRuns wr(ncell, v.nb, v.bi); wr.next();) {
         const long long c = wr.c;
         if (c >= ncell) continue;
         if (is_halo(om, c)) {
@@ -636,7 +642,7 @@ __device__ __forceinline__ void prune_mark_body(const Model& m, const Bufs& b, c
     const double pstar = m.thr_rel * v.maxq;
     const T* Q = static_cast<const T*>(b.q[v.pb]);
     const unsigned short* om = b.om[v.g];
-    for (WarpRuns r(v.N); r.next();) {
+    for (WarpRuns r(v.N, v.nb, v.bi); r.next();) {
         const long long c = r.c;
         if (c < v.N) b.keep[c] = !is_halo(om, c) && (double)Q[c] > pstar;
     }
@@ -651,7 +657,7 @@ __device__ __forceinline__ void prune_scatter_body(const Model& m, const Bufs& b
     const int* link = b.link[v.g];
     const unsigned short* om = b.om[v.g];
     const long long cap = m.cap;
-    for (WarpRuns r(v.N); r.next();) {
+    for (WarpRuns r(v.N, v.nb, v.bi); r.next();) {
         const long long c = r.c;
         if (c >= v.N) continue;
         const unsigned f = om[c];
@@ -676,12 +682,15 @@ __device__ __forceinline__ void prune_scatter_body(const Model& m, const Bufs& b
     }
 }
 
-// chunk [c0, c1) of a range of `total` items handled by this block
-__device__ __forceinline__ void block_chunk(long long total, long long& c0, long long& c1) {
-    long long per = (total + gridDim.x - 1) / gridDim.x;
+// chunk [c0, c1) of a range of `total` items handled by block bi of nb
+__device__ __forceinline__ void block_chunk(long long total, long long& c0, long long& c1, int nb, int bi) {
+    long long per = (total + nb - 1) / nb;
     per = (per + THREADS - 1) / THREADS * THREADS;
-    c0 = min(total, per * blockIdx.x);
+    c0 = min(total, per * bi);
     c1 = min(total, c0 + per);
+}
+__device__ __forceinline__ void block_chunk(long long total, long long& c0, long long& c1) {
+    block_chunk(total, c0, c1, gridDim.x, blockIdx.x);
 }
 
 // Sum of a per-thread count over the block (every thread gets it).
@@ -706,7 +715,7 @@ __device__ __forceinline__ void prune_count_body(const Model& m, const Bufs& b, 
     const unsigned short* om = b.om[v.g];
     const long long cap = m.cap;
     long long c0, c1;
-    block_chunk(v.N, c0, c1);
+    block_chunk(v.N, c0, c1, v.nb, v.bi);
     int na = 0, ng = 0;
     for (long long c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
         int st = 0;
@@ -726,8 +735,8 @@ __device__ __forceinline__ void prune_count_body(const Model& m, const Bufs& b, 
     const long long ta = block_count(na);
     const long long tg = block_count(ng);
     if (threadIdx.x == 0) {
-        b.blk[blockIdx.x] = ta;
-        b.blk2[blockIdx.x] = tg;
+        b.blk[v.bi] = ta;
+        b.blk2[v.bi] = tg;
     }
     const unsigned int* slots = b.slot[v.g];
     for (long long c = c0 + threadIdx.x; c < c1; c += blockDim.x)
@@ -739,15 +748,15 @@ __device__ __forceinline__ void prune_count_body(const Model& m, const Bufs& b, 
 struct Survivors {
     long long base_a, base_g, total_a, total_g;
 };
-__device__ __forceinline__ Survivors block_offsets(const Bufs& b) {
+__device__ __forceinline__ Survivors block_offsets(const Bufs& b, int nb, int bi) {
     __shared__ long long s[4][WARPS];
     long long v[4] = {0, 0, 0, 0};  // offset a, total a, offset g, total g
-    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
         const long long a = __ldcg(&b.blk[i]);
         const long long g = __ldcg(&b.blk2[i]);
         v[1] += a;
         v[3] += g;
-        if (i < (int)blockIdx.x) {
+        if (i < bi) {
             v[0] += a;
             v[2] += g;
         }
@@ -791,7 +800,7 @@ __device__ __forceinline__ void prune_compact_body(const Model& m, const Bufs& b
     const double s2 = (mq > 0.0 && isfinite(mq)) ? ldexp(1.0, -ilogb(mq)) : 1.0;
     long long ba = sv.base_a, bg = sv.base_g;
     long long c0, c1;
-    block_chunk(v.N, c0, c1);
+    block_chunk(v.N, c0, c1, v.nb, v.bi);
     for (long long t0 = c0; t0 < c1; t0 += blockDim.x) {
         const long long c = t0 + threadIdx.x;
         const int st = (c < c1) ? b.map[c] : 0;
@@ -834,7 +843,7 @@ __device__ __forceinline__ void prune_relink_body(const Model& m, const Bufs& b,
     int* linko = b.link[v.g ^ 1];
     const unsigned long long* keyo = b.key[v.g ^ 1];
     const long long cap = m.cap;
-    for (WarpRuns r(v.N); r.next();) {
+    for (WarpRuns r(v.N, v.nb, v.bi); r.next();) {
         const long long c = r.c;
         if (c >= v.N) continue;
         const int nc = b.map[c];

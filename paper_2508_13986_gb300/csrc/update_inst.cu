@@ -28,6 +28,8 @@ using Real = float;
 template <int N, int DYN>
 static void kernels_of(Kernels* k) {
     k->persist = (void*)k_persistent<N, DYN, Real>;
+    k->batch = (void*)k_batch<N, DYN, Real>;
+    k->batch_teams = (void*)k_batch_teams<N, DYN, Real>;
     k->pre[0] = (void*)k_grow_waves<N, DYN, Real>;
     k->pre[1] = (void*)k_halo<N, Real, 1>;
     k->npre = 2;

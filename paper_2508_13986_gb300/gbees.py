@@ -100,6 +100,8 @@ _SIGNATURES = {
     "gbees_destroy": (None, [_vp]),
     "gbees_propagate_cells_noalloc": (ctypes.c_int, [_P(gbees_config), _P(_i32), _P(_d), _i64, _d, _i64, _d, _vp,
                                                      _P(_i32), _P(_d), _i64, _P(_i64), _P(gbees_stats)]),
+    "gbees_batch_workspace_bytes": (ctypes.c_size_t, [_i32]),
+    "gbees_batch_propagate": (ctypes.c_int, [_P(_vp), _i32, _P(_d), _vp, ctypes.c_size_t, _P(gbees_stats)]),
 }
 GBEES_NOALLOC_SCRATCH_BYTES = 16 << 20
 
@@ -193,6 +195,16 @@ def gbees_last_error(ctx: int) -> str:
 
 def gbees_destroy(ctx: int) -> None:
     _f("gbees_destroy")(_vp(ctx))
+
+
+def gbees_batch_workspace_bytes(count: int) -> int:
+    return int(_f("gbees_batch_workspace_bytes")(int(count)))
+
+
+def gbees_batch_propagate(ctxs: Sequence[int], t_end: np.ndarray, d_scratch: int, nbytes: int, stats) -> int:
+    arr = (_vp * len(ctxs))(*[_vp(c) for c in ctxs])
+    te = np.ascontiguousarray(t_end, dtype=np.float64)
+    return _f("gbees_batch_propagate")(arr, len(ctxs), _dp(te), _vp(d_scratch), nbytes, stats)
 
 
 def gbees_propagate_cells_noalloc(cfg: gbees_config, idx: np.ndarray, p: np.ndarray, t0: float, step0: int,
@@ -363,6 +375,27 @@ class Grid:
         }
 
     _prof_on = False
+
+
+def propagate_batch(grids: Sequence["Grid"], t_end: Sequence[float]) -> list:
+    """Propagate many grids (same dimension, dynamics and precision) in one
+    launch on the first grid's stream; returns their Stats."""
+    import torch
+
+    count = len(grids)
+    nbytes = gbees_batch_workspace_bytes(count)
+    if nbytes == 0:
+        raise GbeesError(GBEES_EINVAL, "empty batch")
+    dev = grids[0].device
+    with torch.cuda.device(dev):
+        scratch = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    stats = (gbees_stats * count)()
+    rc = gbees_batch_propagate([g.ctx for g in grids], np.asarray(t_end, dtype=np.float64), scratch.data_ptr(),
+                               nbytes, stats)
+    if rc != 0:
+        msgs = [gbees_last_error(g.ctx) for g in grids if g.status != 0] or [gbees_last_error(grids[0].ctx)]
+        raise GbeesError(rc, "batch: " + msgs[0])
+    return [Stats.of(stats[i]) for i in range(count)]
 
 
 def grid_for_workload(w, precision: int = GBEES_FP64, max_cells: int = 1 << 20, device: str = "cuda:0",

@@ -146,6 +146,36 @@ def lorenz96(h: float = 0.25, t_end: float = 1.0, thr_rel: float = 1e-6, cfl: fl
                     t_end=t_end, prune_interval=prune_interval, limiter=limiter)
 
 
+def lorenz63_batch(count: int = 256, seed: int = 2509, thr_rel: float = 1e-7, cfl: float = 0.9,
+                   prune_interval: int = 20, h_choices=(0.25, 0.5), t_range=(0.25, 1.0),
+                   sigma_range=(0.5, 2.0)) -> List[Workload]:
+    """Independent classic Lorenz '63 grids for the batched propagation: means
+    uniform in [-15, 15] x [-20, 20] x [5, 40], diagonal standard deviations
+    uniform in sigma_range per axis, cell width drawn from h_choices, end times
+    uniform in t_range (ragged grids of 10^3-10^5 cells). NumPy PCG64(seed)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(count):
+        mean = (rng.uniform(-15, 15), rng.uniform(-20, 20), rng.uniform(5, 40))
+        sig = rng.uniform(sigma_range[0], sigma_range[1], 3)
+        h = float(h_choices[int(rng.integers(len(h_choices)))])
+        t_end = float(rng.uniform(t_range[0], t_range[1]))
+        out.append(Workload(name=f"lorenz63_batch{count}_{i}", n=3, dynamics=DYN_LORENZ63, params=L63_PARAMS,
+                            h=(h, h, h), mean=tuple(float(x) for x in mean), cov=np.diag(sig ** 2),
+                            thr_rel=thr_rel, cfl=cfl, t_end=t_end, prune_interval=prune_interval))
+    return out
+
+
+def initial_cells_estimate(w: Workload) -> float:
+    """Cells of the initial set: the volume of the ellipsoid p > thr * max p in
+    cell units (a sizing aid for the capacity, not part of the method)."""
+    r2 = -2.0 * np.log(w.thr_rel)
+    n = w.n
+    unit_ball = np.pi ** (n / 2) / math.gamma(n / 2 + 1)
+    vol = unit_ball * r2 ** (n / 2) * np.sqrt(np.linalg.det(w.cov)) / np.prod(w.h)
+    return float(vol)
+
+
 def config(name: str) -> Workload:
     """The named workloads of the benchmark and the parity tests."""
     if name == "lorenz63_h0.5":

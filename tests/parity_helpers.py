@@ -8,6 +8,26 @@ from oracle.oracle import Oracle
 from paper_2508_13986_gb300 import gbees
 
 
+# tolerances of the parity bar: FP64 L1 over the union of the active sets;
+# FP32 store: L1 and relative error of mean and covariance
+FP64_L1 = 1e-10
+FP32_L1 = 1e-5
+FP32_MOM = 1e-4
+
+
+def assert_fp64_parity(g, o, w, gst=None, ost=None):
+    """Identical active sets, L1 within FP64_L1, and (with the propagate stats)
+    the same steps, times and cell updates."""
+    same, l1, ng, no, only_g, only_o = compare(g, o, w.h)
+    assert same, f"active sets differ: gpu {ng} oracle {no}; only gpu {only_g[:5]} only oracle {only_o[:5]}"
+    assert l1 <= FP64_L1, l1
+    if gst is not None:
+        assert [s.steps for s in gst] == [s.steps for s in ost]
+        assert [s.t for s in gst] == [s.t for s in ost]
+        assert sum(s.cell_updates for s in gst) == sum(s.cell_updates for s in ost)
+    return l1
+
+
 def make_pair(w, precision=gbees.GBEES_FP64, max_cells=1 << 20, probe_width=1, table_factor=2.0):
     g = gbees.grid_for_workload(w, precision=precision, max_cells=max_cells, probe_width=probe_width,
                                 table_factor=table_factor)

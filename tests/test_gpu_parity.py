@@ -9,30 +9,16 @@ import pytest
 from oracle.oracle import LIM_LW, LIM_MC, LIM_NONE, Oracle
 from paper_2508_13986_gb300 import gbees
 from paper_2508_13986_gb300 import workloads as W
-from parity_helpers import compare, make_pair, run_schedule
+from parity_helpers import FP32_L1, FP32_MOM, FP64_L1, assert_fp64_parity, compare, make_pair, run_schedule
 
 pytestmark = pytest.mark.gpu
 
-FP64_L1 = 1e-10
-FP32_L1 = 1e-5
-FP32_MOM = 1e-4
 
 
 @pytest.fixture(scope="module", autouse=True)
 def built():
     import __graft_entry__ as ge
     ge.build()
-
-
-def assert_fp64_parity(g, o, w, gst=None, ost=None):
-    same, l1, ng, no, only_g, only_o = compare(g, o, w.h)
-    assert same, f"active sets differ: gpu {ng} oracle {no}; only gpu {only_g[:5]} only oracle {only_o[:5]}"
-    assert l1 <= FP64_L1, l1
-    if gst is not None:
-        assert [s.steps for s in gst] == [s.steps for s in ost]
-        assert [s.t for s in gst] == [s.t for s in ost]
-        assert sum(s.cell_updates for s in gst) == sum(s.cell_updates for s in ost)
-    return l1
 
 
 def test_lorenz63_short_fp64():
