@@ -316,12 +316,12 @@ def time_precision(args, w, precision, dev, rank, world):
 
 def batch_capacity(w) -> int:
     """Pool capacity of one batched grid: room for the initial set growing
-    six-fold with its halo (a power of two, 2^15..2^22)."""
+    24-fold with its halo by t = 1 (a power of two, 2^15..2^23)."""
     from paper_2508_13986_gb300 import workloads
 
-    want = 6.0 * workloads.initial_cells_estimate(w) + 4096
+    want = 24.0 * workloads.initial_cells_estimate(w) + 4096
     cap = 1 << 15
-    while cap < want and cap < (1 << 22):
+    while cap < want and cap < (1 << 23):
         cap <<= 1
     return cap
 

@@ -212,9 +212,11 @@ __device__ __forceinline__ long long insert_cell(const Model& m, const Bufs& b, 
 //
 // The candidates of a cell (2n faces, 4 C(n,2) edges, those that are not
 // downwind skipped at once) are independent chains of dependent loads and
-// atomics; the (cell, candidate) pairs of the qualifying cells of a warp are
-// spread over its lanes. Returns the largest CFL rate of the halo cells this
-// thread activated (inserted cells get theirs in the link phase).
+// atomics. Cells that qualify cluster in storage order (the cells a grow adds
+// are appended together), so the qualifying cells of all warps of the block
+// are gathered in shared memory and their (cell, candidate) pairs spread over
+// all threads of the block. Returns the largest CFL rate of the halo cells
+// this thread activated (inserted cells get theirs in the link phase).
 template <int N, typename T>
 __device__ __forceinline__ double grow_body(const Model& m, const Bufs& b, const StepView& v) {
     constexpr int K = 2 * N + 2 * N * (N - 1);  // candidates per cell
@@ -226,9 +228,8 @@ __device__ __forceinline__ double grow_body(const Model& m, const Bufs& b, const
     const int* link = b.link[v.g];
     unsigned short* om = b.om[v.g];
     const long long cap = m.cap;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __shared__ long long s_cell[WARPS][32];
-    __shared__ unsigned s_out[WARPS][32];
+    __shared__ long long s_cell[THREADS];
+    __shared__ unsigned s_out[THREADS];
     double rmax = 0.0;
     auto make_active = [&](long long e) {
         if (!(om[e] & OM_GHOST) || !activate(om, e)) return;
@@ -281,28 +282,34 @@ __device__ __forceinline__ double grow_body(const Model& m, const Bufs& b, const
         if (d2 >= 0) J[d2 >> 1] += (d2 & 1) ? 1 : -1;
         insert_active(J);
     };
-    for (WarpRuns r(ncell, v.nb, v.bi); r.next();) {
-        const long long c = r.c;
+    // rounds of one run of 32 cells per warp; the block's first warp has the most
+    const long long runs = (ncell + 31) / 32;
+    const long long stride = (long long)v.nb * (blockDim.x >> 5);
+    const long long rounds = runs > v.bi ? (runs - v.bi + stride - 1) / stride : 0;
+    const int wid = threadIdx.x >> 5;
+    for (long long rd = 0; rd < rounds; ++rd) {
+        const long long k = v.bi + (long long)v.nb * wid + stride * rd;
+        const long long c = k * 32 + (threadIdx.x & 31);
         unsigned f = 0;
         bool q = false;
-        if (c < ncell && (double)Q[c] > pstar) {
+        if (k < runs && c < ncell && (double)Q[c] > pstar) {
             f = om[c];
             q = !(f & (OM_COMPLETE | OM_GHOST)) && (f & 0xfffu);
         }
-        const unsigned qm = __ballot_sync(0xffffffffu, q);
-        if (!qm) continue;
+        int nq;
+        const int pos = block_exclusive_scan(q, nq);
+        if (nq == 0) continue;
         if (q) {
-            const int pos = __popc(qm & ((1u << lane) - 1u));
-            s_cell[wid][pos] = c;
-            s_out[wid][pos] = f & 0xfffu;
+            s_cell[pos] = c;
+            s_out[pos] = f & 0xfffu;
         }
-        __syncwarp();
-        const int pairs = __popc(qm) * K;
-        for (int t = lane; t < pairs; t += 32) {
+        __syncthreads();
+        const int pairs = nq * K;
+        for (int t = threadIdx.x; t < pairs; t += blockDim.x) {
             const int rank = t / K;
-            candidate(s_cell[wid][rank], s_out[wid][rank], t - rank * K);
+            candidate(s_cell[rank], s_out[rank], t - rank * K);
         }
-        __syncwarp();
+        __syncthreads();
         if (q) om[c] = (unsigned short)(f | OM_COMPLETE);
     }
     return rmax;
