@@ -57,6 +57,8 @@ def parse():
                     help="seconds of oracle work for cpu_baseline (0: skip, for grids the oracle cannot initialise quickly)")
     ap.add_argument("--max-cells", type=int, default=1 << 22)
     ap.add_argument("--launch-mode", choices=["auto", "persistent", "graph", "direct"], default="auto")
+    ap.add_argument("--requests", type=int, default=100, help="requests of the serving stream (--workload serving)")
+    ap.add_argument("--rate", type=float, default=50.0, help="arrival rate per second of the serving stream")
     ap.add_argument("--t-end", type=float, default=None,
                     help="stop the workload at this time (large-grid runs); the default is its own t_end")
     return ap.parse_args()
@@ -314,27 +316,15 @@ def time_precision(args, w, precision, dev, rank, world):
     }
 
 
-def batch_capacity(w) -> int:
-    """Pool capacity of one batched grid: room for the initial set growing
-    24-fold with its halo by t = 1 (a power of two, 2^15..2^23)."""
-    from paper_2508_13986_gb300 import workloads
-
-    want = 24.0 * workloads.initial_cells_estimate(w) + 4096
-    cap = 1 << 15
-    while cap < want and cap < (1 << 23):
-        cap <<= 1
-    return cap
-
-
 def time_batch(args, ws, precision, dev, rank, world):
     """Many independent grids per step: the initial Gaussians of all grids and
     one batched propagation of all of them to their own end times."""
     import torch
 
-    from paper_2508_13986_gb300 import gbees
+    from paper_2508_13986_gb300 import gbees, workloads
 
     prec = gbees.GBEES_FP64 if precision == "f64" else gbees.GBEES_FP32
-    grids = [gbees.grid_for_workload(w, precision=prec, max_cells=batch_capacity(w), device=f"cuda:{dev}")
+    grids = [gbees.grid_for_workload(w, precision=prec, max_cells=workloads.capacity_for(w), device=f"cuda:{dev}")
              for w in ws]
     stream = grids[0].stream
     t_ends = [w.t_end for w in ws]
@@ -389,6 +379,8 @@ def time_batch(args, ws, precision, dev, rank, world):
         e2e_updates += u
     for g in grids:
         g.close()
+    del grids
+    torch.cuda.empty_cache()
     ms_max = reduce_max(total_ms, world)
     upd_sum = reduce_sum(total_updates, world)
     e2e_max = reduce_max(e2e_ms, world)
@@ -426,6 +418,44 @@ def time_batch(args, ws, precision, dev, rank, world):
         "gpu_launches": launches,
         "clocks": clk,
     }
+
+
+def main_serving(args):
+    """The request stream served three ways on one GPU: batched FP32, batched
+    FP64, and the plain FP64 form (one request at a time, gbees_propagate)."""
+    import torch
+
+    from paper_2508_13986_gb300 import gbees, workloads
+    from paper_2508_13986_gb300.serving import Server
+
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    stream = workloads.serving_stream(count=args.requests, rate=args.rate)
+    warm = workloads.serving_stream(count=8, rate=1000.0, seed=7)
+    out = {}
+    for tag, prec, mode in (("batched_f32", gbees.GBEES_FP32, "batched"), ("batched_f64", gbees.GBEES_FP64, "batched"),
+                            ("single_f64", gbees.GBEES_FP64, "single")):
+        Server(precision=prec, device=f"cuda:{local}", mode=mode, realtime=False).run(warm)
+        clocks = ClockSampler(local)
+        clocks.start()
+        srv = Server(precision=prec, device=f"cuda:{local}", mode=mode, realtime=True)
+        srv.run(stream)
+        st = dict(srv.stats)
+        st["clocks"] = clocks.stop()
+        out[tag] = st
+    main = out["batched_f32"]
+    print(json.dumps({
+        "metric": METRIC, "value": main["cell_updates_per_s"], "unit": METRIC, "n_gpus": 1, "steps": 1, "warmup": 1,
+        "ms_per_step": main["wall_s"] * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "serving", "requests": args.requests, "rate_per_s": args.rate,
+                   "mix": "70 % Lorenz '63 (batch distributions), 30 % Lorenz '96 6-D; 0-3 corrections each",
+                   "pool_bytes": 120 << 30, "round_steps": 64,
+                   "timing": "wall clock from the first arrival to the last completion (arrivals in real time)"},
+        "serving": out,
+    }))
 
 
 def cpu_baseline(w, budget_s):
@@ -597,5 +627,7 @@ if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         main_reference(a)
+    elif a.workload == "serving":
+        main_serving(a)
     else:
         main_ours(a)

@@ -169,14 +169,18 @@ int gbees_propagate(gbees_ctx* ctx, double t_end, gbees_stats* stats);
  * fit on the GPU at once, each grid gets a team of thread blocks in proportion
  * to its work (active cells x remaining time / h; cooperative launch, a
  * barrier per team); otherwise each block takes the next grid from a queue
- * and runs its whole step loop alone. d_scratch: device memory of
- * gbees_batch_workspace_bytes(count) bytes, 256-byte aligned, owned by the
- * caller. stats: NULL or count entries. Returns the first error of any grid
- * (that grid's context is poisoned as by gbees_propagate), GBEES_EINVAL for
- * mismatched contexts. The contexts must have no work in flight. */
+ * and runs its whole step loop alone. max_steps = 0 runs every grid to its
+ * t_end; max_steps > 0 makes one launch in which every grid takes at most
+ * max_steps steps (a round of a serving loop: stats[i].t < t_end[i] tells
+ * that grid i is not there yet, and the next call continues). d_scratch:
+ * device memory of gbees_batch_workspace_bytes(count) bytes, 256-byte
+ * aligned, owned by the caller. stats: NULL or count entries. Returns the
+ * first error of any grid (that grid's context is poisoned as by
+ * gbees_propagate), GBEES_EINVAL for mismatched contexts. The contexts must
+ * have no work in flight. */
 size_t gbees_batch_workspace_bytes(int32_t count);
-int gbees_batch_propagate(gbees_ctx* const* ctxs, int32_t count, const double* t_end, void* d_scratch,
-                          size_t scratch_bytes, gbees_stats* stats);
+int gbees_batch_propagate(gbees_ctx* const* ctxs, int32_t count, const double* t_end, int64_t max_steps,
+                          void* d_scratch, size_t scratch_bytes, gbees_stats* stats);
 
 /* Bayesian measurement update (Eq. 4) with the Gaussian likelihood
  * exp(-1/2 (y - x_H)^T R^{-1} (y - x_H)) of m measured components

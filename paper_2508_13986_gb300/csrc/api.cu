@@ -967,9 +967,9 @@ std::vector<int> team_sizes(gbees_ctx* const* ctxs, int32_t count, const double*
 
 size_t gbees_batch_workspace_bytes(int32_t count) { return count < 1 ? 0 : batch_layout(count).total; }
 
-int gbees_batch_propagate(gbees_ctx* const* ctxs, int32_t count, const double* t_end, void* d_scratch,
-                          size_t scratch_bytes, gbees_stats* stats) {
-    if (!ctxs || count < 1 || !t_end || !d_scratch) return GBEES_EINVAL;
+int gbees_batch_propagate(gbees_ctx* const* ctxs, int32_t count, const double* t_end, int64_t max_steps,
+                          void* d_scratch, size_t scratch_bytes, gbees_stats* stats) {
+    if (!ctxs || count < 1 || !t_end || !d_scratch || max_steps < 0) return GBEES_EINVAL;
     const BatchLayout L = batch_layout(count);
     if (scratch_bytes < L.total || ((uintptr_t)d_scratch % ALIGN) != 0) return GBEES_EINVAL;
     gbees_ctx* c0 = ctxs[0];
@@ -1036,13 +1036,14 @@ int gbees_batch_propagate(gbees_ctx* const* ctxs, int32_t count, const double* t
     }
     std::vector<DevScalars> hs((size_t)count);
     std::vector<long long> steps_before((size_t)count, -1), upd_before((size_t)count, 0);
-    long long max_steps = kBatchSteps;
+    const bool one_launch = max_steps > 0;
+    long long launch_steps = one_launch ? max_steps : kBatchSteps;
     for (auto& e : c0->pev)
         if (!e && !cuda_ok(c0, cudaEventCreate(&e), "batch_propagate")) return c0->status;
     for (int round = 0;; ++round) {
         if (!cuda_ok(c0, cudaMemsetAsync(next, 0, sizeof(unsigned int), s), "batch_propagate")) return c0->status;
-        void* args[] = {&items, &count, &next, &max_steps};
-        void* targs[] = {&items, &slots, &max_steps};
+        void* args[] = {&items, &count, &next, &launch_steps};
+        void* targs[] = {&items, &slots, &launch_steps};
         cudaEventRecord(c0->pev[0], s);
         const cudaError_t le = teams ? cudaLaunchCooperativeKernel(c0->kern.batch_teams, dim3(G), dim3(THREADS), targs, 0, s)
                                      : cudaLaunchKernel(c0->kern.batch, dim3(G), dim3(THREADS), args, 0, s);
@@ -1070,7 +1071,7 @@ int gbees_batch_propagate(gbees_ctx* const* ctxs, int32_t count, const double* t
             c0->prof.persist_launches += 1;
             c0->prof.persist_updates += upd;
         }
-        if (all_done) break;
+        if (all_done || one_launch) break;
         if (!progress) {
             set_err(c0, GBEES_ETIMEOUT, "batch_propagate: a launch made no progress");
             return c0->status;

@@ -101,7 +101,7 @@ _SIGNATURES = {
     "gbees_propagate_cells_noalloc": (ctypes.c_int, [_P(gbees_config), _P(_i32), _P(_d), _i64, _d, _i64, _d, _vp,
                                                      _P(_i32), _P(_d), _i64, _P(_i64), _P(gbees_stats)]),
     "gbees_batch_workspace_bytes": (ctypes.c_size_t, [_i32]),
-    "gbees_batch_propagate": (ctypes.c_int, [_P(_vp), _i32, _P(_d), _vp, ctypes.c_size_t, _P(gbees_stats)]),
+    "gbees_batch_propagate": (ctypes.c_int, [_P(_vp), _i32, _P(_d), _i64, _vp, ctypes.c_size_t, _P(gbees_stats)]),
 }
 GBEES_NOALLOC_SCRATCH_BYTES = 16 << 20
 
@@ -201,10 +201,11 @@ def gbees_batch_workspace_bytes(count: int) -> int:
     return int(_f("gbees_batch_workspace_bytes")(int(count)))
 
 
-def gbees_batch_propagate(ctxs: Sequence[int], t_end: np.ndarray, d_scratch: int, nbytes: int, stats) -> int:
+def gbees_batch_propagate(ctxs: Sequence[int], t_end: np.ndarray, max_steps: int, d_scratch: int, nbytes: int,
+                          stats) -> int:
     arr = (_vp * len(ctxs))(*[_vp(c) for c in ctxs])
     te = np.ascontiguousarray(t_end, dtype=np.float64)
-    return _f("gbees_batch_propagate")(arr, len(ctxs), _dp(te), _vp(d_scratch), nbytes, stats)
+    return _f("gbees_batch_propagate")(arr, len(ctxs), _dp(te), int(max_steps), _vp(d_scratch), nbytes, stats)
 
 
 def gbees_propagate_cells_noalloc(cfg: gbees_config, idx: np.ndarray, p: np.ndarray, t0: float, step0: int,
@@ -377,9 +378,10 @@ class Grid:
     _prof_on = False
 
 
-def propagate_batch(grids: Sequence["Grid"], t_end: Sequence[float]) -> list:
+def propagate_batch(grids: Sequence["Grid"], t_end: Sequence[float], max_steps: int = 0) -> list:
     """Propagate many grids (same dimension, dynamics and precision) in one
-    launch on the first grid's stream; returns their Stats."""
+    launch on the first grid's stream (max_steps > 0: at most that many steps
+    each); returns their Stats."""
     import torch
 
     count = len(grids)
@@ -390,8 +392,8 @@ def propagate_batch(grids: Sequence["Grid"], t_end: Sequence[float]) -> list:
     with torch.cuda.device(dev):
         scratch = torch.empty(nbytes, dtype=torch.uint8, device=dev)
     stats = (gbees_stats * count)()
-    rc = gbees_batch_propagate([g.ctx for g in grids], np.asarray(t_end, dtype=np.float64), scratch.data_ptr(),
-                               nbytes, stats)
+    rc = gbees_batch_propagate([g.ctx for g in grids], np.asarray(t_end, dtype=np.float64), max_steps,
+                               scratch.data_ptr(), nbytes, stats)
     if rc != 0:
         msgs = [gbees_last_error(g.ctx) for g in grids if g.status != 0] or [gbees_last_error(grids[0].ctx)]
         raise GbeesError(rc, "batch: " + msgs[0])

@@ -1,0 +1,203 @@
+"""Continuous-batching request loop over the GBEES C ABI.
+
+Requests (a grid's initial Gaussian, its measurement schedule and end time)
+arrive over time. The loop admits arrived requests in arrival order while the
+workspace bytes of the grids in service stay within a device-memory budget,
+keeps every admitted grid resident on the device between its propagation
+segments and measurement updates, and advances all grids in service together:
+one round is one batched launch per model family (dimension, dynamics) in which
+every grid takes at most `round_steps` steps towards its next segment target
+(gbees_batch_propagate with a step cap). Between rounds, grids that reached a
+measurement time get their Bayesian update (Eq. 4), finished grids are read
+out and released, and requests that arrived meanwhile join the next round.
+
+Every grid runs the same phases with the same arithmetic whether it is served
+alone or in a mix, so its result does not depend on the mix.
+
+mode "single" serves one request at a time with gbees_propagate (no batching),
+the plain form that the batched loop is compared with.
+"""
+from __future__ import annotations
+
+import time
+from collections import deque
+from dataclasses import dataclass, field
+from typing import Dict, List, Optional, Sequence, Tuple
+
+import numpy as np
+
+from . import gbees
+from .workloads import Workload, capacity_for
+
+
+@dataclass
+class Result:
+    rid: int
+    name: str
+    arrival: float       # seconds after the start of the stream
+    admitted: float
+    finished: float
+    steps: int
+    cell_updates: int
+    mean: np.ndarray
+    cov: np.ndarray
+    n_cells: int
+    idx: Optional[np.ndarray] = None
+    p: Optional[np.ndarray] = None
+    error: Optional[str] = None      # a grid that failed (e.g. out of capacity) ends with its status
+
+    @property
+    def latency(self) -> float:
+        return self.finished - self.arrival
+
+
+@dataclass
+class _Active:
+    rid: int
+    w: Workload
+    arrival: float
+    admitted: float
+    grid: gbees.Grid
+    nbytes: int
+    segments: List[Tuple[float, object]]
+    seg: int = 0
+    steps: int = 0
+    updates: int = 0
+
+
+@dataclass
+class Server:
+    precision: int = gbees.GBEES_FP32
+    device: str = "cuda:0"
+    pool_bytes: int = 120 << 30
+    round_steps: int = 64
+    mode: str = "batched"           # or "single"
+    keep_density: bool = False
+    realtime: bool = True            # arrivals follow the wall clock
+    stats: Dict[str, float] = field(default_factory=dict)
+
+    def _admit(self, rid: int, w: Workload, arrival: float, now: float) -> _Active:
+        cfg = gbees.make_config(w.n, w.dynamics, w.params, w.h, w.x0, w.thr_rel, w.cfl, w.prune_interval,
+                                self.precision, w.limiter, capacity_for(w))
+        g = gbees.Grid(cfg, self.device)
+        g.init_gaussian(w.mean, w.cov)
+        return _Active(rid, w, arrival, now, g, gbees.gbees_workspace_bytes(cfg), w.segments())
+
+    def _finish(self, a: _Active, now: float, error: Optional[str] = None) -> Result:
+        if error is None:
+            mean, cov = a.grid.moments()
+            idx = p = None
+            if self.keep_density:
+                idx, p = a.grid.read_cells()
+            r = Result(a.rid, a.w.name, a.arrival, a.admitted, now, a.steps, a.updates, mean, cov, a.grid.count(),
+                       idx, p)
+        else:
+            r = Result(a.rid, a.w.name, a.arrival, a.admitted, now, a.steps, a.updates, np.full(a.w.n, np.nan),
+                       np.full((a.w.n, a.w.n), np.nan), 0, error=error)
+        a.grid.close()
+        return r
+
+    def _advance_segment(self, a: _Active) -> bool:
+        """After the grid reached its current target: the measurement update if
+        one is due; True when the request is complete."""
+        t_target, meas = a.segments[a.seg]
+        if meas is not None:
+            a.grid.correct_gaussian(meas.y, meas.R, meas.H_idx)
+        a.seg += 1
+        return a.seg >= len(a.segments)
+
+    def run(self, stream: Sequence[Tuple[float, Workload]]) -> List[Result]:
+        import torch
+
+        t0 = time.perf_counter()
+        clock = (lambda: time.perf_counter() - t0) if self.realtime else None
+        pending = deque((rid, arr, w) for rid, (arr, w) in enumerate(sorted(stream, key=lambda x: x[0])))
+        active: List[_Active] = []
+        results: List[Result] = []
+        used = 0
+        rounds = 0
+        max_active = max_used = 0
+        virtual_now = 0.0
+        while pending or active:
+            now = clock() if clock else virtual_now
+            # admission in arrival order while the memory budget allows
+            while pending and (pending[0][1] <= now or not self.realtime):
+                rid, arr, w = pending[0]
+                if not self.realtime:
+                    virtual_now = max(virtual_now, arr)
+                need = gbees.gbees_workspace_bytes(gbees.make_config(
+                    w.n, w.dynamics, w.params, w.h, w.x0, w.thr_rel, w.cfl, w.prune_interval, self.precision,
+                    w.limiter, capacity_for(w)))
+                if active and used + need > self.pool_bytes:
+                    break
+                if self.mode == "single" and active:
+                    break
+                pending.popleft()
+                a = self._admit(rid, w, arr, now if clock else virtual_now)
+                active.append(a)
+                used += a.nbytes
+                max_active = max(max_active, len(active))
+                max_used = max(max_used, used)
+            if not active:
+                if pending and clock:
+                    time.sleep(max(0.0, min(0.002, pending[0][1] - clock())))
+                continue
+            # one round: every grid in service towards its next target
+            rounds += 1
+            failed: List[_Active] = []
+            reached: List[_Active] = []
+            if self.mode == "single":
+                a = active[0]
+                try:
+                    st = a.grid.propagate(a.segments[a.seg][0])
+                    a.steps += st.steps
+                    a.updates += st.cell_updates
+                    reached.append(a)
+                except gbees.GbeesError:
+                    failed.append(a)
+            else:
+                families: Dict[Tuple[int, int], List[_Active]] = {}
+                for a in active:
+                    families.setdefault((a.w.n, a.w.dynamics), []).append(a)
+                for members in families.values():
+                    targets = [m.segments[m.seg][0] for m in members]
+                    try:
+                        sts = gbees.propagate_batch([m.grid for m in members], targets, max_steps=self.round_steps)
+                    except gbees.GbeesError:
+                        sts = [m.grid.stats() if m.grid.status == 0 else None for m in members]
+                    for m, s, tt in zip(members, sts, targets):
+                        if s is None:
+                            failed.append(m)
+                            continue
+                        m.steps = s.total_steps
+                        m.updates += s.cell_updates
+                        if s.t == tt:
+                            reached.append(m)
+            torch.cuda.synchronize(self.device)
+            done_now = clock() if clock else virtual_now
+            for a in failed:
+                results.append(self._finish(a, done_now, error=gbees.STATUS_NAMES.get(a.grid.status, "error")))
+                active.remove(a)
+                used -= a.nbytes
+            for a in reached:
+                if self._advance_segment(a):
+                    results.append(self._finish(a, clock() if clock else done_now))
+                    active.remove(a)
+                    used -= a.nbytes
+        elapsed = time.perf_counter() - t0
+        lat = np.array([r.latency for r in results]) if results else np.zeros(1)
+        self.stats = {
+            "requests": len(results),
+            "failed": sum(r.error is not None for r in results),
+            "rounds": rounds,
+            "max_active": max_active,
+            "max_used_bytes": max_used,
+            "wall_s": elapsed,
+            "cell_updates": float(sum(r.cell_updates for r in results)),
+            "cell_updates_per_s": float(sum(r.cell_updates for r in results)) / elapsed,
+            "requests_per_s": len(results) / elapsed,
+            "latency_p50_s": float(np.percentile(lat, 50)),
+            "latency_p99_s": float(np.percentile(lat, 99)),
+            "latency_max_s": float(lat.max()),
+        }
+        return sorted(results, key=lambda r: r.rid)

@@ -105,14 +105,15 @@ def truth_trajectory(rhs, x0: np.ndarray, times: Sequence[float], dt: float = 1e
     return out
 
 
-def gaussian_measurements(rhs, mean, cov0, times, R, seed: int) -> List[Measurement]:
+def gaussian_measurements(rhs, mean, cov0, times, R, seed: int, dt: float = 1e-4) -> List[Measurement]:
     """Full-state measurements y_k = x(t_k) + nu_k of a truth started at mean + xi,
-    xi ~ N(0, cov0), nu_k ~ N(0, R); NumPy PCG64 with the given seed."""
+    xi ~ N(0, cov0), nu_k ~ N(0, R); NumPy PCG64 with the given seed; the truth
+    is integrated by RK4 with step dt."""
     rng = np.random.Generator(np.random.PCG64(seed))
     n = len(mean)
     L0 = np.linalg.cholesky(np.asarray(cov0, dtype=np.float64))
     x0 = np.asarray(mean, dtype=np.float64) + L0 @ rng.standard_normal(n)
-    xs = truth_trajectory(rhs, x0, times)
+    xs = truth_trajectory(rhs, x0, times, dt)
     LR = np.linalg.cholesky(np.asarray(R, dtype=np.float64))
     out = []
     for t, x in zip(times, xs):
@@ -166,6 +167,42 @@ def lorenz63_batch(count: int = 256, seed: int = 2509, thr_rel: float = 1e-7, cf
     return out
 
 
+def serving_stream(count: int = 1000, rate: float = 50.0, seed: int = 2510, frac_l63: float = 0.7,
+                   l96_sigma: float = 0.5, l96_h: float = 0.5, l96_t=(0.1, 0.5), l63_kw=None,
+                   max_corrections: int = 3) -> List[Tuple[float, Workload]]:
+    """A seeded stream of propagation requests: Poisson arrivals at `rate` per
+    second; a fraction frac_l63 are Lorenz '63 grids drawn like lorenz63_batch,
+    the rest Lorenz '96 6-D grids (means 4 + N(0, 0.1^2) per component,
+    standard deviation l96_sigma, h = l96_h, thr 1e-6, t_end uniform in l96_t).
+    Each request carries 0..max_corrections full-state Gaussian measurements
+    (R = 0.25 I) equally spaced in (0, t_end), drawn from a truth trajectory
+    started at the mean plus N(0, cov) (RK4, step 5e-3). Returns (arrival
+    seconds, workload)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    l63 = lorenz63_batch(count=count, seed=seed + 1, **(l63_kw or {}))
+    out = []
+    t = 0.0
+    for i in range(count):
+        t += float(rng.exponential(1.0 / rate))
+        if rng.random() < frac_l63:
+            w = l63[i]
+            rhs = lambda x: _l63_rhs(x, L63_PARAMS)  # noqa: E731
+        else:
+            n = 6
+            mean = tuple(float(x) for x in 4.0 + 0.1 * rng.standard_normal(n))
+            t_end = float(rng.uniform(*l96_t))
+            w = Workload(name=f"lorenz96_{n}d_req{i}", n=n, dynamics=DYN_LORENZ96, params=(4.0,),
+                         h=tuple([l96_h] * n), mean=mean, cov=l96_sigma ** 2 * np.eye(n), thr_rel=1e-6, cfl=0.9,
+                         t_end=t_end, prune_interval=20)
+            rhs = lambda x: _l96_rhs(x, 4.0)  # noqa: E731
+        m = int(rng.integers(0, max_corrections + 1))
+        times = [w.t_end * (k + 1) / (m + 1) for k in range(m)]
+        meas = gaussian_measurements(rhs, np.asarray(w.mean), w.cov, times, 0.25 * np.eye(w.n),
+                                     seed=seed * 1000 + i, dt=5e-3) if m else []
+        out.append((t, w.with_(name=f"req{i}_{w.name}", measurements=meas)))
+    return out
+
+
 def initial_cells_estimate(w: Workload) -> float:
     """Cells of the initial set: the volume of the ellipsoid p > thr * max p in
     cell units (a sizing aid for the capacity, not part of the method)."""
@@ -174,6 +211,17 @@ def initial_cells_estimate(w: Workload) -> float:
     unit_ball = np.pi ** (n / 2) / math.gamma(n / 2 + 1)
     vol = unit_ball * r2 ** (n / 2) * np.sqrt(np.linalg.det(w.cov)) / np.prod(w.h)
     return float(vol)
+
+
+def capacity_for(w: Workload) -> int:
+    """Pool capacity (active plus halo entries) for propagating w to its t_end:
+    the initial set times a growth bound measured on GB300 runs of these
+    workloads (Lorenz '63: at most 36x by t = 1; Lorenz '96 6-D: at most 50x by
+    t = 0.5), with margin, rounded up to a multiple of 4096 in 2^15..2^24. A
+    sizing aid, not part of the method."""
+    growth = 4.0 + (56.0 if w.n <= 3 else 120.0) * max(w.t_end, 0.0)
+    want = growth * initial_cells_estimate(w) + 4096
+    return int(min(1 << 24, max(1 << 15, math.ceil(want / 4096.0) * 4096)))
 
 
 def config(name: str) -> Workload:
