@@ -920,12 +920,14 @@ BatchLayout batch_layout(int32_t count) {
     return L;
 }
 constexpr long long kBatchSteps = 1ll << 20;  // steps per grid and launch at most
-constexpr int kMaxTeam = 32;                  // blocks per grid in a team launch at most
+constexpr int kMaxTeam = 256;                 // blocks per grid in a team launch at most
 
 // Team sizes of a team launch over G resident blocks: one block per grid plus
-// the rest in proportion to each grid's work (active cells x remaining time /
-// smallest cell width, the step count scaling as 1/h), at most kMaxTeam.
-std::vector<int> team_sizes(gbees_ctx* const* ctxs, int32_t count, const double* t_end, int G) {
+// the rest in proportion to each grid's work, at most kMaxTeam. Without a step
+// cap the work is the whole run (active cells x remaining time / smallest
+// cell width, the step count scaling as 1/h); with one (every grid takes the
+// same number of steps) it is the work of a step (active cells).
+std::vector<int> team_sizes(gbees_ctx* const* ctxs, int32_t count, const double* t_end, int G, bool per_step) {
     std::vector<double> w((size_t)count, 0.0);
     double W = 0.0;
     for (int32_t i = 0; i < count; ++i) {
@@ -933,7 +935,8 @@ std::vector<int> team_sizes(gbees_ctx* const* ctxs, int32_t count, const double*
         double hmin = c->cfg.h[0];
         for (int j = 1; j < c->cfg.n; ++j) hmin = std::min(hmin, c->cfg.h[j]);
         const double rem = t_end[i] - c->hs.t;
-        w[i] = rem > 0.0 ? (double)std::max(1ll, c->hs.NA) * rem / hmin : 0.0;
+        const double cells = (double)std::max(1ll, c->hs.NA);
+        w[i] = rem > 0.0 ? (per_step ? cells : cells * rem / hmin) : 0.0;
         W += w[i];
     }
     std::vector<int> k((size_t)count, 1);
@@ -1025,7 +1028,7 @@ int gbees_batch_propagate(gbees_ctx* const* ctxs, int32_t count, const double* t
     cudaGetLastError();
     if (teams) {
         const int Gt = std::min(GRID_MAX, sms * per_sm_team);
-        const std::vector<int> k = team_sizes(ctxs, count, t_end, Gt);
+        const std::vector<int> k = team_sizes(ctxs, count, t_end, Gt, max_steps > 0);
         std::vector<TeamSlot> h_slots;
         for (int32_t i = 0; i < count; ++i)
             for (int j = 0; j < k[i]; ++j) h_slots.push_back(TeamSlot{(int)i, k[i], j});
