@@ -485,26 +485,26 @@ def barrier(world):
         dist.barrier()
 
 
-def reduce_max(x, world):
+def _reduce(x, world, op_name):
+    """All-reduce one number over the replicas (a CUDA tensor under NCCL, a CPU
+    tensor under gloo)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([float(x)], device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=getattr(dist.ReduceOp, op_name))
     return float(t.item())
+
+
+def reduce_max(x, world):
+    return _reduce(x, world, "MAX")
 
 
 def reduce_sum(x, world):
-    if world == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-
-    t = torch.tensor([float(x)], device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return _reduce(x, world, "SUM")
 
 
 def main_ours(args):

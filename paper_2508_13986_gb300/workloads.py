@@ -224,8 +224,34 @@ def capacity_for(w: Workload) -> int:
     return int(min(1 << 24, max(1 << 15, math.ceil(want / 4096.0) * 4096)))
 
 
+def paper_e1(thr_rel: float = 1e-7, prune_interval: int = 20) -> Workload:
+    """The paper's Lorenz '63 validation case (Sec. 5.1.1): the shifted form with
+    (sigma, b, r) = (4, 1, 48), initial Gaussian at (-11.5, -10, 9.5) with unit
+    standard deviations, h = 0.5 (half the standard deviation, Table 2), CFL
+    1.0, a measurement y = x3 = -8 with sigma_y = 1 at t = 1, end at t = 2. The
+    paper does not state its threshold: thr_rel is this library's reading."""
+    meas = [Measurement(1.0, np.array([-8.0]), np.array([[1.0]]), np.array([2], dtype=np.int32))]
+    return Workload(name="paper_e1", n=3, dynamics=DYN_LORENZ63_SHIFTED, params=(4.0, 1.0, 48.0),
+                    h=(0.5, 0.5, 0.5), mean=(-11.5, -10.0, 9.5), cov=np.eye(3), thr_rel=thr_rel, cfl=1.0,
+                    t_end=2.0, prune_interval=prune_interval, measurements=meas)
+
+
+def paper_e2(thr_rel: float = 1e-6, prune_interval: int = 20) -> Workload:
+    """The paper's Lorenz '96 validation case (Sec. 5.1.2): n = 6, F = 4, initial
+    Gaussian at (F + 0.5, F, ..., F) with standard deviations 0.2, h = 0.1,
+    CFL 1.0, no measurement, end at t = 1.3 (Table 2: about 5e7 cells)."""
+    F = 4.0
+    return Workload(name="paper_e2", n=6, dynamics=DYN_LORENZ96, params=(F,), h=tuple([0.1] * 6),
+                    mean=tuple([F + 0.5] + [F] * 5), cov=0.04 * np.eye(6), thr_rel=thr_rel, cfl=1.0, t_end=1.3,
+                    prune_interval=prune_interval)
+
+
 def config(name: str) -> Workload:
     """The named workloads of the benchmark and the parity tests."""
+    if name == "paper_e1":
+        return paper_e1()
+    if name == "paper_e2":
+        return paper_e2()
     if name == "lorenz63_h0.5":
         return lorenz63(h=0.5, t_end=0.5)
     if name == "lorenz63_h0.25":

@@ -263,3 +263,21 @@ def test_profiled_direct_path_times_every_phase():
     for k in ("grow", "halo", "link", "faces", "apply"):
         assert prof["timed"][k] >= st.steps and prof["ms"][k] > 0
     assert prof["timed"]["grow"] >= st.steps and prof["launches"]["prune"] >= 5
+
+
+def test_paper_e1_shifted_lorenz63_with_x3_measurement_fp64():
+    """The paper's Lorenz '63 case (shifted form, CFL 1.0, a measurement of x3
+    alone), with its measurement moved to t = 0.15 and the end to t = 0.3 so
+    that the oracle finishes in seconds."""
+    e1 = W.paper_e1()
+    m = e1.measurements[0]
+    w = e1.with_(t_end=0.3, measurements=[W.Measurement(0.15, m.y, m.R, m.H_idx)])
+    g, o = make_pair(w, max_cells=1 << 17)
+    g.init_gaussian(w.mean, w.cov)
+    o.init_gaussian(w.mean, w.cov)
+    gst, ost = run_schedule(g, o, w)
+    assert_fp64_parity(g, o, w, gst, ost)
+    gm, gc = g.moments()
+    om, oc = o.moments()
+    np.testing.assert_allclose(gm, om, atol=1e-12)
+    np.testing.assert_allclose(gc, oc, atol=1e-12)
