@@ -39,7 +39,12 @@ DEFAULT_WORKLOAD = "lorenz63_h0.25"
 # (dram__bytes_read.sum + dram__bytes_write.sum of the launch divided by the
 # cell updates it made), keyed by workload/precision; valid only while the
 # device sources have the recorded hash (null otherwise).
-TRAFFIC_BYTES_PER_CELL = {}
+TRAFFIC_BYTES_PER_CELL = {
+    # k_persistent, third launch of `bench.py --steps 1 --warmup 1 --no-secondary --cpu-budget 0
+    # --max-cells 1048576` (segment t = 0.5..0.75: 2118979 cell updates, counted by the oracle):
+    # 9.268 MB read + 1.092 MB written
+    "lorenz63_h0.25/f64": {"bytes_per_cell": 10.360832e6 / 2118979, "src": "c00cd41fc877901a"},
+}
 DEVICE_SOURCES = [os.path.join(ROOT, "paper_2508_13986_gb300", "csrc", f)
                   for f in ("gbees_device.cuh", "gbees_phases.cuh", "gbees_kernels.cuh", "gbees_persistent.cuh")]
 
