@@ -97,7 +97,7 @@ constexpr size_t ALIGN = 256;
 size_t align_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
 
 struct Layout {
-    size_t sc, blk, part, key[2], q[2], link[2], om[2], slot[2], keep, map, table, wv_u, wv_g, fl, total;
+    size_t sc, blk, part, sorthist, key[2], q[2], link[2], om[2], slot[2], keep, map, table, wv_u, wv_g, fl, total;
     unsigned long long slots;
 };
 
@@ -159,6 +159,7 @@ bool make_layout(const gbees_config* c, Layout* L) {
     L->sc = take(sizeof(DevScalars));
     L->blk = take(sizeof(long long) * 2 * (GRID_MAX + 1));
     L->part = take(sizeof(Partial) * GRID_MAX);
+    L->sorthist = take(sizeof(unsigned int) * 256 * SORT_BLOCKS);
     for (int g = 0; g < 2; ++g) L->key[g] = take(8 * cap);
     for (int g = 0; g < 2; ++g) L->q[g] = take(S * cap);
     for (int g = 0; g < 2; ++g) L->link[g] = take((size_t)4 * lrow_of(c->n) * cap);
@@ -216,6 +217,7 @@ void bind_context(gbees_ctx* ctx, const gbees_config* cfg, const Layout& L, void
     b.blk = (long long*)(base + L.blk);
     b.blk2 = b.blk + (GRID_MAX + 1);
     b.part = (Partial*)(base + L.part);
+    b.sorthist = (unsigned int*)(base + L.sorthist);
     for (int g = 0; g < 2; ++g) {
         b.key[g] = (unsigned long long*)(base + L.key[g]);
         b.q[g] = (void*)(base + L.q[g]);
@@ -388,19 +390,32 @@ void launch_list(gbees_ctx* ctx, void* const* f, int nf) {
     for (int i = 0; i < nf; ++i) cudaLaunchKernel(f[i], dim3(ctx->grid), dim3(THREADS), args, 0, ctx->stream);
 }
 
-// The prune of Algorithm 3 (directional marking, scan, compaction, relink,
-// rehash). It runs only when the device flag prune_now is set.
+// The prune of Algorithm 3 (directional marking, status, key-order sort,
+// compaction, relink, rehash). It runs only when the device flag prune_now is
+// set. The graph and direct paths put the survivors in key order (active cells
+// first), which keeps the neighbour rows of large grids close together.
+constexpr int kSortPasses = 8;                          // 8-bit digits of the 64-bit sort key
+constexpr int kPruneKernels = 3 + 1 + 3 * kSortPasses + 1 + 2;
+
 void launch_prune(gbees_ctx* ctx) {
     const int G = ctx->grid;
+    const int Gs = std::min(G, SORT_BLOCKS);
     cudaStream_t s = ctx->stream;
-    Phase ph(ctx, GBEES_PHASE_PRUNE, 5);
+    Phase ph(ctx, GBEES_PHASE_PRUNE, kPruneKernels);
     with_nt(ctx, [&](auto NN, auto TT) {
         constexpr int N = decltype(NN)::value;
         using T = decltype(TT);
         k_prune_mark<T><<<G, THREADS, 0, s>>>(ctx->m, ctx->b);
         k_prune_scatter<N, T><<<G, THREADS, 0, s>>>(ctx->m, ctx->b);
         k_prune_count<N><<<G, THREADS, 0, s>>>(ctx->m, ctx->b);
-        k_prune_compact<N, T><<<G, THREADS, 0, s>>>(ctx->m, ctx->b);
+        k_sort_init<<<G, THREADS, 0, s>>>(ctx->m, ctx->b);
+        for (int pass = 0; pass < kSortPasses; ++pass) {
+            k_sort_hist<<<Gs, THREADS, 0, s>>>(ctx->m, ctx->b, pass & 1, 8 * pass);
+            k_sort_scan<<<1, THREADS, 0, s>>>(ctx->m, ctx->b, Gs);
+            k_sort_scatter<<<Gs, THREADS, 0, s>>>(ctx->m, ctx->b, pass & 1, 8 * pass);
+        }
+        k_sort_map<<<G, THREADS, 0, s>>>(ctx->m, ctx->b);
+        k_prune_compact_sorted<N, T><<<G, THREADS, 0, s>>>(ctx->m, ctx->b);
         k_prune_relink<N><<<G, THREADS, 0, s>>>(ctx->m, ctx->b, G);
     });
 }
@@ -496,17 +511,32 @@ void graph_nodes(gbees_ctx* ctx, GraphBuilder& gb, cudaGraph_t body, cudaGraphCo
     DevScalars* sc = ctx->b.sc;
     long long maxit = kGraphMaxIter;
     int step_kernels = ctx->kern.npre + 1 + ctx->kern.npost + 1;
-    void* ctl_args[] = {&sc, &hw, &hp, &maxit, &step_kernels};
+    int prune_kernels = kPruneKernels;
+    void* ctl_args[] = {&sc, &hw, &hp, &maxit, &step_kernels, &prune_kernels};
     n = gb.add(body, n, (void*)k_loop_ctl, 1, 1, ctl_args);
     cudaGraph_t pb = nullptr;
     gb.cond(body, n, hp, cudaGraphCondTypeIf, &pb);
     if (gb.err != cudaSuccess) return;
     int nblk = G;
     void* relink_args[] = {m, b, &nblk};
+    const int Gs = std::min(G, SORT_BLOCKS);
+    static int srcs[2] = {0, 1};
+    static int shifts[kSortPasses] = {0, 8, 16, 24, 32, 40, 48, 56};
+    static int nsort = 0;
+    nsort = Gs;
     cudaGraphNode_t q = gb.add(pb, nullptr, (void*)k_prune_mark<T>, G, THREADS, mb);
     q = gb.add(pb, q, (void*)k_prune_scatter<N, T>, G, THREADS, mb);
     q = gb.add(pb, q, (void*)k_prune_count<N>, G, THREADS, mb);
-    q = gb.add(pb, q, (void*)k_prune_compact<N, T>, G, THREADS, mb);
+    q = gb.add(pb, q, (void*)k_sort_init, G, THREADS, mb);
+    for (int pass = 0; pass < kSortPasses; ++pass) {
+        void* pass_args[] = {m, b, &srcs[pass & 1], &shifts[pass]};
+        void* scan_args[] = {m, b, &nsort};
+        q = gb.add(pb, q, (void*)k_sort_hist, Gs, THREADS, pass_args);
+        q = gb.add(pb, q, (void*)k_sort_scan, 1, THREADS, scan_args);
+        q = gb.add(pb, q, (void*)k_sort_scatter, Gs, THREADS, pass_args);
+    }
+    q = gb.add(pb, q, (void*)k_sort_map, G, THREADS, mb);
+    q = gb.add(pb, q, (void*)k_prune_compact_sorted<N, T>, G, THREADS, mb);
     gb.add(pb, q, (void*)k_prune_relink<N>, G, THREADS, relink_args);
 }
 

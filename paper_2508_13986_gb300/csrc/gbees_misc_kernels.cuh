@@ -49,13 +49,14 @@ __global__ void k_loop_reset(DevScalars* sc) {
     sc->graph_kernels += 1;
 }
 
-// step_kernels: kernels of one step up to and including this one; a prune adds 5.
+// step_kernels: kernels of one step up to and including this one; a prune adds
+// prune_kernels.
 __global__ void k_loop_ctl(DevScalars* sc, cudaGraphConditionalHandle h_while, cudaGraphConditionalHandle h_prune,
-                           long long max_iter, int step_kernels) {
+                           long long max_iter, int step_kernels, int prune_kernels) {
     const long long it = ++sc->loop_iter;
     const int err = sc->error;
     const bool prune = sc->prune_now && !err;
-    sc->graph_kernels += step_kernels + (prune ? 5 : 0);
+    sc->graph_kernels += step_kernels + (prune ? prune_kernels : 0);
     cudaGraphSetConditional(h_prune, prune ? 1u : 0u);
     cudaGraphSetConditional(h_while, (!sc->done && !err && it < max_iter) ? 1u : 0u);
 }
@@ -149,6 +150,152 @@ __global__ void k_set_count(DevScalars* sc, long long count, long long step0) {
     sc->N_prev = 0;
     sc->n_act = 0;
     sc->step = step0;
+}
+
+// ------------------------------------------------------------------ key order at a prune
+// The graph and direct paths give the survivors of a prune their key order
+// (active cells first, then the halo; each in key order) with a stable LSD
+// radix sort of (region bit | key, old index), 8 bits per pass, so that the
+// neighbour rows a sweep reads are mostly near each other (L2 hits). Scratch:
+// the other generation's key/slot arrays (A), its link/value arrays (B), the
+// velocity scratch (histograms), all free until the compaction writes them.
+
+constexpr int SORT_BLOCKS = 1024;  // blocks of the sort kernels at most (histogram rows)
+
+struct SortBufs {
+    unsigned long long* key[2];
+    unsigned int* val[2];
+};
+
+__device__ __forceinline__ SortBufs sort_bufs(const Bufs& b, const StepView& v) {
+    SortBufs s;
+    s.key[0] = b.key[v.g ^ 1];
+    s.key[1] = reinterpret_cast<unsigned long long*>(b.link[v.g ^ 1]);
+    s.val[0] = b.slot[v.g ^ 1];
+    s.val[1] = static_cast<unsigned int*>(b.q[v.pb ^ 1]);
+    return s;
+}
+
+// keep[c] = status (0 drop, 1 active, 2 halo, from the status pass in map);
+// A = (sort key, c): dropped entries last, halo cells after the active ones.
+__global__ void __launch_bounds__(THREADS) k_sort_init(const Model m, Bufs b) {
+    if (!prune_due(b.sc)) return;
+    const StepView v = view_of(m, b.sc);
+    const SortBufs sb = sort_bufs(b, v);
+    const unsigned long long* key = b.key[v.g];
+    long long c0, c1;
+    block_chunk(v.N, c0, c1);
+    for (long long c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+        const int st = b.map[c];
+        b.keep[c] = (unsigned char)st;
+        sb.key[0][c] = st == 0 ? ~0ull : ((st == 2 ? (1ull << 63) : 0ull) | key[c]);
+        sb.val[0][c] = (unsigned int)c;
+    }
+}
+
+// Pass histogram: sorthist[d * nblk + block] = entries of this block's chunk
+// whose digit (key >> shift) & 255 is d.
+__global__ void __launch_bounds__(THREADS) k_sort_hist(const Model m, Bufs b, int src, int shift) {
+    if (!prune_due(b.sc)) return;
+    __shared__ unsigned int cnt[256];
+    const StepView v = view_of(m, b.sc);
+    const SortBufs sb = sort_bufs(b, v);
+    for (int d = threadIdx.x; d < 256; d += blockDim.x) cnt[d] = 0;
+    __syncthreads();
+    long long c0, c1;
+    block_chunk(v.N, c0, c1);
+    for (long long c = c0 + threadIdx.x; c < c1; c += blockDim.x)
+        atomicAdd(&cnt[(unsigned)(sb.key[src][c] >> shift) & 255u], 1u);
+    __syncthreads();
+    for (int d = threadIdx.x; d < 256; d += blockDim.x) b.sorthist[(long long)d * gridDim.x + blockIdx.x] = cnt[d];
+}
+
+// Exclusive scan of the 256 x nblk histogram in place (one block).
+__global__ void __launch_bounds__(THREADS) k_sort_scan(const Model m, Bufs b, int nblk) {
+    if (!prune_due(b.sc)) return;
+    __shared__ unsigned long long part[THREADS];
+    unsigned int* hist = b.sorthist;
+    const long long total = 256ll * nblk;
+    const long long per = (total + blockDim.x - 1) / blockDim.x;
+    const long long i0 = min(total, threadIdx.x * per), i1 = min(total, i0 + per);
+    unsigned long long sum = 0;
+    for (long long i = i0; i < i1; ++i) sum += hist[i];
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long run = 0;
+        for (int t = 0; t < (int)blockDim.x; ++t) {
+            const unsigned long long x = part[t];
+            part[t] = run;
+            run += x;
+        }
+    }
+    __syncthreads();
+    unsigned long long run = part[threadIdx.x];
+    for (long long i = i0; i < i1; ++i) {
+        const unsigned int x = hist[i];
+        hist[i] = (unsigned int)run;
+        run += x;
+    }
+}
+
+// Stable scatter of a pass: every block walks its chunk in tiles of one
+// element per thread; an element's place is its digit's offset for the block,
+// plus the elements of that digit in earlier tiles, earlier warps of the tile
+// and earlier lanes of its warp.
+__global__ void __launch_bounds__(THREADS) k_sort_scatter(const Model m, Bufs b, int src, int shift) {
+    if (!prune_due(b.sc)) return;
+    __shared__ unsigned int base[256];
+    __shared__ unsigned int wcnt[WARPS][256];
+    const StepView v = view_of(m, b.sc);
+    const SortBufs sb = sort_bufs(b, v);
+    for (int d = threadIdx.x; d < 256; d += blockDim.x) base[d] = b.sorthist[(long long)d * gridDim.x + blockIdx.x];
+    long long c0, c1;
+    block_chunk(v.N, c0, c1);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (long long t0 = c0; t0 < c1; t0 += blockDim.x) {
+        for (int i = threadIdx.x; i < WARPS * 256; i += blockDim.x) (&wcnt[0][0])[i] = 0;
+        __syncthreads();
+        const long long c = t0 + threadIdx.x;
+        const bool ok = c < c1;
+        unsigned long long k = 0;
+        unsigned int val = 0;
+        int d = 256 + lane;  // distinct dummies for lanes past the end
+        if (ok) {
+            k = sb.key[src][c];
+            val = sb.val[src][c];
+            d = (int)((k >> shift) & 255u);
+        }
+        const unsigned same = __match_any_sync(0xffffffffu, d);
+        const int rank = __popc(same & ((1u << lane) - 1u));
+        if (ok && rank == 0) wcnt[wid][d] = __popc(same);
+        __syncthreads();
+        if (ok) {
+            unsigned int off = base[d] + rank;
+            for (int w = 0; w < wid; ++w) off += wcnt[w][d];
+            sb.key[src ^ 1][off] = k;
+            sb.val[src ^ 1][off] = val;
+        }
+        __syncthreads();
+        for (int dd = threadIdx.x; dd < 256; dd += blockDim.x) {
+            unsigned int tot = 0;
+            for (int w = 0; w < WARPS; ++w) tot += wcnt[w][dd];
+            base[dd] += tot;
+        }
+        __syncthreads();
+    }
+}
+
+// New index of every survivor: its rank in the sorted order (survivors sort
+// before the dropped entries); -1 for the dropped.
+__global__ void __launch_bounds__(THREADS) k_sort_map(const Model m, Bufs b) {
+    if (!prune_due(b.sc)) return;
+    const StepView v = view_of(m, b.sc);
+    const SortBufs sb = sort_bufs(b, v);
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < v.N; r += (long long)gridDim.x * blockDim.x) {
+        const unsigned int c = sb.val[0][r];
+        b.map[c] = b.keep[c] ? (int)r : -1;
+    }
 }
 
 // Per-block counts of the active cells (read-out, first pass).

@@ -843,6 +843,45 @@ __device__ __forceinline__ void prune_compact_body(const Model& m, const Bufs& b
     }
 }
 
+// The compaction of the graph and direct paths: every survivor goes to the
+// place map[c] that the key-order sort gave it (status in keep); the same
+// values, rescaling and partials as prune_compact_body.
+template <int N, typename T>
+__device__ __forceinline__ void prune_compact_sorted_body(const Model& m, const Bufs& b, const StepView& v,
+                                                          long long (&d)[NDIG], double& mx, double& rmax,
+                                                          int& err) {
+    const T* Q = static_cast<const T*>(b.q[v.pb]);
+    T* Qo = static_cast<T*>(b.q[v.pb ^ 1]);
+    const unsigned long long* key = b.key[v.g];
+    unsigned long long* keyo = b.key[v.g ^ 1];
+    const unsigned short* om = b.om[v.g];
+    unsigned short* omo = b.om[v.g ^ 1];
+    const double mq = v.maxq;
+    const double s2 = (mq > 0.0 && isfinite(mq)) ? ldexp(1.0, -ilogb(mq)) : 1.0;
+    for (WarpRuns r(v.N, v.nb, v.bi); r.next();) {
+        const long long c = r.c;
+        if (c >= v.N) continue;
+        const int st = b.keep[c];
+        if (st == 0) continue;
+        const long long nc = b.map[c];
+        const unsigned long long k = key[c];
+        keyo[nc] = k;
+        if (st == 1) {
+            const T val = (T)((double)Q[c] * s2);
+            Qo[nc] = val;
+            omo[nc] = (unsigned short)(om[c] & 0xfffu);
+            acc_add(d, (double)val, err);
+            mx = fmax(mx, (double)val);
+            int I[N];
+            unpack_key<N>(m, k, I);
+            rmax = fmax(rmax, cfl_rate64<N>(m, I));
+        } else {
+            Qo[nc] = (T)0;
+            omo[nc] = (unsigned short)((om[c] & 0xfffu) | OM_GHOST);
+        }
+    }
+}
+
 // New links through the map, and the rehash of the survivors.
 template <int N>
 __device__ __forceinline__ void prune_relink_body(const Model& m, const Bufs& b, const StepView& v) {
