@@ -131,8 +131,8 @@ class ClockSampler:
             for name, v in zip(names, parts[5:9]):
                 if v.lower().startswith("active"):
                     reasons.add(name)
-        out_dir = os.path.join(ROOT, "gpurun_out")
-        if os.path.isdir(out_dir):
+        out_dir = os.environ.get("BENCH_CLOCKS_DIR")  # keep the raw samples there when set
+        if out_dir and os.path.isdir(out_dir):
             with open(os.path.join(out_dir, "clocks.csv"), "a") as f:
                 f.write("\n".join(self.lines) + "\n")
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,

@@ -24,7 +24,7 @@
  *   normalisation                      Sec. 4.3 / 4.5
  *   Bayesian measurement update        Eq. 4
  *
- * Readings of points the paper leaves open (each one is listed in the design doc):
+ * Readings of points the paper leaves open (the CUDA library follows the same):
  *   - Lorenz '63 is available both in the classic form (sigma, rho, beta) and in
  *     the shifted form the paper prints in Sec. 5.1.1 (sigma, b, r).
  *   - Eq. 8 is read with |f| and multiplied by the CFL number:
