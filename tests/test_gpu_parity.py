@@ -80,6 +80,21 @@ def test_lorenz96_6d_h05_short_fp64():
     assert_fp64_parity(g, o, w, gst, ost)
 
 
+def test_lorenz96_6d_h05_short_fp32_store():
+    """FP32 storage and fluxes on the 6-D grid: L1 and moments within the FP32 bar."""
+    w = W.lorenz96(h=0.5, t_end=0.06, prune_interval=2)
+    g, o = make_pair(w, precision=gbees.GBEES_FP32, max_cells=1 << 20)
+    g.init_gaussian(w.mean, w.cov)
+    o.init_gaussian(w.mean, w.cov)
+    run_schedule(g, o, w)
+    _, l1, _, _, _, _ = compare(g, o, w.h)
+    assert l1 <= FP32_L1, l1
+    gm, gc = g.moments()
+    om, oc = o.moments()
+    assert np.abs(gm - om).max() <= FP32_MOM * np.abs(om).max()
+    assert np.abs(gc - oc).max() <= FP32_MOM * np.abs(oc).max()
+
+
 @pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("lim", [LIM_MC, LIM_NONE, LIM_LW])
 def test_random_sets_linear_dynamics_fp64(n, lim):
