@@ -8,10 +8,9 @@
 //   grow       directional grow of the significant cells (Sec. 3.3, Algorithm 2)
 //   halo       the missing face neighbours of the newly active cells, as halo cells
 //   link       neighbour links, outward mask and CFL rate of the new entries (Sec. 4.1)
-//   waves      FP64: per-entry velocities u_d and entering waves G_d
-//   faces      FP64: one flux per face (Eq. 7 + Algorithm 1 gathered + HR term)
-//   apply      FP64: P -= sum_j dt/h_j (F_hi - F_lo), normalised, reduced
-//   gather     single-pass update (any precision), normalised, reduced
+//   waves      per-entry velocities u_d and entering waves G_d
+//   faces      one flux per face (Eq. 7 + Algorithm 1 gathered + HR term)
+//   apply      P -= sum_j dt/h_j (F_hi - F_lo), normalised, reduced
 //   prune      mark S, mark D(S), status, compact, relink and rehash (Algorithm 3)
 //
 // The pool holds the active cells and, as halo cells with p = 0, every face
