@@ -556,3 +556,63 @@ def test_probability_is_normalised_after_each_propagation():
         _, p = o.read_cells()
         assert math.fsum(p.tolist()) * 0.125 == pytest.approx(1.0, abs=1e-14)
         assert o.t == t
+
+
+# ---------------------------------------------------------------- symmetries of the whole step
+
+def _run_const(idx, p, c, h, limiter, t_end, K=3):
+    o = const_oracle(c, h, limiter=limiter, thr=1e-3, cfl=0.8, K=K)
+    o.init_cells(idx, p)
+    st = o.propagate(t_end)
+    return o, st
+
+
+@pytest.mark.parametrize("lim", [LIM_MC, LIM_LW])
+def test_translation_of_the_cell_set_translates_the_result_exactly(lim):
+    """Under a constant drift nothing depends on where the grid sits: shifting
+    every index by an integer vector shifts the result (grow, dt, CTU, prune,
+    normalisation), bit for bit."""
+    idx, p = W.random_cells(3, 300, 4, seed=31)
+    c, h = [0.7, -0.4, 0.25], [0.5, 0.4, 0.3]
+    shift = np.array([7, -11, 3], dtype=np.int32)
+    a, sa = _run_const(idx, p, c, h, lim, 0.4)
+    b, sb = _run_const(idx + shift, p, c, h, lim, 0.4)
+    assert sa.steps == sb.steps and sa.t == sb.t
+    ca, cb = cells_of(a), cells_of(b)
+    assert {tuple(int(x) for x in np.array(k) + shift): v for k, v in ca.items()} == cb
+
+
+@pytest.mark.parametrize("lim", [LIM_MC, LIM_NONE])
+def test_permuting_the_dimensions_permutes_the_result(lim):
+    """Relabelling the axes (cells, velocity and widths together) relabels the
+    result: a transposed operand or a wrong h index in the step breaks this."""
+    idx, p = W.random_cells(3, 250, 4, seed=32)
+    c, h = np.array([0.6, -0.3, 0.45]), np.array([0.5, 0.35, 0.45])
+    perm = [2, 0, 1]
+    a, sa = _run_const(idx, p, list(c), list(h), lim, 0.35)
+    b, sb = _run_const(np.ascontiguousarray(idx[:, perm]), p, list(c[perm]), list(h[perm]), lim, 0.35)
+    assert sa.steps == sb.steps and sa.t == pytest.approx(sb.t, abs=1e-15)
+    ca, cb = cells_of(a), cells_of(b)
+    assert set(tuple(k[i] for i in perm) for k in ca) == set(cb)
+    scale = max(abs(v) for v in ca.values())
+    for k, v in ca.items():
+        assert cb[tuple(k[i] for i in perm)] == pytest.approx(v, abs=1e-13 * scale)
+
+
+@pytest.mark.parametrize("lim", [LIM_MC, LIM_LW])
+def test_mirroring_an_axis_and_the_drift_mirrors_the_result(lim):
+    """Reflecting axis 0 (i -> -i) with the drift component negated reflects the
+    result: upwinding, the sign tests of Algorithm 1 and the limiter's upwind
+    wave must treat both directions alike."""
+    idx, p = W.random_cells(2, 120, 5, seed=33)
+    c, h = [0.55, -0.35], [0.5, 0.4]
+    a, sa = _run_const(idx, p, c, h, lim, 0.3)
+    mirrored = idx.copy()
+    mirrored[:, 0] = -mirrored[:, 0]
+    b, sb = _run_const(mirrored, p, [-c[0], c[1]], h, lim, 0.3)
+    assert sa.steps == sb.steps
+    ca, cb = cells_of(a), cells_of(b)
+    assert set((-k[0], k[1]) for k in ca) == set(cb)
+    scale = max(abs(v) for v in ca.values())
+    for k, v in ca.items():
+        assert cb[(-k[0], k[1])] == pytest.approx(v, abs=1e-13 * scale)
