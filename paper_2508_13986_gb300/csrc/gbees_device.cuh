@@ -56,7 +56,6 @@ struct alignas(256) DevScalars {
     double t_target;      // end of the current propagate call
     double dt;            // last step
     unsigned long long maxrate_bits;      // max CFL rate over the cells (non-negative double bits)
-    unsigned long long maxrate_new_bits;  // max rate over the survivors of a prune
     unsigned long long maxq_ord;          // order key of the running max of Q
     double maxq;          // max of Q after the last finalisation
     double w;             // (prod h) * sum Q at the last finalisation
@@ -78,10 +77,10 @@ struct alignas(256) DevScalars {
     unsigned int bar_count;   // grid barrier of the persistent kernel: arrivals
     unsigned int bar_gen;     // and generation
     // SM cycles spent by block 0 of the persistent kernel per phase (grow,
-    // link, faces, update, prune, combine/scalars) and the steps they cover
+    // halo, link, faces, apply, prune, step scalars) and the steps they cover
     long long phase_cycles[8];
     long long phase_steps;
-    // the current step (written by the last block of the grow kernel)
+    // the current step (written by the last block of the link kernel)
     double step_dt;       // dt of the step being taken
     double step_t_new;    // time after it
     int step_last;        // the step lands on t_target
@@ -651,18 +650,9 @@ __device__ __forceinline__ bool last_block(DevScalars* sc) {
     return s_last;
 }
 
-// Normalisation scalars from the exact sum and the running maximum; also the
-// end of a prune (swap buffers, new count, new CFL maximum).
-// mode bit 1: a prune just completed; mode bit 2: keep w = 1 (cells loaded as given).
+// Normalisation scalars of a new grid from the exact sum and the running
+// maximum. mode bit 2: keep w = 1 (cells loaded as given).
 __device__ __forceinline__ void finalise_norm(const Model& m, DevScalars* sc, int mode) {
-    if (mode & 1) {
-        sc->N = sc->N_new;
-        sc->gen ^= 1;
-        sc->pbuf ^= 1;
-        sc->maxrate_bits = sc->maxrate_new_bits;
-        sc->maxrate_new_bits = 0;
-        sc->prune_now = 0;
-    }
     sc->N_prev = sc->N;
     sc->maxq = sc->maxq_ord ? ord_val(sc->maxq_ord) : 0.0;
     if (mode & 2) {
@@ -685,20 +675,6 @@ __device__ __forceinline__ void finalise_norm(const Model& m, DevScalars* sc, in
     sc->maxq_ord = 0;
     sc->ticket = 0;
     if (sc->N == 0 && !(mode & 2)) set_error(sc, ST_EDEGENERATE);
-}
-
-// Bookkeeping after the flux update of a step (last block, one thread): time,
-// step count, buffer swap, prune schedule and the normalisation scalars.
-__device__ __forceinline__ void finish_step(const Model& m, DevScalars* sc, long long ncell, int pb) {
-    sc->dt = sc->step_dt;
-    sc->t = sc->step_t_new;
-    sc->step += 1;
-    sc->steps_call += 1;
-    sc->updates_call += ncell;
-    sc->done = sc->step_last;
-    sc->pbuf = pb ^ 1;
-    sc->prune_now = (m.prune_interval > 0 && (sc->step % m.prune_interval) == 0);
-    finalise_norm(m, sc, 0);
 }
 
 // Write this block's partial (exact digits, maximum value, maximum rate).
@@ -854,8 +830,5 @@ __device__ __forceinline__ int block_exclusive_scan(int flag, int& total) {
     total = tot;
     return before + in_warp;
 }
-
-template <typename T>
-__device__ __forceinline__ T ldq(const T* p) { return __ldg(p); }
 
 }  // namespace gbees

@@ -365,24 +365,6 @@ __global__ void __launch_bounds__(THREADS) k_prune_count(const Model m, Bufs b) 
 }
 
 template <int N, typename T>
-__global__ void __launch_bounds__(THREADS) k_prune_compact(const Model m, Bufs b) {
-    DevScalars* sc = b.sc;
-    if (!prune_due(sc)) return;
-    const StepView v = view_of(m, sc);
-    const Survivors sv = block_offsets(b, v.nb, v.bi);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        sc->N_new = sv.total_a + sv.total_g;
-        sc->NA_new = sv.total_a;
-    }
-    long long d[NDIG] = {0, 0, 0, 0, 0, 0};
-    double mx = -INFINITY, rmax = 0.0;
-    int err = 0;
-    prune_compact_body<N, T>(m, b, v, sv, d, mx, rmax, err);
-    if (err) set_error(sc, ST_EDEGENERATE);
-    block_partial(b.part, d, mx, rmax);
-}
-
-template <int N, typename T>
 __global__ void __launch_bounds__(THREADS) k_prune_compact_sorted(const Model m, Bufs b) {
     DevScalars* sc = b.sc;
     if (!prune_due(sc)) return;

@@ -110,7 +110,6 @@ __global__ void k_reset(DevScalars* sc, double t0) {
     sc->t_target = t0;
     sc->dt = 0.0;
     sc->maxrate_bits = 0;
-    sc->maxrate_new_bits = 0;
     sc->maxq_ord = 0;
     sc->maxq = 0.0;
     sc->w = 1.0;
