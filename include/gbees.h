@@ -167,8 +167,8 @@ int gbees_propagate(gbees_ctx* ctx, double t_end, gbees_stats* stats);
  * on ctxs[0]'s stream with the same phases and arithmetic as gbees_propagate,
  * so every grid ends bit-identical to its own gbees_propagate. When all grids
  * fit on the GPU at once, each grid gets a team of thread blocks in proportion
- * to its work (active cells x remaining time / h; cooperative launch, a
- * barrier per team); otherwise each block takes the next grid from a queue
+ * to its work (active cells x remaining time / h, or active cells alone when
+ * max_steps > 0; cooperative launch, a barrier per team); otherwise each block takes the next grid from a queue
  * and runs its whole step loop alone. max_steps = 0 runs every grid to its
  * t_end; max_steps > 0 makes one launch in which every grid takes at most
  * max_steps steps (a round of a serving loop: stats[i].t < t_end[i] tells
@@ -217,7 +217,8 @@ enum {
     GBEES_PHASE_LINK = 2,    /* neighbour links of the new entries, CFL step (Sec. 4.1, Eq. 8) */
     GBEES_PHASE_FACES = 3,   /* face fluxes: DCU + CTU + high-resolution term (Eq. 7, Algorithm 1) */
     GBEES_PHASE_APPLY = 4,   /* conservative update, normalisation partials */
-    GBEES_PHASE_PRUNE = 5,   /* mark, scan, compaction, relink and rehash (Algorithm 3) */
+    GBEES_PHASE_PRUNE = 5,   /* mark, status, key-order sort (graph and direct launch modes),
+                                compaction, relink and rehash (Algorithm 3) */
     GBEES_PHASE_CORRECT = 6, /* Bayesian update (Eq. 4) */
     GBEES_PHASE_OTHER = 7,   /* init, read-out, moments */
     GBEES_NPHASES = 8
