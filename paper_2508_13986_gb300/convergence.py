@@ -1,0 +1,140 @@
+"""Convergence tooling (Sec. 5.2.2): the 1-norm E(t) and the Bhattacharyya
+coefficient BC(t) of a propagated density against a reference propagation,
+and the temporal (CFL number epsilon) and spatial (cell width factor eta)
+studies built on them.
+
+Densities are the read-out of a grid: cell indices (N x n int32) and
+densities p with (prod h) sum p = 1 on a grid of widths h and origin x0
+(cell i has centre x0 + i h). A cell missing from one density counts as 0.
+
+  E  = (prod h) sum_i |p_i - p0_i|         (over the union of the two sets)
+  BC = (prod h) sum_i sqrt(p_i p0_i)       (over the intersection; 1 for equal
+                                            densities, 0 for disjoint ones)
+
+The paper prints BC without the cell volume; with densities normalised as
+above the factor prod h keeps BC in [0, 1]. Densities on different grids are
+compared on the coarser one: every fine cell's mass goes to the coarse cell
+that contains its centre (`restrict`).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+from typing import Callable, Dict, List, Optional, Sequence, Tuple
+
+import numpy as np
+
+from .workloads import Workload
+
+
+def _pack(idx: np.ndarray) -> np.ndarray:
+    """Rows of int32 cell indices as one structured key per row (for set
+    operations); any n."""
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    return idx.view(np.dtype((np.void, idx.dtype.itemsize * idx.shape[1]))).ravel()
+
+
+def _align(idx_a, p_a, idx_b, p_b) -> Tuple[np.ndarray, np.ndarray]:
+    """Values of both densities on the union of their cells (0 where absent)."""
+    ka, kb = _pack(idx_a), _pack(idx_b)
+    keys, inv = np.unique(np.concatenate([ka, kb]), return_inverse=True)
+    va = np.zeros(keys.shape[0])
+    vb = np.zeros(keys.shape[0])
+    va[inv[:ka.shape[0]]] = p_a
+    vb[inv[ka.shape[0]:]] = p_b
+    return va, vb
+
+
+def l1_error(idx_a, p_a, idx_b, p_b, h: Sequence[float]) -> float:
+    """E = (prod h) sum |p_a - p_b| over the union of the two active sets."""
+    va, vb = _align(idx_a, p_a, idx_b, p_b)
+    return math.prod(h) * math.fsum(np.abs(va - vb).tolist())
+
+
+def bhattacharyya(idx_a, p_a, idx_b, p_b, h: Sequence[float]) -> float:
+    """BC = (prod h) sum sqrt(p_a p_b) (negative densities count as 0)."""
+    va, vb = _align(idx_a, p_a, idx_b, p_b)
+    return math.prod(h) * math.fsum(np.sqrt(np.maximum(va, 0.0) * np.maximum(vb, 0.0)).tolist())
+
+
+def restrict(idx_f, p_f, h_f: Sequence[float], x0_f: Sequence[float], h_c: Sequence[float],
+             x0_c: Sequence[float]) -> Tuple[np.ndarray, np.ndarray]:
+    """A density on a fine grid moved to a coarser grid: the mass
+    (prod h_f) p_f of every fine cell goes to the coarse cell containing the
+    fine cell's centre; returns the coarse cells and their densities."""
+    h_f, x0_f = np.asarray(h_f, dtype=np.float64), np.asarray(x0_f, dtype=np.float64)
+    h_c, x0_c = np.asarray(h_c, dtype=np.float64), np.asarray(x0_c, dtype=np.float64)
+    centres = x0_f + np.asarray(idx_f, dtype=np.float64) * h_f
+    coarse = np.floor((centres - x0_c) / h_c + 0.5).astype(np.int32)
+    keys, inv = np.unique(_pack(coarse), return_inverse=True)
+    mass = np.zeros(keys.shape[0])
+    np.add.at(mass, inv, np.asarray(p_f, dtype=np.float64) * float(np.prod(h_f)))
+    first = np.zeros(keys.shape[0], dtype=np.int64)
+    first[inv[::-1]] = np.arange(inv.shape[0])[::-1]
+    return coarse[first], mass / float(np.prod(h_c))
+
+
+# ------------------------------------------------------------------ studies
+
+Runner = Callable[[Workload], Tuple[np.ndarray, np.ndarray]]
+
+
+def gpu_runner(precision: Optional[int] = None, device: str = "cuda:0") -> Runner:
+    """Propagation through the CUDA library (measurements included) to the
+    workload's t_end; returns the read-out (sorted cells, densities)."""
+    from . import gbees
+    from .workloads import capacity_for
+
+    prec = gbees.GBEES_FP64 if precision is None else precision
+
+    def run(w: Workload):
+        g = gbees.grid_for_workload(w, precision=prec, max_cells=capacity_for(w), device=device)
+        try:
+            g.init_gaussian(w.mean, w.cov)
+            for t, meas in w.segments():
+                g.propagate(t)
+                if meas is not None:
+                    g.correct_gaussian(meas.y, meas.R, meas.H_idx)
+            return g.read_cells()
+        finally:
+            g.close()
+
+    return run
+
+
+@dataclass
+class Point:
+    value: float       # epsilon (CFL number) or eta (cell width factor)
+    E: float
+    BC: float
+
+
+def temporal_study(w: Workload, eps: Sequence[float], eps_ref: float, run: Optional[Runner] = None) -> List[Point]:
+    """E and BC at t_end of propagations with CFL number epsilon against a
+    reference with a small epsilon (same grid)."""
+    run = run or gpu_runner()
+    ri, rp = run(w.with_(cfl=eps_ref))
+    out = []
+    for e in eps:
+        i, p = run(w.with_(cfl=e))
+        out.append(Point(e, l1_error(i, p, ri, rp, w.h), bhattacharyya(i, p, ri, rp, w.h)))
+    return out
+
+
+def spatial_study(w: Workload, etas: Sequence[float], eta_ref: float, run: Optional[Runner] = None) -> List[Point]:
+    """E and BC at t_end of propagations with cell widths eta h against a
+    reference with widths eta_ref h, both on the grid of the coarser one."""
+    run = run or gpu_runner()
+    h_ref = tuple(eta_ref * x for x in w.h)
+    ri, rp = run(w.with_(h=h_ref))
+    out = []
+    for eta in etas:
+        h = tuple(eta * x for x in w.h)
+        i, p = run(w.with_(h=h))
+        if eta >= eta_ref:   # compare on the grid of the approximation
+            ci, cp = restrict(ri, rp, h_ref, w.x0, h, w.x0)
+            out.append(Point(eta, l1_error(i, p, ci, cp, h), bhattacharyya(i, p, ci, cp, h)))
+        else:
+            ci, cp = restrict(i, p, h, w.x0, h_ref, w.x0)
+            out.append(Point(eta, l1_error(ci, cp, ri, rp, h_ref), bhattacharyya(ci, cp, ri, rp, h_ref)))
+    return out

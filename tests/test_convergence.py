@@ -1,0 +1,86 @@
+"""Convergence tooling (CPU): the metrics' defining properties, the transfer
+between grids, and the paper's temporal and spatial studies run through the
+oracle on a small case (the errors fall as epsilon and eta fall)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle.oracle import DYN_LINEAR, Oracle
+from paper_2508_13986_gb300 import workloads as W
+from paper_2508_13986_gb300.convergence import bhattacharyya, l1_error, restrict, spatial_study, temporal_study
+
+
+def normalised(idx, p, h):
+    return idx, p / (math.prod(h) * p.sum())
+
+
+def test_metrics_of_equal_and_of_disjoint_densities():
+    h = (0.5, 0.25)
+    idx, p = W.random_cells(2, 40, 5, seed=51)
+    idx, p = normalised(idx, p, h)
+    assert l1_error(idx, p, idx, p, h) == 0.0
+    assert bhattacharyya(idx, p, idx, p, h) == pytest.approx(1.0, abs=1e-14)
+    far = idx + np.array([100, 0], dtype=np.int32)
+    assert l1_error(idx, p, far, p, h) == pytest.approx(2.0, abs=1e-14)
+    assert bhattacharyya(idx, p, far, p, h) == 0.0
+
+
+def test_metrics_are_symmetric_bounded_and_e_is_a_metric():
+    h = (0.5, 0.5, 0.5)
+    a = normalised(*W.random_cells(3, 60, 3, seed=52), h)
+    b = normalised(*W.random_cells(3, 60, 3, seed=53), h)
+    c = normalised(*W.random_cells(3, 60, 3, seed=54), h)
+    assert l1_error(*a, *b, h) == pytest.approx(l1_error(*b, *a, h), abs=1e-15)
+    assert bhattacharyya(*a, *b, h) == pytest.approx(bhattacharyya(*b, *a, h), abs=1e-15)
+    assert 0.0 <= bhattacharyya(*a, *b, h) <= 1.0                    # Cauchy-Schwarz
+    assert l1_error(*a, *c, h) <= l1_error(*a, *b, h) + l1_error(*b, *c, h) + 1e-15
+    # Hellinger bound: E <= 2 sqrt(1 - BC^2)
+    bc = bhattacharyya(*a, *b, h)
+    assert l1_error(*a, *b, h) <= 2.0 * math.sqrt(max(0.0, 1.0 - bc * bc)) + 1e-12
+
+
+def test_restriction_keeps_the_mass_and_averages_aligned_cells():
+    h_f, h_c = (0.25, 0.25), (0.5, 0.5)
+    x0_f, x0_c = (0.125, 0.125), (0.25, 0.25)    # two fine cells per coarse cell and axis, centres inside
+    idx, p = W.random_cells(2, 200, 6, seed=55)
+    ci, cp = restrict(idx, p, h_f, x0_f, h_c, x0_c)
+    assert math.prod(h_c) * cp.sum() == pytest.approx(math.prod(h_f) * p.sum(), rel=1e-14)
+    fine = {tuple(r): v for r, v in zip(idx.tolist(), p.tolist())}
+    for (a, b), v in zip(ci.tolist(), cp.tolist()):
+        kids = [fine.get((2 * a + i, 2 * b + j), 0.0) for i in (0, 1) for j in (0, 1)]
+        assert v == pytest.approx(sum(kids) / 4.0, rel=1e-14)
+
+
+def rotation():
+    """A 2-D rotation with slight contraction: a Gaussian blob that turns."""
+    A = np.array([[-0.1, -2.0], [2.0, -0.1]])
+    return W.Workload(name="rot2d", n=2, dynamics=DYN_LINEAR, params=tuple(A.reshape(-1)) + (0.0, 0.0),
+                      h=(0.25, 0.25), mean=(1.5, 0.0), cov=0.09 * np.eye(2), thr_rel=1e-6, cfl=0.8, t_end=0.4,
+                      prune_interval=10)
+
+
+def oracle_run(w):
+    o = Oracle(w.n, w.dynamics, w.params, w.h, w.x0, w.thr_rel, w.cfl, w.prune_interval, w.limiter)
+    o.init_gaussian(w.mean, w.cov)
+    for t, m in w.segments():
+        o.propagate(t)
+        if m is not None:
+            o.correct_gaussian(m.y, m.R, m.H_idx)
+    return o.read_cells()
+
+
+def test_temporal_study_converges_as_epsilon_falls():
+    pts = temporal_study(rotation(), eps=(0.8, 0.4, 0.2), eps_ref=0.05, run=oracle_run)
+    E = [q.E for q in pts]
+    BC = [q.BC for q in pts]
+    assert E[0] > E[1] > E[2] > 0.0
+    assert BC[0] < BC[1] < BC[2] <= 1.0
+
+
+def test_spatial_study_converges_as_eta_falls():
+    w = rotation().with_(cfl=0.5)
+    pts = spatial_study(w, etas=(2.0, 1.5, 1.0), eta_ref=0.5, run=oracle_run)
+    E = [q.E for q in pts]
+    assert E[0] > E[1] > E[2] > 0.0
+    assert all(0.0 < q.BC <= 1.0 for q in pts) and pts[0].BC < pts[2].BC
