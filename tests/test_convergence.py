@@ -84,3 +84,16 @@ def test_spatial_study_converges_as_eta_falls():
     E = [q.E for q in pts]
     assert E[0] > E[1] > E[2] > 0.0
     assert all(0.0 < q.BC <= 1.0 for q in pts) and pts[0].BC < pts[2].BC
+
+
+@pytest.mark.gpu
+def test_temporal_study_through_the_library_matches_the_oracle():
+    import __graft_entry__ as ge
+    from paper_2508_13986_gb300.convergence import gpu_runner
+
+    ge.build()
+    w = rotation()
+    gpu = temporal_study(w, eps=(0.8, 0.4), eps_ref=0.1, run=gpu_runner())
+    orc = temporal_study(w, eps=(0.8, 0.4), eps_ref=0.1, run=oracle_run)
+    for a, b in zip(gpu, orc):
+        assert a.E == pytest.approx(b.E, abs=1e-10) and a.BC == pytest.approx(b.BC, abs=1e-10)
