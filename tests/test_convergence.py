@@ -86,6 +86,52 @@ def test_spatial_study_converges_as_eta_falls():
     assert all(0.0 < q.BC <= 1.0 for q in pts) and pts[0].BC < pts[2].BC
 
 
+class OracleGrid:
+    """Stands in for gbees.Grid: the same methods, backed by the oracle, built
+    from the library's configuration struct."""
+
+    def __init__(self, cfg, device="cuda:0"):
+        n = cfg.n
+        self.o = Oracle(n, cfg.dynamics, list(cfg.params), list(cfg.h)[:n], list(cfg.x0)[:n],
+                        cfg.thr_rel, cfg.cfl, cfg.prune_interval, cfg.limiter)
+        self.closed = False
+
+    def init_gaussian(self, mean, cov):
+        self.o.init_gaussian(mean, cov)
+
+    def propagate(self, t):
+        return self.o.propagate(t)
+
+    def correct_gaussian(self, y, R, H_idx):
+        self.o.correct_gaussian(y, R, H_idx)
+
+    def read_cells(self):
+        return self.o.read_cells()
+
+    def close(self):
+        self.closed = True
+
+
+def test_library_runner_plumbing_with_an_oracle_backed_grid(monkeypatch):
+    """The library runner (configuration, schedule, read-out, release) gives the
+    oracle's result when the grid behind it is the oracle."""
+    from paper_2508_13986_gb300 import gbees
+    from paper_2508_13986_gb300.convergence import gpu_runner
+
+    made = []
+
+    def grid(cfg, device="cuda:0"):
+        made.append(OracleGrid(cfg, device))
+        return made[-1]
+
+    monkeypatch.setattr(gbees, "Grid", grid)
+    w = rotation().with_(t_end=0.2)
+    gi, gp = gpu_runner()(w)
+    oi, op = oracle_run(w)
+    assert np.array_equal(gi, oi) and np.array_equal(gp, op)
+    assert len(made) == 1 and made[0].closed
+
+
 @pytest.mark.gpu
 def test_temporal_study_through_the_library_matches_the_oracle():
     import __graft_entry__ as ge
