@@ -7,6 +7,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "gbees_keys.cuh"
+
 namespace gbees {
 
 namespace cg = cooperative_groups;
@@ -237,39 +239,12 @@ struct WarpRuns {
 
 template <int N>
 __device__ __forceinline__ bool pack_key(const Model& m, const int* I, unsigned long long& k) {
-    const int b = m.key_bits;
-    const long long bias = 1ll << (b - 1);
-    const long long lim = 1ll << b;
-    k = 0;
-#pragma unroll
-    for (int j = 0; j < N; ++j) {
-        long long v = (long long)I[j] + bias;
-        if (v < 0 || v >= lim) return false;
-        k = (k << b) | (unsigned long long)v;
-    }
-    return true;
+    return pack_key_bits<N>(m.key_bits, I, k);
 }
 
 template <int N>
 __device__ __forceinline__ void unpack_key(const Model& m, unsigned long long k, int* I) {
-    const int b = m.key_bits;
-    const long long bias = 1ll << (b - 1);
-    const unsigned long long mask = (b >= 64) ? ~0ull : ((1ull << b) - 1);
-#pragma unroll
-    for (int j = N - 1; j >= 0; --j) {
-        I[j] = (int)((long long)(k & mask) - bias);
-        k >>= b;
-    }
-}
-
-// murmur3 64-bit finaliser
-__device__ __forceinline__ unsigned long long mix64(unsigned long long x) {
-    x ^= x >> 33;
-    x *= 0xff51afd7ed558ccdull;
-    x ^= x >> 33;
-    x *= 0xc4ceb9fe1a85ec53ull;
-    x ^= x >> 33;
-    return x;
+    unpack_key_bits<N>(m.key_bits, k, I);
 }
 
 // ------------------------------------------------------------------ hashtable
