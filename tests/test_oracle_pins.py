@@ -260,6 +260,56 @@ def test_ctu_constant_velocity_2d_is_bilinear_interpolation(sx, sy):
         assert got[tuple(X)] == pytest.approx(want[i, j], abs=1e-14)
 
 
+def mc_phi(theta):
+    return np.maximum(0.0, np.minimum(np.minimum((1.0 + theta) / 2.0, 2.0), 2.0 * theta))
+
+
+def hr_ctu_positive(P, nx, ny, phi):
+    """LeVeque's high-resolution wave-propagation step (Ch. 20) for constant
+    velocity with both components positive, written as bilinear CTU plus the
+    limited second-order flux differences of each axis (increment waves
+    propagated transversely, corrections not), on a zero-padded array (two
+    cells of padding on each side)."""
+    def sh(A, ox, oy):                      # A shifted so that out[i, j] = A[i - ox, j - oy]
+        return np.roll(np.roll(A, ox, 0), oy, 1)
+    new = ((1 - nx) * (1 - ny) * P + nx * (1 - ny) * sh(P, 1, 0) + (1 - nx) * ny * sh(P, 0, 1)
+           + nx * ny * sh(P, 1, 1))
+    for axis, nu in ((0, nx), (1, ny)):
+        W = P - np.roll(P, 1, axis)                  # wave at the lower face
+        Wup = np.roll(W, 1, axis)                    # the wave one face upwind
+        theta = np.divide(Wup, W, out=np.zeros_like(W), where=W != 0)
+        F = 0.5 * nu * (1 - nu) * phi(theta) * W     # dt/h times the correction flux
+        new -= np.roll(F, -1, axis) - F
+    return new
+
+
+@pytest.mark.parametrize("sx,sy", [(1, 1), (1, -1), (-1, 1), (-1, -1)])
+def test_ctu_mc_constant_velocity_2d_is_the_textbook_high_resolution_step(sx, sy):
+    """With the MC limiter a constant-velocity step is bilinear CTU plus the
+    MC-limited flux correction along each axis (LeVeque, Ch. 20), in all four
+    velocity quadrants; the data mix smooth and rough parts so that every
+    branch of the limiter is taken."""
+    h = [0.5, 0.25]
+    a, b = 3.0 * sx, 1.25 * sy
+    dt = 0.1
+    nx, ny = abs(a) * dt / h[0], abs(b) * dt / h[1]
+    rng = np.random.default_rng(61)
+    shape = (12, 14)
+    X, Y = np.meshgrid(np.arange(shape[0]), np.arange(shape[1]), indexing="ij")
+    P = np.exp(-0.5 * ((X - 6.0) ** 2 / 4.0 + (Y - 7.0) ** 2 / 6.0)) + 0.2 * rng.random(shape)
+    idx = box_cells(shape, (-6, -7))
+    o = const_oracle([a, b], h, limiter=LIM_MC)
+    o.init_cells(idx, P.reshape(-1))
+    o.ctu_step(dt)
+    got = cells_of(o)
+    pad = np.zeros((shape[0] + 4, shape[1] + 4))
+    pad[2:-2, 2:-2] = P
+    flip = (slice(None, None, sx), slice(None, None, sy))   # reflect negative components to positive
+    want = hr_ctu_positive(pad[flip], nx, ny, mc_phi)[flip][2:-2, 2:-2]
+    err = max(abs(got[tuple(Xc)] - want[Xc[0] + 6, Xc[1] + 7]) for Xc in idx)
+    assert err <= 1e-14
+
+
 @pytest.mark.parametrize("c", [2.0, -2.0])
 def test_ctu_lw_limiter_is_lax_wendroff_1d(c):
     """phi = 1 turns the high-resolution flux into Lax-Wendroff:
@@ -557,6 +607,32 @@ def test_probability_is_normalised_after_each_propagation():
         assert math.fsum(p.tolist()) * 0.125 == pytest.approx(1.0, abs=1e-14)
         assert o.t == t
 
+
+
+def test_first_order_mass_loss_per_step_is_small_and_never_a_gain():
+    """Conservation on Lorenz '63 h = 0.5 with the first-order scheme: fluxes
+    between active cells cancel, so a step changes the total only by what
+    leaves through the faces of the active set, and prune only removes cells;
+    both are losses (the scheme is positive for these Courant numbers) and
+    small (the set's edge is below thr_rel of the maximum): under 1e-6 per
+    step, 1e-6 per prune. The loop is taken step by step: grow, dt (Eq. 8),
+    update, normalise, prune every K steps."""
+    w = W.config("lorenz63_h0.5")
+    o = Oracle(w.n, w.dynamics, w.params, w.h, w.x0, w.thr_rel, w.cfl, w.prune_interval, LIM_NONE)
+    o.init_gaussian(w.mean, w.cov)
+    vol = math.prod(w.h)
+    mass = lambda: vol * math.fsum(o.read_cells()[1].tolist())
+    for k in range(1, 41):
+        o.grow()
+        before = mass()
+        o.ctu_step(o.cfl_dt())
+        lost = before - mass()
+        assert 0.0 <= lost < 1e-6
+        o.normalise()
+        if k % 20 == 0:
+            o.prune()
+            assert 0.0 <= 1.0 - mass() < 1e-6
+    assert o.read_cells()[1].min() >= 0.0
 
 # ---------------------------------------------------------------- symmetries of the whole step
 
