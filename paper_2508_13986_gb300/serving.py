@@ -63,6 +63,7 @@ class _Active:
     seg: int = 0
     steps: int = 0
     updates: int = 0
+    error: Optional[int] = None     # status of a failed call; the request ends with it
 
 
 @dataclass
@@ -80,8 +81,18 @@ class Server:
         cfg = gbees.make_config(w.n, w.dynamics, w.params, w.h, w.x0, w.thr_rel, w.cfl, w.prune_interval,
                                 self.precision, w.limiter, capacity_for(w))
         g = gbees.Grid(cfg, self.device)
-        g.init_gaussian(w.mean, w.cov)
-        return _Active(rid, w, arrival, now, g, gbees.gbees_workspace_bytes(cfg), w.segments())
+        a = _Active(rid, w, arrival, now, g, gbees.gbees_workspace_bytes(cfg), w.segments())
+        try:
+            g.init_gaussian(w.mean, w.cov)
+        except gbees.GbeesError as e:
+            a.error = e.status      # ends in the next round, before any step
+        return a
+
+    @staticmethod
+    def _failed_result(rid: int, w: Workload, arrival: float, admitted: float, now: float, steps: int,
+                       updates: int, error: str) -> Result:
+        return Result(rid, w.name, arrival, admitted, now, steps, updates, np.full(w.n, np.nan),
+                      np.full((w.n, w.n), np.nan), 0, error=error)
 
     def _finish(self, a: _Active, now: float, error: Optional[str] = None) -> Result:
         if error is None:
@@ -92,14 +103,14 @@ class Server:
             r = Result(a.rid, a.w.name, a.arrival, a.admitted, now, a.steps, a.updates, mean, cov, a.grid.count(),
                        idx, p)
         else:
-            r = Result(a.rid, a.w.name, a.arrival, a.admitted, now, a.steps, a.updates, np.full(a.w.n, np.nan),
-                       np.full((a.w.n, a.w.n), np.nan), 0, error=error)
+            r = self._failed_result(a.rid, a.w, a.arrival, a.admitted, now, a.steps, a.updates, error)
         a.grid.close()
         return r
 
     def _advance_segment(self, a: _Active) -> bool:
         """After the grid reached its current target: the measurement update if
-        one is due; True when the request is complete."""
+        one is due; True when the request is complete. Raises GbeesError when
+        the update fails (a measurement the density gives no weight to)."""
         t_target, meas = a.segments[a.seg]
         if meas is not None:
             a.grid.correct_gaussian(meas.y, meas.R, meas.H_idx)
@@ -133,7 +144,16 @@ class Server:
                 if self.mode == "single" and active:
                     break
                 pending.popleft()
-                a = self._admit(rid, w, arr, now if clock else virtual_now)
+                t_adm = now if clock else virtual_now
+                try:
+                    a = self._admit(rid, w, arr, t_adm)
+                except gbees.GbeesError as e:          # the configuration was refused
+                    results.append(self._failed_result(rid, w, arr, t_adm, t_adm, 0, 0,
+                                                       gbees.STATUS_NAMES.get(e.status, "error")))
+                    continue
+                except torch.cuda.OutOfMemoryError:    # the workspace could not be allocated
+                    results.append(self._failed_result(rid, w, arr, t_adm, t_adm, 0, 0, "ENOMEM"))
+                    continue
                 active.append(a)
                 used += a.nbytes
                 max_active = max(max_active, len(active))
@@ -144,20 +164,22 @@ class Server:
                 continue
             # one round: every grid in service towards its next target
             rounds += 1
-            failed: List[_Active] = []
+            failed: List[_Active] = [a for a in active if a.error is not None]
+            runnable = [a for a in active if a.error is None]
             reached: List[_Active] = []
             if self.mode == "single":
-                a = active[0]
-                try:
-                    st = a.grid.propagate(a.segments[a.seg][0])
-                    a.steps += st.steps
-                    a.updates += st.cell_updates
-                    reached.append(a)
-                except gbees.GbeesError:
-                    failed.append(a)
+                for a in runnable[:1]:
+                    try:
+                        st = a.grid.propagate(a.segments[a.seg][0])
+                        a.steps += st.steps
+                        a.updates += st.cell_updates
+                        reached.append(a)
+                    except gbees.GbeesError as e:
+                        a.error = e.status
+                        failed.append(a)
             else:
                 families: Dict[Tuple[int, int], List[_Active]] = {}
-                for a in active:
+                for a in runnable:
                     families.setdefault((a.w.n, a.w.dynamics), []).append(a)
                 for members in families.values():
                     targets = [m.segments[m.seg][0] for m in members]
@@ -167,6 +189,7 @@ class Server:
                         sts = [m.grid.stats() if m.grid.status == 0 else None for m in members]
                     for m, s, tt in zip(members, sts, targets):
                         if s is None:
+                            m.error = m.grid.status
                             failed.append(m)
                             continue
                         m.steps = s.total_steps
@@ -176,11 +199,18 @@ class Server:
             torch.cuda.synchronize(self.device)
             done_now = clock() if clock else virtual_now
             for a in failed:
-                results.append(self._finish(a, done_now, error=gbees.STATUS_NAMES.get(a.grid.status, "error")))
+                results.append(self._finish(a, done_now, error=gbees.STATUS_NAMES.get(a.error, "error")))
                 active.remove(a)
                 used -= a.nbytes
             for a in reached:
-                if self._advance_segment(a):
+                try:
+                    complete = self._advance_segment(a)
+                except gbees.GbeesError as e:
+                    results.append(self._finish(a, done_now, error=gbees.STATUS_NAMES.get(e.status, "error")))
+                    active.remove(a)
+                    used -= a.nbytes
+                    continue
+                if complete:
                     results.append(self._finish(a, clock() if clock else done_now))
                     active.remove(a)
                     used -= a.nbytes

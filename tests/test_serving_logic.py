@@ -169,3 +169,64 @@ def test_a_failing_grid_ends_alone_and_the_others_complete(fake_device, monkeypa
     assert len(res) == len(st) and srv.stats["failed"] == 1
     assert res[2].error == "ECAPACITY" and np.isnan(res[2].mean).all()
     assert all(r.error is None for i, r in enumerate(res) if i != 2)
+
+
+def _failing(monkeypatch, which, method, exc):
+    """Make the grid of the `which`-th request raise exc from `method`."""
+    orig = getattr(FakeGrid, method)
+
+    def wrapped(self, *a, **k):
+        if FakeGrid.created.index(self) == which:
+            raise exc
+        return orig(self, *a, **k)
+
+    monkeypatch.setattr(FakeGrid, method, wrapped)
+
+
+@pytest.mark.parametrize("mode", ["batched", "single"])
+def test_a_refused_initial_density_ends_that_request_alone(fake_device, monkeypatch, mode):
+    st = stream(count=8, seed=45)
+    _failing(monkeypatch, 2, "init_gaussian", gbees.GbeesError(gbees.GBEES_EKEYRANGE, "key range"))
+    srv = serving.Server(realtime=False, mode=mode, round_steps=4)
+    res = srv.run(st)
+    assert len(res) == len(st) and srv.stats["failed"] == 1
+    assert res[2].error == "EKEYRANGE" and res[2].steps == 0
+    assert not any(c[0] == "propagate" for c in fake_device.created[2].calls)
+    assert all(r.error is None for i, r in enumerate(res) if i != 2)
+
+
+@pytest.mark.parametrize("mode", ["batched", "single"])
+def test_a_degenerate_measurement_update_ends_that_request_alone(fake_device, monkeypatch, mode):
+    st = stream(count=10, seed=46)
+    which = next(i for i, (_, w) in enumerate(st) if any(m is not None for _, m in w.segments()))
+    _failing(monkeypatch, which, "correct_gaussian", gbees.GbeesError(gbees.GBEES_EDEGENERATE, "C = 0"))
+    srv = serving.Server(realtime=False, mode=mode, round_steps=4)
+    res = srv.run(st)
+    assert len(res) == len(st) and srv.stats["failed"] == 1
+    assert res[which].error == "EDEGENERATE" and np.isnan(res[which].mean).all()
+    assert all(r.error is None for i, r in enumerate(res) if i != which)
+
+
+@pytest.mark.parametrize("exc,name", [(gbees.GbeesError(gbees.GBEES_EINVAL, "bad configuration"), "EINVAL"),
+                                      ("oom", "ENOMEM")])
+def test_a_grid_that_cannot_be_made_is_reported_and_the_stream_goes_on(fake_device, monkeypatch, exc, name):
+    import torch
+
+    if exc == "oom":
+        exc = torch.cuda.OutOfMemoryError("no room")
+    st = stream(count=6, seed=47)
+    made = {"n": 0}
+
+    def grid(cfg, device="cuda:0"):
+        made["n"] += 1
+        if made["n"] == 4:
+            raise exc
+        return FakeGrid(cfg, device)
+
+    monkeypatch.setattr(gbees, "Grid", grid)
+    srv = serving.Server(realtime=False, round_steps=4)
+    res = srv.run(st)
+    assert len(res) == len(st) and srv.stats["failed"] == 1
+    assert res[3].error == name and res[3].steps == 0
+    assert len(fake_device.created) == len(st) - 1
+    assert all(r.error is None for i, r in enumerate(res) if i != 3)
