@@ -8,7 +8,7 @@
  * Cartesian grid that holds only the cells where p is non-negligible, and
  * folds in measurements by Bayes' rule (Eq. 4).
  *
- * One call sequence (the paper's flowchart, Fig. 1):
+ * One call sequence (the estimation loop of Sec. 2):
  *   gbees_workspace_bytes -> caller allocates device memory and a stream
  *   gbees_create -> gbees_init_gaussian | gbees_init_cells
  *   { gbees_propagate(t_m) -> gbees_correct_gaussian(y_m) }* -> gbees_propagate(t_end)
