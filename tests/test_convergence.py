@@ -131,15 +131,3 @@ def test_library_runner_plumbing_with_an_oracle_backed_grid(monkeypatch):
     assert np.array_equal(gi, oi) and np.array_equal(gp, op)
     assert len(made) == 1 and made[0].closed
 
-
-@pytest.mark.gpu
-def test_temporal_study_through_the_library_matches_the_oracle():
-    import __graft_entry__ as ge
-    from paper_2508_13986_gb300.convergence import gpu_runner
-
-    ge.build()
-    w = rotation()
-    gpu = temporal_study(w, eps=(0.8, 0.4), eps_ref=0.1, run=gpu_runner())
-    orc = temporal_study(w, eps=(0.8, 0.4), eps_ref=0.1, run=oracle_run)
-    for a, b in zip(gpu, orc):
-        assert a.E == pytest.approx(b.E, abs=1e-10) and a.BC == pytest.approx(b.BC, abs=1e-10)
