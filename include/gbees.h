@@ -29,6 +29,10 @@
  *     stream (the host buffers it writes are valid on return).
  *   - Host pointers (mean, cov, idx, p, y, R, ...) belong to the caller and are
  *     read or written only during the call.
+ *   - Device: a context belongs to the CUDA device that was current at
+ *     gbees_create (its workspace must be on that device). A call made while
+ *     another device is current returns GBEES_EINVAL (the context stays
+ *     usable).
  *   - Cell indices are signed integers; cell i has centre x0 + i * h (Eq. 5).
  *     Keys pack the indices with floor(63 / n) bits per dimension (32 for n = 1),
  *     i.e. -2^(bits-1) <= i_j < 2^(bits-1). An active cell must lie one layer
@@ -176,8 +180,8 @@ int gbees_propagate(gbees_ctx* ctx, double t_end, gbees_stats* stats);
  * device memory of gbees_batch_workspace_bytes(count) bytes, 256-byte
  * aligned, owned by the caller. stats: NULL or count entries. Returns the
  * first error of any grid (that grid's context is poisoned as by
- * gbees_propagate), GBEES_EINVAL for mismatched contexts. The contexts must
- * have no work in flight. */
+ * gbees_propagate), GBEES_EINVAL for mismatched contexts or a context listed
+ * more than once. The contexts must have no work in flight. */
 size_t gbees_batch_workspace_bytes(int32_t count);
 int gbees_batch_propagate(gbees_ctx* const* ctxs, int32_t count, const double* t_end, int64_t max_steps,
                           void* d_scratch, size_t scratch_bytes, gbees_stats* stats);

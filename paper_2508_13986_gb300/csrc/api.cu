@@ -49,6 +49,7 @@ struct gbees_ctx {
     Model m;
     Bufs b;
     cudaStream_t stream;
+    int dev = -1;      // CUDA device of the workspace (-1: not recorded)
     int grid;          // blocks of the fixed launch grid
     int status;        // sticky status
     bool has_grid;     // an init succeeded
@@ -327,6 +328,13 @@ bool sync_scalars(gbees_ctx* ctx, const char* where) {
 int guard(gbees_ctx* ctx, bool need_grid) {
     if (!ctx) return GBEES_EINVAL;
     if (ctx->status != GBEES_OK) return ctx->status;
+    if (ctx->dev >= 0) {  // kernels would get another device's pointers
+        int cur = -1;
+        if (cudaGetDevice(&cur) != cudaSuccess || cur != ctx->dev) {
+            ctx->err = "the current CUDA device is not the device of the context's workspace";
+            return GBEES_EINVAL;
+        }
+    }
     if (need_grid && !ctx->has_grid) {
         ctx->err = "no grid: call gbees_init_gaussian or gbees_init_cells first";
         return GBEES_EINVAL;
@@ -652,6 +660,7 @@ int gbees_create(const gbees_config* cfg, void* d_workspace, size_t workspace_by
         delete ctx;
         return GBEES_ECUDA;
     }
+    ctx->dev = dev;
     ctx->grid = std::min(GRID_MAX, std::max(1, sms * 4));
     k_reset<<<1, 1, 0, ctx->stream>>>(ctx->b.sc, 0.0);
     if (!sync_scalars(ctx, "create")) {
@@ -1006,6 +1015,14 @@ int gbees_batch_propagate(gbees_ctx* const* ctxs, int32_t count, const double* t
     const BatchLayout L = batch_layout(count);
     if (scratch_bytes < L.total || ((uintptr_t)d_scratch % ALIGN) != 0) return GBEES_EINVAL;
     gbees_ctx* c0 = ctxs[0];
+    {  // one block (or team) per grid: a context listed twice would be stepped twice at once
+        std::vector<gbees_ctx*> sorted_ctxs(ctxs, ctxs + count);
+        std::sort(sorted_ctxs.begin(), sorted_ctxs.end());
+        if (std::adjacent_find(sorted_ctxs.begin(), sorted_ctxs.end()) != sorted_ctxs.end()) {
+            if (c0) c0->err = "batch: a context appears more than once";
+            return GBEES_EINVAL;
+        }
+    }
     for (int32_t i = 0; i < count; ++i) {
         gbees_ctx* c = ctxs[i];
         if (!c) return GBEES_EINVAL;

@@ -9,6 +9,7 @@ is no CPU fallback.
 from __future__ import annotations
 
 import ctypes
+import functools
 import os
 from dataclasses import dataclass
 from typing import Optional, Sequence, Tuple
@@ -270,6 +271,18 @@ def make_config(n: int, dynamics: int, params: Sequence[float], h: Sequence[floa
     return c
 
 
+def _on_device(fn):
+    """Run a Grid method with the grid's device current (the library refuses
+    calls made while another device is current)."""
+    @functools.wraps(fn)
+    def wrapper(self, *args, **kwargs):
+        import torch
+
+        with torch.cuda.device(self.device):
+            return fn(self, *args, **kwargs)
+    return wrapper
+
+
 class Grid:
     """One GBEES grid on a CUDA device; the workspace is a torch uint8 tensor."""
 
@@ -305,32 +318,38 @@ class Grid:
         if rc != 0:
             raise GbeesError(rc, gbees_last_error(self.ctx))
 
+    @_on_device
     def init_gaussian(self, mean, cov, t0: float = 0.0):
         m = np.ascontiguousarray(mean, dtype=np.float64)
         C = np.ascontiguousarray(cov, dtype=np.float64)
         self._check(gbees_init_gaussian(self.ctx, m, C, t0))
 
+    @_on_device
     def init_cells(self, idx, p, t0: float = 0.0, step0: int = 0):
         I = np.ascontiguousarray(idx, dtype=np.int32).reshape(-1, self.n)
         P = np.ascontiguousarray(p, dtype=np.float64)
         self._check(gbees_init_cells(self.ctx, I, P, t0, step0))
 
+    @_on_device
     def propagate(self, t_end: float) -> Stats:
         st = gbees_stats()
         self._check(gbees_propagate(self.ctx, t_end, st))
         return Stats.of(st)
 
+    @_on_device
     def correct_gaussian(self, y, R, H_idx=None):
         yy = np.ascontiguousarray(y, dtype=np.float64).reshape(-1)
         RR = np.ascontiguousarray(R, dtype=np.float64)
         HH = np.ascontiguousarray(np.arange(yy.size) if H_idx is None else H_idx, dtype=np.int32)
         self._check(gbees_correct_gaussian(self.ctx, yy, RR, HH))
 
+    @_on_device
     def count(self) -> int:
         rc, n = gbees_count(self.ctx)
         self._check(rc)
         return n
 
+    @_on_device
     def read_cells(self, sorted_: bool = True):
         n = self.count()
         idx = np.zeros((max(n, 1), self.n), dtype=np.int32)
@@ -339,12 +358,14 @@ class Grid:
         self._check(rc)
         return idx[:n2], p[:n2]
 
+    @_on_device
     def moments(self):
         mean = np.zeros(self.n)
         cov = np.zeros((self.n, self.n))
         self._check(gbees_moments(self.ctx, mean, cov))
         return mean, cov
 
+    @_on_device
     def stats(self) -> Stats:
         st = gbees_stats()
         self._check(gbees_get_stats(self.ctx, st))
@@ -354,6 +375,7 @@ class Grid:
     def status(self) -> int:
         return gbees_get_status(self.ctx)
 
+    @_on_device
     def profile(self, enable: Optional[bool] = None, reset: bool = False) -> dict:
         """Switch per-phase event timing on or off and return the counters as a dict."""
         if enable is not None or reset:
@@ -392,8 +414,9 @@ def propagate_batch(grids: Sequence["Grid"], t_end: Sequence[float], max_steps: 
     with torch.cuda.device(dev):
         scratch = torch.empty(nbytes, dtype=torch.uint8, device=dev)
     stats = (gbees_stats * count)()
-    rc = gbees_batch_propagate([g.ctx for g in grids], np.asarray(t_end, dtype=np.float64), max_steps,
-                               scratch.data_ptr(), nbytes, stats)
+    with torch.cuda.device(dev):
+        rc = gbees_batch_propagate([g.ctx for g in grids], np.asarray(t_end, dtype=np.float64), max_steps,
+                                   scratch.data_ptr(), nbytes, stats)
     if rc != 0:
         msgs = [gbees_last_error(g.ctx) for g in grids if g.status != 0] or [gbees_last_error(grids[0].ctx)]
         raise GbeesError(rc, "batch: " + msgs[0])
