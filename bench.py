@@ -46,7 +46,8 @@ TRAFFIC_BYTES_PER_CELL = {
     "lorenz63_h0.25/f64": {"bytes_per_cell": 10.360832e6 / 2118979, "src": "c00cd41fc877901a"},
 }
 DEVICE_SOURCES = [os.path.join(ROOT, "paper_2508_13986_gb300", "csrc", f)
-                  for f in ("gbees_device.cuh", "gbees_phases.cuh", "gbees_kernels.cuh", "gbees_persistent.cuh")]
+                  for f in ("gbees_keys.cuh", "gbees_device.cuh", "gbees_phases.cuh", "gbees_kernels.cuh",
+                            "gbees_misc_kernels.cuh", "gbees_persistent.cuh")]
 
 
 def parse():
