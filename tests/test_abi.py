@@ -5,6 +5,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 from paper_2508_13986_gb300 import gbees
@@ -81,3 +82,45 @@ def test_create_rejects_a_short_or_misaligned_workspace(lib):
     assert rc == gbees.GBEES_EINVAL and ctx == 0
     rc, ctx = gbees.gbees_create(cfg, 256 * 1000 + 8, nb, 0)
     assert rc == gbees.GBEES_EINVAL and ctx == 0
+
+
+def test_every_entry_point_refuses_a_null_context(lib):
+    """A NULL context is GBEES_EINVAL (or a no-op for destroy) before any CUDA
+    call; nothing here needs a GPU."""
+    gbees.load_library()
+    E = gbees.GBEES_EINVAL
+    d = np.zeros(9)
+    i = np.zeros(9, dtype=np.int32)
+    st = gbees.gbees_stats()
+    assert gbees.gbees_init_gaussian(0, d[:3], d, 0.0) == E
+    assert gbees.gbees_init_cells(0, i[:3], d[:1], 0.0, 0) == E
+    assert gbees.gbees_propagate(0, 1.0, st) == E
+    assert gbees.gbees_correct_gaussian(0, d[:1], d[:1], i[:1]) == E
+    assert gbees.gbees_count(0)[0] == E
+    assert gbees.gbees_read_cells(0, i[:3].reshape(1, 3), d[:1], True)[0] == E
+    assert gbees.gbees_moments(0, d[:3], d) == E
+    assert gbees.gbees_get_stats(0, st) == E
+    assert gbees.gbees_get_status(0) == E
+    assert gbees.gbees_profile_control(0, True, False) == E
+    assert gbees.gbees_profile_read(0, gbees.gbees_profile()) == E
+    assert isinstance(gbees.gbees_last_error(0), str)
+    gbees.gbees_destroy(0)
+
+
+def test_batch_arguments_are_checked_before_any_launch(lib):
+    gbees.load_library()
+    E = gbees.GBEES_EINVAL
+    assert gbees.gbees_batch_workspace_bytes(0) == 0
+    nb = gbees.gbees_batch_workspace_bytes(2)
+    assert nb > 0
+    f = gbees._f("gbees_batch_propagate")
+    ctxs = (ctypes.c_void_p * 2)(0, 0)
+    t_end = np.ones(2)
+    stats = (gbees.gbees_stats * 2)()
+    dp = t_end.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    assert f(None, 2, dp, 0, ctypes.c_void_p(256), nb, stats) == E                 # no contexts
+    assert f(ctxs, 0, dp, 0, ctypes.c_void_p(256), nb, stats) == E                 # empty batch
+    assert f(ctxs, 2, dp, -1, ctypes.c_void_p(256), nb, stats) == E                # negative step cap
+    assert f(ctxs, 2, dp, 0, ctypes.c_void_p(256), nb - 1, stats) == E             # scratch too small
+    assert f(ctxs, 2, dp, 0, ctypes.c_void_p(256 + 8), nb, stats) == E             # misaligned scratch
+    assert f(ctxs, 2, dp, 0, ctypes.c_void_p(256), nb, stats) == E                 # NULL contexts
