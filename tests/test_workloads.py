@@ -60,3 +60,16 @@ def test_paper_cases():
     (m,) = e1.measurements
     assert m.t == 1.0 and m.y.tolist() == [-8.0] and m.H_idx.tolist() == [2] and m.R.tolist() == [[1.0]]
     assert e2.n == 6 and e2.h == (0.1,) * 6 and e2.mean[0] == 4.5 and e2.t_end == 1.3
+
+
+def test_the_truth_integrator_is_fourth_order_and_converged_at_its_step():
+    """The measurements' truth (RK4, dt = 1e-4) agrees with dt = 1e-5 far below
+    the measurement noise, and halving a coarse step cuts the error by 2^4."""
+    rhs = lambda x: W._l63_rhs(x, (10.0, 28.0, 8.0 / 3.0))
+    x0 = np.array([-11.5, -10.0, 9.5])
+    ref = W.truth_trajectory(rhs, x0, [0.25, 0.5], dt=1e-5)
+    used = W.truth_trajectory(rhs, x0, [0.25, 0.5], dt=1e-4)
+    assert max(np.abs(a - b).max() for a, b in zip(ref, used)) < 1e-9
+    e1 = np.abs(W.truth_trajectory(rhs, x0, [0.5], dt=0.01)[0] - ref[1]).max()
+    e2 = np.abs(W.truth_trajectory(rhs, x0, [0.5], dt=0.005)[0] - ref[1]).max()
+    assert 12.0 < e1 / e2 < 20.0
