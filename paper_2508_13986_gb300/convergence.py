@@ -76,28 +76,58 @@ def restrict(idx_f, p_f, h_f: Sequence[float], x0_f: Sequence[float], h_c: Seque
 
 # ------------------------------------------------------------------ studies
 
-Runner = Callable[[Workload], Tuple[np.ndarray, np.ndarray]]
+Runner = Callable[..., object]
+ReadOut = Tuple[np.ndarray, np.ndarray]
+
+
+def schedule(w: Workload, times: Optional[Sequence[float]] = None) -> List[Tuple[float, object, bool]]:
+    """The targets of a run in time order: (t, measurement or None, read out
+    here?). Without sample times the run reads out once, at t_end. A sample at
+    a measurement time is taken after the update. Sample times must lie in
+    [0, t_end]."""
+    marks: Dict[float, List[object]] = {}
+    for t, meas in w.segments():
+        marks.setdefault(float(t), [None, False])[0] = meas
+    samples = [w.t_end] if times is None else [float(t) for t in times]
+    for t in samples:
+        if not 0.0 <= t <= w.t_end:
+            raise ValueError(f"sample time {t} outside [0, {w.t_end}]")
+        marks.setdefault(t, [None, False])[1] = True
+    return [(t, marks[t][0], marks[t][1]) for t in sorted(marks)]
+
+
+def run_schedule(grid, w: Workload, times: Optional[Sequence[float]] = None) -> List[ReadOut]:
+    """Drive a grid (the library's Grid or any object with the same methods)
+    from its initial Gaussian through the schedule; the read-outs at the
+    sample times, in order."""
+    grid.init_gaussian(w.mean, w.cov)
+    out = []
+    for t, meas, sample in schedule(w, times):
+        if t > 0.0:
+            grid.propagate(t)
+        if meas is not None:
+            grid.correct_gaussian(meas.y, meas.R, meas.H_idx)
+        if sample:
+            out.append(grid.read_cells())
+    return out
 
 
 def gpu_runner(precision: Optional[int] = None, device: str = "cuda:0") -> Runner:
-    """Propagation through the CUDA library (measurements included) to the
-    workload's t_end; returns the read-out (sorted cells, densities)."""
+    """Propagation through the CUDA library (measurements included). run(w)
+    returns the read-out (sorted cells, densities) at the workload's t_end;
+    run(w, times) the read-outs at the given times."""
     from . import gbees
     from .workloads import capacity_for
 
     prec = gbees.GBEES_FP64 if precision is None else precision
 
-    def run(w: Workload):
+    def run(w: Workload, times: Optional[Sequence[float]] = None):
         g = gbees.grid_for_workload(w, precision=prec, max_cells=capacity_for(w), device=device)
         try:
-            g.init_gaussian(w.mean, w.cov)
-            for t, meas in w.segments():
-                g.propagate(t)
-                if meas is not None:
-                    g.correct_gaussian(meas.y, meas.R, meas.H_idx)
-            return g.read_cells()
+            outs = run_schedule(g, w, times)
         finally:
             g.close()
+        return outs if times is not None else outs[-1]
 
     return run
 
@@ -107,6 +137,28 @@ class Point:
     value: float       # epsilon (CFL number) or eta (cell width factor)
     E: float
     BC: float
+
+
+@dataclass
+class SeriesPoint:
+    t: float
+    E: float
+    BC: float
+
+
+def temporal_series(w: Workload, eps: Sequence[float], eps_ref: float, times: Sequence[float],
+                    run: Optional[Runner] = None) -> Dict[float, List[SeriesPoint]]:
+    """E(t) and BC(t) at the sample times for every CFL number epsilon,
+    against the reference epsilon (the curves the paper plots against time).
+    run(w, times) returns the read-outs at the sample times."""
+    run = run or gpu_runner()
+    ref = run(w.with_(cfl=eps_ref), times)
+    out = {}
+    for e in eps:
+        got = run(w.with_(cfl=e), times)
+        out[e] = [SeriesPoint(float(t), l1_error(*a, *r, w.h), bhattacharyya(*a, *r, w.h))
+                  for t, a, r in zip(times, got, ref)]
+    return out
 
 
 def temporal_study(w: Workload, eps: Sequence[float], eps_ref: float, run: Optional[Runner] = None) -> List[Point]:

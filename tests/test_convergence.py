@@ -8,7 +8,8 @@ import pytest
 
 from oracle.oracle import DYN_LINEAR, Oracle
 from paper_2508_13986_gb300 import workloads as W
-from paper_2508_13986_gb300.convergence import bhattacharyya, l1_error, restrict, spatial_study, temporal_study
+from paper_2508_13986_gb300.convergence import (bhattacharyya, l1_error, restrict, run_schedule, schedule,
+                                                 spatial_study, temporal_series, temporal_study)
 
 
 def normalised(idx, p, h):
@@ -60,8 +61,12 @@ def rotation():
                       prune_interval=10)
 
 
-def oracle_run(w):
+def oracle_run(w, times=None):
+    """The workload through the oracle: the read-out at t_end, or (times given)
+    the read-outs at those times through the library's schedule."""
     o = Oracle(w.n, w.dynamics, w.params, w.h, w.x0, w.thr_rel, w.cfl, w.prune_interval, w.limiter)
+    if times is not None:
+        return run_schedule(o, w, times)
     o.init_gaussian(w.mean, w.cov)
     for t, m in w.segments():
         o.propagate(t)
@@ -131,3 +136,34 @@ def test_library_runner_plumbing_with_an_oracle_backed_grid(monkeypatch):
     assert np.array_equal(gi, oi) and np.array_equal(gp, op)
     assert len(made) == 1 and made[0].closed
 
+
+def test_schedule_merges_sample_times_with_the_measurements():
+    w = rotation().with_(t_end=0.3)
+    m1 = W.Measurement(0.1, np.array([1.5, 0.0]), 0.25 * np.eye(2), np.arange(2, dtype=np.int32))
+    m2 = W.Measurement(0.2, np.array([1.4, 0.2]), 0.25 * np.eye(2), np.arange(2, dtype=np.int32))
+    w = w.with_(measurements=[m1, m2])
+    got = schedule(w, [0.0, 0.15, 0.2, 0.3])
+    assert [(t, m, s) for t, m, s in got] == [(0.0, None, True), (0.1, m1, False), (0.15, None, True),
+                                              (0.2, m2, True), (0.3, None, True)]
+    assert schedule(w) == [(0.1, m1, False), (0.2, m2, False), (0.3, None, True)]
+    with pytest.raises(ValueError):
+        schedule(w, [0.35])
+
+
+def test_sampling_at_the_end_time_alone_is_the_plain_run():
+    w = rotation().with_(t_end=0.2)
+    (i1, p1), = oracle_run(w, [0.2])
+    i2, p2 = oracle_run(w)
+    assert np.array_equal(i1, i2) and np.array_equal(p1, p2)
+
+
+def test_temporal_series_starts_equal_and_orders_by_epsilon():
+    """E(0) = 0 and BC(0) = 1 (the same initial density), and at every later
+    sample the coarser epsilon is further from the reference."""
+    times = [0.0, 0.1, 0.2, 0.4]
+    series = temporal_series(rotation(), eps=(0.8, 0.4), eps_ref=0.1, times=times, run=oracle_run)
+    for e, pts in series.items():
+        assert [q.t for q in pts] == times
+        assert pts[0].E == 0.0 and pts[0].BC == pytest.approx(1.0, abs=1e-14)
+    for a, b in zip(series[0.8][1:], series[0.4][1:]):
+        assert a.E > b.E > 0.0 and a.BC < b.BC
