@@ -173,6 +173,31 @@ def temporal_study(w: Workload, eps: Sequence[float], eps_ref: float, run: Optio
     return out
 
 
+def _on_common_grid(a: ReadOut, h_a, r: ReadOut, h_r, x0) -> Tuple[float, float]:
+    """E and BC of read-out a (widths h_a) against r (widths h_r), both on the
+    coarser of the two grids."""
+    if tuple(h_a) >= tuple(h_r):
+        ci, cp = restrict(*r, h_r, x0, h_a, x0)
+        return l1_error(*a, ci, cp, h_a), bhattacharyya(*a, ci, cp, h_a)
+    ci, cp = restrict(*a, h_a, x0, h_r, x0)
+    return l1_error(ci, cp, *r, h_r), bhattacharyya(ci, cp, *r, h_r)
+
+
+def spatial_series(w: Workload, etas: Sequence[float], eta_ref: float, times: Sequence[float],
+                   run: Optional[Runner] = None) -> Dict[float, List[SeriesPoint]]:
+    """E(t) and BC(t) at the sample times for every cell width factor eta,
+    against the reference widths eta_ref h, compared on the coarser grid."""
+    run = run or gpu_runner()
+    h_ref = tuple(eta_ref * x for x in w.h)
+    ref = run(w.with_(h=h_ref), times)
+    out = {}
+    for eta in etas:
+        h = tuple(eta * x for x in w.h)
+        got = run(w.with_(h=h), times)
+        out[eta] = [SeriesPoint(float(t), *_on_common_grid(a, h, r, h_ref, w.x0)) for t, a, r in zip(times, got, ref)]
+    return out
+
+
 def spatial_study(w: Workload, etas: Sequence[float], eta_ref: float, run: Optional[Runner] = None) -> List[Point]:
     """E and BC at t_end of propagations with cell widths eta h against a
     reference with widths eta_ref h, both on the grid of the coarser one."""

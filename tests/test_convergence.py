@@ -9,7 +9,7 @@ import pytest
 from oracle.oracle import DYN_LINEAR, Oracle
 from paper_2508_13986_gb300 import workloads as W
 from paper_2508_13986_gb300.convergence import (bhattacharyya, l1_error, restrict, run_schedule, schedule,
-                                                 spatial_study, temporal_series, temporal_study)
+                                                 spatial_series, spatial_study, temporal_series, temporal_study)
 
 
 def normalised(idx, p, h):
@@ -167,3 +167,18 @@ def test_temporal_series_starts_equal_and_orders_by_epsilon():
         assert pts[0].E == 0.0 and pts[0].BC == pytest.approx(1.0, abs=1e-14)
     for a, b in zip(series[0.8][1:], series[0.4][1:]):
         assert a.E > b.E > 0.0 and a.BC < b.BC
+
+
+def test_spatial_series_equals_the_study_at_the_end_time():
+    """Sampled at t_end alone, the series is the study (a sample at an earlier
+    time clips a time step, so it changes the later values slightly)."""
+    w = rotation().with_(cfl=0.5, t_end=0.2)
+    at_end = spatial_series(w, etas=(2.0, 1.0), eta_ref=0.5, times=[0.2], run=oracle_run)
+    study = spatial_study(w, etas=(2.0, 1.0), eta_ref=0.5, run=oracle_run)
+    for q in study:
+        (end,) = at_end[q.value]
+        assert end.t == 0.2 and end.E == q.E and end.BC == q.BC
+    series = spatial_series(w, etas=(2.0, 1.0), eta_ref=0.5, times=[0.1, 0.2], run=oracle_run)
+    for eta in (2.0, 1.0):
+        assert all(0.0 < q.E < 2.0 and 0.0 < q.BC <= 1.0 for q in series[eta])
+    assert series[2.0][-1].E > series[1.0][-1].E
