@@ -264,6 +264,7 @@ def time_precision(args, w, precision, dev, rank, world):
     upd_sum = reduce_sum(total_updates, world)
     e2e_max = reduce_max(e2e_ms, world)
     e2e_sum = reduce_sum(e2e_updates, world)
+    steps_sum = reduce_sum(total_steps, world)
 
     peak_gbs, peak_src = load_peaks()
     bpc = bytes_per_update(w.n, precision)
@@ -298,6 +299,7 @@ def time_precision(args, w, precision, dev, rank, world):
         "ms_per_step": ms_max / args.steps,
         "updates_per_step": total_updates / args.steps,
         "time_steps_per_run": total_steps / args.steps,
+        "time_steps_per_s": steps_sum / (ms_max / 1e3),
         "peak_cells": peak,
         "e2e": {"value": e2e_sum / (e2e_max / 1e3), "unit": METRIC, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_max / args.steps},
@@ -391,6 +393,7 @@ def time_batch(args, ws, precision, dev, rank, world):
     upd_sum = reduce_sum(total_updates, world)
     e2e_max = reduce_max(e2e_ms, world)
     e2e_sum = reduce_sum(e2e_updates, world)
+    steps_sum = reduce_sum(total_steps, world)
     peak_gbs, peak_src = load_peaks()
     bpc = bytes_per_update(ws[0].n, precision)
     launches_k = max(pt["persist_launches"], 1)
@@ -402,6 +405,7 @@ def time_batch(args, ws, precision, dev, rank, world):
         "ms_per_step": ms_max / args.steps,
         "updates_per_step": total_updates / args.steps,
         "time_steps_per_run": total_steps / args.steps,
+        "time_steps_per_s": steps_sum / (ms_max / 1e3),
         "peak_cells": peak,
         "e2e": {"value": e2e_sum / (e2e_max / 1e3), "unit": METRIC, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_max / args.steps},
@@ -566,6 +570,7 @@ def main_ours(args):
                        "launch_mode": args.launch_mode,
                        "cell_updates_per_step": main["updates_per_step"],
                        "time_steps_per_run": main["time_steps_per_run"],
+                       "time_steps_per_s": main["time_steps_per_s"],
                        "peak_cells": main["peak_cells"]},
             "e2e": main["e2e"],
             "roofline": main["roofline"],

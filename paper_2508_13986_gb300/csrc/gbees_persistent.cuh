@@ -48,7 +48,7 @@ template <int N, int DYN, typename T>
 __device__ __forceinline__ void step_loop(const Model& m, const Bufs& b, long long max_steps, int nb, int bi) {
     __shared__ StepShared ss;
     DevScalars* sc = b.sc;
-    // The verdict is the same for every thread of the block: a warp that read
+    // The result is the same for every thread of the block: a warp that read
     // the error flag after another warp of the block had already raised it in
     // the next phase must not return while the others go on (their block
     // barriers would then pair with the wrong ones).
