@@ -531,9 +531,12 @@ def test_translation_at_courant_one_is_an_exact_shift():
             assert v == 0.0
 
 
-def test_linear_dynamics_moments_converge_to_closed_form():
+@pytest.mark.parametrize("lim", [LIM_MC, LIM_NONE])
+def test_linear_dynamics_moments_converge_to_closed_form(lim):
     """f = A x keeps a Gaussian Gaussian: m(t) = e^{At} m0, S(t) = e^{At} S0 e^{A't}.
-    The grid moments approach it as h is refined."""
+    The grid moments approach it as h is refined, at observed order >= 1 (the
+    face velocities of a varying drift make the moments first order even
+    where the limited scheme is second order)."""
     A = np.array([[-0.5, 1.0], [-1.0, -0.5]])
     m0 = np.array([1.0, 0.5])
     S0 = np.array([[0.09, 0.02], [0.02, 0.06]])
@@ -542,14 +545,14 @@ def test_linear_dynamics_moments_converge_to_closed_form():
     m_ref, S_ref = E @ m0, E @ S0 @ E.T
     errs = []
     for h in (0.1, 0.05, 0.025):
-        o = Oracle(2, DYN_LINEAR, list(A.reshape(-1)) + [0.0, 0.0], [h, h], list(m0), 1e-9, 0.9, 5, LIM_MC)
+        o = Oracle(2, DYN_LINEAR, list(A.reshape(-1)) + [0.0, 0.0], [h, h], list(m0), 1e-9, 0.9, 5, lim)
         o.init_gaussian(m0, S0)
         o.propagate(T)
         m, S = o.moments()
         errs.append(np.abs(m - m_ref).max() + np.abs(S - S_ref).max())
-    assert errs[0] > errs[1] > errs[2]
-    assert errs[2] < 2e-3
-    assert errs[0] / errs[2] > 3.0
+    orders = [math.log2(errs[k] / errs[k + 1]) for k in range(2)]
+    assert min(orders) >= 0.95, orders
+    assert errs[2] < (2e-3 if lim == LIM_MC else 1.2e-2)
 
 
 def test_measurement_update_of_a_gaussian_is_the_kalman_posterior():
