@@ -98,9 +98,9 @@ def test_batch_edge_cases():
         g.close()
 
 
-def test_batch_queue_mode_with_more_grids_than_resident_blocks():
-    """More grids than resident blocks: each block takes the next grid from the
-    queue and runs it alone; sampled grids equal their one-by-one runs."""
+def test_a_batch_of_many_small_grids_equals_one_by_one_runs():
+    """320 grids in one launch (small teams, many of one block); sampled grids
+    equal their one-by-one runs."""
     count = 320
     ws = W.lorenz63_batch(count=count, seed=14, h_choices=(0.5,), t_range=(0.01, 0.03),
                           sigma_range=(0.5, 0.6), prune_interval=3)

@@ -1,0 +1,46 @@
+"""A batch wider than the GPU holds at once: with more grids than resident
+blocks the batched launch cannot give every grid a team, so each block takes
+the next grid from a queue and runs its whole step loop alone (one-block
+barriers). Sampled grids must equal their one-by-one runs bit for bit."""
+import numpy as np
+import pytest
+
+from paper_2508_13986_gb300 import gbees
+from paper_2508_13986_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+BLOCKS_PER_SM_MAX = 4   # 256 threads x 64 registers: at most 4 batch blocks fit an SM's 65536 registers
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__ as ge
+    ge.build()
+
+
+def test_queue_mode_batch_equals_one_by_one_runs():
+    import torch
+
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    count = (BLOCKS_PER_SM_MAX + 1) * sms          # more grids than resident blocks
+    ws = W.lorenz63_batch(count=count, seed=15, h_choices=(0.5,), t_range=(0.01, 0.02),
+                          sigma_range=(0.5, 0.6), prune_interval=3)
+    gs = []
+    for w in ws:
+        g = gbees.grid_for_workload(w, precision=gbees.GBEES_FP32, max_cells=1 << 14)
+        g.init_gaussian(w.mean, w.cov)
+        gs.append(g)
+    st = gbees.propagate_batch(gs, [w.t_end for w in ws])
+    assert all(s.t == w.t_end and s.steps > 0 for s, w in zip(st, ws))
+    for i in (0, 1, sms, count // 2, count - 2, count - 1):
+        a = gbees.grid_for_workload(ws[i], precision=gbees.GBEES_FP32, max_cells=1 << 14)
+        a.init_gaussian(ws[i].mean, ws[i].cov)
+        sa = a.propagate(ws[i].t_end)
+        assert sa.steps == st[i].steps and sa.t == st[i].t and sa.cell_updates == st[i].cell_updates
+        ia, pa = a.read_cells()
+        ib, pb = gs[i].read_cells()
+        assert np.array_equal(ia, ib) and np.array_equal(pa, pb)
+        a.close()
+    for g in gs:
+        g.close()
