@@ -6,6 +6,7 @@ invariant, a textbook special case, a library routine or a brute force on tiny
 inputs. Together they are chosen so that a dropped term, a wrong sign, a wrong
 index or a transposed operand anywhere in the oracle fails at least one.
 """
+import itertools
 import math
 import os
 
@@ -180,6 +181,18 @@ def test_downwind_sets_for_divergent_convergent_and_3d_flows():
     # zero velocity in one dimension grows nothing along it
     o = const_oracle([1.0, 0.0], [1, 1])
     assert set(o.downwind([0, 0])) == {(1, 0)}
+    # 6-D: the faces of the dimensions with a velocity and every pair of them
+    c = [1.0, -1.0, 0.5, 0.0, 2.0, -0.25]
+    o = const_oracle(c, [1] * 6)
+    moving = [(j, 1 if v > 0 else -1) for j, v in enumerate(c) if v != 0.0]
+    want = set()
+    for j, s_ in moving:
+        want.add(tuple(s_ if k == j else 0 for k in range(6)))
+    for (j, sj), (l, sl) in itertools.combinations(moving, 2):
+        want.add(tuple(sj if k == j else sl if k == l else 0 for k in range(6)))
+    d = o.downwind([3, -2, 0, 5, 1, -7])
+    assert len(d) == len(set(d)) == 5 + 10
+    assert {tuple(x - y for x, y in zip(X, (3, -2, 0, 5, 1, -7))) for X in d} == want
 
 
 def test_grow_then_prune_leaves_exactly_S_and_its_downwind_set():
