@@ -21,7 +21,6 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -144,8 +143,6 @@ class ClockSampler:
 
 def run_workload(grid, w, with_readout=False):
     """One whole run through the public API. Returns (cell updates, steps, bytes in, bytes out, peak cells)."""
-    import numpy as np
-
     grid.init_gaussian(w.mean, w.cov)
     h2d = 8 * w.n + 8 * w.n * w.n
     updates = steps = 0

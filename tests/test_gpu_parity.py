@@ -1,15 +1,13 @@
 """GPU parity: the CUDA library against the CPU oracle, cell by cell, on seeded
 synthetic workloads (FP64: identical active sets and L1 <= 1e-10; FP32 store:
 L1 <= 1e-5 and moments within 1e-4 relative)."""
-import math
-
 import numpy as np
 import pytest
 
-from oracle.oracle import LIM_LW, LIM_MC, LIM_NONE, Oracle
+from oracle.oracle import LIM_LW, LIM_MC, LIM_NONE
 from paper_2508_13986_gb300 import gbees
 from paper_2508_13986_gb300 import workloads as W
-from parity_helpers import FP32_L1, FP32_MOM, FP64_L1, assert_fp64_parity, compare, make_pair, run_schedule
+from parity_helpers import FP32_L1, FP32_MOM, assert_fp64_parity, compare, make_pair, run_schedule
 
 pytestmark = pytest.mark.gpu
 
