@@ -325,16 +325,20 @@ bool sync_scalars(gbees_ctx* ctx, const char* where) {
     return true;
 }
 
+// Kernels of a context must run on the device of its workspace: a call made
+// while another device is current is refused (the context stays usable).
+bool on_ctx_device(gbees_ctx* ctx) {
+    if (ctx->dev < 0) return true;
+    int cur = -1;
+    if (cudaGetDevice(&cur) == cudaSuccess && cur == ctx->dev) return true;
+    ctx->err = "the current CUDA device is not the device of the context's workspace";
+    return false;
+}
+
 int guard(gbees_ctx* ctx, bool need_grid) {
     if (!ctx) return GBEES_EINVAL;
     if (ctx->status != GBEES_OK) return ctx->status;
-    if (ctx->dev >= 0) {  // kernels would get another device's pointers
-        int cur = -1;
-        if (cudaGetDevice(&cur) != cudaSuccess || cur != ctx->dev) {
-            ctx->err = "the current CUDA device is not the device of the context's workspace";
-            return GBEES_EINVAL;
-        }
-    }
+    if (!on_ctx_device(ctx)) return GBEES_EINVAL;
     if (need_grid && !ctx->has_grid) {
         ctx->err = "no grid: call gbees_init_gaussian or gbees_init_cells first";
         return GBEES_EINVAL;
@@ -716,6 +720,7 @@ const char* gbees_last_error(gbees_ctx* ctx) {
 
 int gbees_init_gaussian(gbees_ctx* ctx, const double* mean, const double* cov, double t0) {
     if (!ctx) return GBEES_EINVAL;
+    if (!on_ctx_device(ctx)) return GBEES_EINVAL;
     if (ctx->status != GBEES_OK && ctx->status != GBEES_ECUDA) {  // a new grid clears a poisoned state
         ctx->status = GBEES_OK;
         ctx->err.clear();
@@ -791,6 +796,7 @@ int gbees_init_gaussian(gbees_ctx* ctx, const double* mean, const double* cov, d
 
 int gbees_init_cells(gbees_ctx* ctx, const int32_t* idx, const double* p, int64_t N, double t0, int64_t step0) {
     if (!ctx) return GBEES_EINVAL;
+    if (!on_ctx_device(ctx)) return GBEES_EINVAL;
     if (ctx->status != GBEES_OK && ctx->status != GBEES_ECUDA) {
         ctx->status = GBEES_OK;
         ctx->err.clear();
