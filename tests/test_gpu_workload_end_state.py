@@ -1,0 +1,71 @@
+"""Parity at full size in the configuration the bench times: the Lorenz '63
+h = 0.25 workload (t_end 2, eight full-state measurements) runs through the
+library to its end as the bench runs it (launch mode AUTO, which picks the
+persistent step-loop kernel at this size; max_cells 2^22). The oracle cannot
+redo the whole run in a test's time, so it takes the GPU's end state as its
+initial cells and both continue for a further 0.02 time units (about a dozen
+steps, with a prune); the two must then agree at the bar of their precision."""
+import numpy as np
+import pytest
+
+from oracle.oracle import Oracle
+from paper_2508_13986_gb300 import gbees
+from paper_2508_13986_gb300 import workloads as W
+from parity_helpers import FP32_L1, FP32_MOM, assert_fp64_parity, compare
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__ as ge
+    ge.build()
+
+
+def run_to_end(w, precision):
+    g = gbees.grid_for_workload(w, precision=precision, max_cells=1 << 22)
+    g.init_gaussian(w.mean, w.cov)
+    updates = 0
+    for t, meas in w.segments():
+        updates += g.propagate(t).cell_updates
+        if meas is not None:
+            g.correct_gaussian(meas.y, meas.R, meas.H_idx)
+    return g, updates
+
+
+def oracle_from(g, w):
+    st = g.stats()
+    idx, p = g.read_cells()
+    o = Oracle(w.n, w.dynamics, w.params, w.h, w.x0, w.thr_rel, w.cfl, w.prune_interval, w.limiter)
+    o.init_cells(idx, p, st.t, st.total_steps)
+    return o, st
+
+
+def test_bench_workload_end_state_continues_like_the_oracle_fp64():
+    w = W.config("lorenz63_h0.25")
+    g, updates = run_to_end(w, gbees.GBEES_FP64)
+    assert updates > 2e7                          # the whole workload ran (3.2e7 cell updates)
+    o, st = oracle_from(g, w)
+    assert st.t == w.t_end
+    t_more = st.t + 0.02
+    gs = g.propagate(t_more)
+    os_ = o.propagate(t_more)
+    assert gs.steps == os_.steps and gs.t == os_.t and gs.cell_updates == os_.cell_updates
+    assert_fp64_parity(g, o, w)
+    g.close()
+
+
+def test_bench_workload_end_state_continues_like_the_oracle_fp32():
+    w = W.config("lorenz63_h0.25")
+    g, _ = run_to_end(w, gbees.GBEES_FP32)
+    o, st = oracle_from(g, w)
+    t_more = st.t + 0.02
+    g.propagate(t_more)
+    o.propagate(t_more)
+    _, l1, _, _, _, _ = compare(g, o, w.h)
+    assert l1 <= FP32_L1, l1
+    gm, gc = g.moments()
+    om, oc = o.moments()
+    assert np.abs(gm - om).max() <= FP32_MOM * np.abs(om).max()
+    assert np.abs(gc - oc).max() <= FP32_MOM * np.abs(oc).max()
+    g.close()
