@@ -9,6 +9,8 @@ the product library never does.
 
 `build()` compiles the C++ source with g++ into `oracle/_lib/`; `Oracle` wraps
 one grid. Every function named here maps one-to-one onto an `orc_*` symbol.
+`compile_variant()` builds a copy of the source with one text replacement (for
+the tests that plant a mistake in the oracle and check that a pin catches it).
 """
 from __future__ import annotations
 
@@ -70,10 +72,27 @@ def build(force: bool = False) -> str:
         return _LIB
 
 
+def compile_variant(old: str, new: str, out_path: str) -> str:
+    """Compile the oracle source with `old` (which must occur exactly once)
+    replaced by `new` into out_path; the flags are those of build()."""
+    src = open(_SRC).read()
+    if src.count(old) != 1:
+        raise ValueError(f"the text to replace occurs {src.count(old)} times")
+    tmp_src = out_path + ".cpp"
+    with open(tmp_src, "w") as f:
+        f.write(src.replace(old, new))
+    cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC",
+           tmp_src, "-o", out_path]
+    subprocess.run(cmd, check=True, capture_output=True)
+    return out_path
+
+
 def _lib():
     global _handle
     if _handle is None:
-        path = build()
+        # GBEES_ORACLE_LIB names another build of the oracle source: the
+        # mutation tests load copies with one planted mistake through it
+        path = os.environ.get("GBEES_ORACLE_LIB") or build()
         L = ctypes.CDLL(path)
         vp, d, i32, i64 = ctypes.c_void_p, ctypes.c_double, ctypes.c_int32, ctypes.c_int64
         P = ctypes.POINTER
