@@ -45,6 +45,33 @@ MUTANTS = [
     ("prune keeps the significant cells but not their downwind sets",
      "            for (auto& d : downwind(o, kv.first)) keep[d] = 1;\n",
      ""),
+    ("Lorenz '63: wrong sign of x2 in f2",
+     "if (j == 1) return x[0] * (a[1] - x[2]) - x[1];",
+     "if (j == 1) return x[0] * (a[1] - x[2]) + x[1];"),
+    ("shifted Lorenz '63: constant term b r replaced by r",
+     "return -a[1] * x[2] + x[0] * x[1] - a[1] * a[2];",
+     "return -a[1] * x[2] + x[0] * x[1] - a[2];"),
+    ("Lorenz '96: x_{j-1} in place of x_{j-2}",
+     "(x[(j + 1) % n] - x[(j + n - 2) % n])",
+     "(x[(j + 1) % n] - x[(j + n - 1) % n])"),
+    ("linear drift with A transposed",
+     "s += a[j * c.n + k] * x[k];",
+     "s += a[k * c.n + j] * x[k];"),
+    ("likelihood without the factor 1/2 (Eq. 4)",
+     "kv.second = std::exp(-0.5 * q) * kv.second;",
+     "kv.second = std::exp(-q) * kv.second;"),
+    ("likelihood residual against the wrong state component",
+     "r[a] = y[a] - centre(o, kv.first, H_idx[a]);",
+     "r[a] = y[a] - centre(o, kv.first, a);"),
+    ("initial set thresholded at a tenth of p*",
+     "if (g > pstar) o.P[i] = g;",
+     "if (g > 0.1 * pstar) o.P[i] = g;"),
+    ("cell volume taken as h_1^n",
+     "for (int j = 0; j < cfg->n; ++j) o->prod_h *= cfg->h[j];",
+     "for (int j = 0; j < cfg->n; ++j) o->prod_h *= cfg->h[0];"),
+    ("exact sum that ignores the sign of a term",
+     "int64_t sgn = x < 0 ? -1 : 1;",
+     "int64_t sgn = 1;"),
 ]
 
 
