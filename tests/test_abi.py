@@ -124,3 +124,15 @@ def test_batch_arguments_are_checked_before_any_launch(lib):
     assert f(ctxs, 2, dp, 0, ctypes.c_void_p(256), nb - 1, stats) == E             # scratch too small
     assert f(ctxs, 2, dp, 0, ctypes.c_void_p(256 + 8), nb, stats) == E             # misaligned scratch
     assert f(ctxs, 2, dp, 0, ctypes.c_void_p(256), nb, stats) == E                 # NULL contexts
+
+
+def test_a_missing_library_fails_loudly(tmp_path, monkeypatch):
+    """No CPU fallback: without the built CUDA library the binding raises, from
+    the loader and from any entry point."""
+    missing = str(tmp_path / "libgbees_gb300.so")
+    monkeypatch.setattr(gbees, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        gbees.load_library(missing)
+    monkeypatch.setattr(gbees.load_library, "__defaults__", (missing,))
+    with pytest.raises(RuntimeError, match="not built"):
+        gbees.gbees_batch_workspace_bytes(1)
