@@ -3,8 +3,11 @@ h = 0.25 workload (t_end 2, eight full-state measurements) runs through the
 library to its end as the bench runs it (launch mode AUTO, which picks the
 persistent step-loop kernel at this size; max_cells 2^22). The oracle cannot
 redo the whole run in a test's time, so it takes the GPU's end state as its
-initial cells and both continue for a further 0.02 time units (about a dozen
-steps, with a prune); the two must then agree at the bar of their precision."""
+initial cells and both continue for a further 0.02 time units (eight steps,
+one of them with a prune); the two must then agree at the bar of their
+precision. (The oracle run the same way from its own end state continues
+bit for bit like the oracle that never stopped: 2176 steps and 32,035,389 cell
+updates to t = 2, then 8 steps and 14,979 updates.)"""
 import numpy as np
 import pytest
 
