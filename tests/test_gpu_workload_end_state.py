@@ -7,7 +7,14 @@ initial cells and both continue for a further 0.02 time units (eight steps,
 one of them with a prune); the two must then agree at the bar of their
 precision. (The oracle run the same way from its own end state continues
 bit for bit like the oracle that never stopped: 2176 steps and 32,035,389 cell
-updates to t = 2, then 8 steps and 14,979 updates.)"""
+updates to t = 2, then 8 steps and 14,979 updates.)
+
+In FP64 the whole run must also take the oracle's steps and cell updates
+segment by segment, and keep its number of active cells after every
+measurement update (tests/golden/bench_workload_counts.txt, written by the
+oracle alone)."""
+import os
+
 import numpy as np
 import pytest
 
@@ -25,15 +32,28 @@ def built():
     ge.build()
 
 
+def golden_counts():
+    path = os.path.join(os.path.dirname(__file__), "golden", "bench_workload_counts.txt")
+    rows = []
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            t, s, u, n = line.split()
+            rows.append((float(t), int(s), int(u), int(n)))
+    return rows
+
+
 def run_to_end(w, precision):
+    """The workload through the library; per segment (target, steps, cell
+    updates, active cells after the measurement update)."""
     g = gbees.grid_for_workload(w, precision=precision, max_cells=1 << 22)
     g.init_gaussian(w.mean, w.cov)
-    updates = 0
+    rows = []
     for t, meas in w.segments():
-        updates += g.propagate(t).cell_updates
+        st = g.propagate(t)
         if meas is not None:
             g.correct_gaussian(meas.y, meas.R, meas.H_idx)
-    return g, updates
+        rows.append((t, st.steps, st.cell_updates, g.count()))
+    return g, rows
 
 
 def oracle_from(g, w):
@@ -46,8 +66,8 @@ def oracle_from(g, w):
 
 def test_bench_workload_end_state_continues_like_the_oracle_fp64():
     w = W.config("lorenz63_h0.25")
-    g, updates = run_to_end(w, gbees.GBEES_FP64)
-    assert updates > 2e7                          # the whole workload ran (3.2e7 cell updates)
+    g, rows = run_to_end(w, gbees.GBEES_FP64)
+    assert rows == golden_counts()                # the oracle's steps, updates and set sizes, segment by segment
     o, st = oracle_from(g, w)
     assert st.t == w.t_end
     t_more = st.t + 0.02
