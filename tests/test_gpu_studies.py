@@ -48,12 +48,27 @@ def table2():
     return vals
 
 
+def golden_rows(name):
+    import os
+
+    path = os.path.join(os.path.dirname(__file__), "golden", name)
+    rows = []
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            t, st, u, n = line.split()
+            rows.append((float(t), int(st), int(u), int(n)))
+    return rows
+
+
 @pytest.mark.gpu
-def test_paper_e1_burden_is_plausible_against_table_2():
-    """The paper's own Lorenz '63 case through the library: steps, largest grid
-    and cell updates within small factors of Table 2. They cannot match: the
-    paper does not state its threshold (this run uses 1e-7 of the maximum),
-    and its grid counts may exclude cells this method keeps."""
+def test_paper_e1_full_run_matches_the_oracle_and_is_plausible_against_table_2():
+    """The paper's own Lorenz '63 case through the library, FP64, read every
+    0.05: the oracle's steps, cell updates and active cells at every read
+    (tests/golden/paper_e1_counts.txt, written by the oracle alone), and
+    steps, largest grid and cell updates within small factors of Table 2.
+    Table 2 cannot be matched: the paper does not state its threshold (this
+    run uses 1e-7 of the maximum), and its grid counts may exclude cells this
+    method keeps."""
     import __graft_entry__ as ge
     from paper_2508_13986_gb300 import gbees
     from paper_2508_13986_gb300 import workloads as W
@@ -61,20 +76,22 @@ def test_paper_e1_burden_is_plausible_against_table_2():
     ge.build()
     ref = table2()
     w = W.paper_e1()
+    marks = {m.t: m for m in w.measurements}
     g = gbees.grid_for_workload(w, precision=gbees.GBEES_FP64, max_cells=1 << 20)
     g.init_gaussian(w.mean, w.cov)
-    steps = updates = peak = 0
-    marks = {m.t: m for m in w.measurements}
-    for k in range(1, 41):                      # 0.05 apart, to follow the grid's size
+    rows = []
+    for k in range(1, 41):
         t = 0.05 * k
         st = g.propagate(t)
-        steps += st.steps
-        updates += st.cell_updates
-        peak = max(peak, st.n_cells)
         m = marks.get(round(t, 12))
         if m is not None:
             g.correct_gaussian(m.y, m.R, m.H_idx)
+        rows.append((t, st.steps, st.cell_updates, g.count()))
     g.close()
+    assert rows == golden_rows("paper_e1_counts.txt")
+    steps = sum(r[1] for r in rows)
+    updates = sum(r[2] for r in rows)
+    peak = max(r[3] for r in rows)
     assert 0.5 <= steps / ref["integration_steps"] <= 2.0, steps
     assert 0.5 <= peak / ref["max_grid_size"] <= 4.0, peak
     assert 0.5 <= updates / ref["cell_computations"] <= 8.0, updates
