@@ -83,12 +83,14 @@ ReadOut = Tuple[np.ndarray, np.ndarray]
 def schedule(w: Workload, times: Optional[Sequence[float]] = None) -> List[Tuple[float, object, bool]]:
     """The targets of a run in time order: (t, measurement or None, read out
     here?). Without sample times the run reads out once, at t_end. A sample at
-    a measurement time is taken after the update. Sample times must lie in
-    [0, t_end]."""
+    a measurement time is taken after the update. Sample times must increase
+    strictly and lie in [0, t_end] (one read-out per sample time)."""
     marks: Dict[float, List[object]] = {}
     for t, meas in w.segments():
         marks.setdefault(float(t), [None, False])[0] = meas
     samples = [w.t_end] if times is None else [float(t) for t in times]
+    if any(b <= a for a, b in zip(samples, samples[1:])):
+        raise ValueError("sample times must increase strictly")
     for t in samples:
         if not 0.0 <= t <= w.t_end:
             raise ValueError(f"sample time {t} outside [0, {w.t_end}]")

@@ -148,6 +148,9 @@ def test_schedule_merges_sample_times_with_the_measurements():
     assert schedule(w) == [(0.1, m1, False), (0.2, m2, False), (0.3, None, True)]
     with pytest.raises(ValueError):
         schedule(w, [0.35])
+    for bad in ([0.2, 0.1], [0.1, 0.1]):
+        with pytest.raises(ValueError):
+            schedule(w, bad)
 
 
 def test_sampling_at_the_end_time_alone_is_the_plain_run():
