@@ -156,7 +156,7 @@ int gbees_init_gaussian(gbees_ctx* ctx, const double* mean, const double* cov, d
  * (the prune schedule counts from it; 0 for a new run). N may be 0. */
 int gbees_init_cells(gbees_ctx* ctx, const int32_t* idx, const double* p, int64_t N, double t0, int64_t step0);
 
-/* Propagate until t == t_end (the grow / step / prune loop of Fig. 1): each
+/* Propagate until t == t_end (the grow / step / prune loop of Sec. 3): each
  * step grows the downwind neighbours of the significant cells (Sec. 3.3),
  * takes dt = min(cfl / max_i sum_j |f_j(x_{i-e_j/2})| / h_j, t_end - t) over
  * the active cells (Eq. 8), applies the DCU flux (Eq. 7), the corner-transport

@@ -539,7 +539,8 @@ int orc_init_cells(void* h, const int32_t* idx, const double* p, int64_t N, doub
     return ORC_OK;
 }
 
-/* Propagate until t == t_end (Fig. 1 loop without measurements). */
+/* Propagate until t == t_end: steps of grow, dt (Eq. 8), flux update, prune
+ * (when due) and normalisation, without measurements. */
 int orc_propagate(void* h, double t_end, orc_stats* st) {
     Oracle& o = *(Oracle*)h;
     int64_t steps = 0, updates = 0;
