@@ -60,7 +60,8 @@ def parse():
     ap.add_argument("--no-secondary", action="store_true", help="skip the other precision's line")
     ap.add_argument("--cpu-budget", type=float, default=12.0,
                     help="seconds of oracle work for cpu_baseline (0: skip, for grids the oracle cannot initialise quickly)")
-    ap.add_argument("--max-cells", type=int, default=1 << 22)
+    ap.add_argument("--max-cells", type=int, default=0,
+                    help="pool capacity of a single-grid workload (0: sized from the workload, see auto_max_cells)")
     ap.add_argument("--launch-mode", choices=["auto", "persistent", "graph", "direct"], default="auto")
     ap.add_argument("--requests", type=int, default=100, help="requests of the serving stream (--workload serving)")
     ap.add_argument("--rate", type=float, default=50.0, help="arrival rate per second of the serving stream")
@@ -141,6 +142,28 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ runs
 
+def auto_max_cells(w, precision, dev) -> int:
+    """Pool capacity for a single-grid workload: 24 times its initial set
+    (growth measured up to 18x over the 6-D horizons, with the halo), a power
+    of two, at least 2^22, and halved while the workspace would take more than
+    80 % of the device memory."""
+    import torch
+
+    from paper_2508_13986_gb300 import gbees, workloads
+
+    cap = 1 << 22
+    while cap < 24 * workloads.initial_cells_estimate(w):
+        cap <<= 1
+    total = torch.cuda.get_device_properties(dev).total_memory
+    while cap > (1 << 22):
+        cfg = gbees.make_config(w.n, w.dynamics, w.params, w.h, w.x0, w.thr_rel, w.cfl, w.prune_interval, precision,
+                                w.limiter, cap)
+        if gbees.gbees_workspace_bytes(cfg) <= 0.8 * total:
+            break
+        cap >>= 1
+    return cap
+
+
 def run_workload(grid, w, with_readout=False):
     """One whole run through the public API. Returns (cell updates, steps, bytes in, bytes out, peak cells)."""
     grid.init_gaussian(w.mean, w.cov)
@@ -199,7 +222,8 @@ def time_precision(args, w, precision, dev, rank, world):
     prec = gbees.GBEES_FP64 if precision == "f64" else gbees.GBEES_FP32
     mode = {"auto": gbees.GBEES_LAUNCH_AUTO, "persistent": gbees.GBEES_LAUNCH_PERSISTENT,
             "graph": gbees.GBEES_LAUNCH_GRAPH, "direct": gbees.GBEES_LAUNCH_DIRECT}[args.launch_mode]
-    grid = gbees.grid_for_workload(w, precision=prec, max_cells=args.max_cells, device=f"cuda:{dev}",
+    max_cells = args.max_cells or auto_max_cells(w, prec, dev)
+    grid = gbees.grid_for_workload(w, precision=prec, max_cells=max_cells, device=f"cuda:{dev}",
                                    launch_mode=mode)
     stream = grid.stream
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=f"cuda:{dev}")
@@ -547,7 +571,11 @@ def main_ours(args):
         other_prec = "f32" if args.precision == "f64" else "f64"
         other = timer(other_prec)
     if rank == 0:
-        cpu = cpu_baseline(w, args.cpu_budget) if (world == 1 and args.cpu_budget > 0) else None
+        # the oracle builds its initial set by scanning a box cell by cell: beyond
+        # a few million initial cells that alone outlasts any bounded sample
+        too_big = workloads.initial_cells_estimate(w) > 2e6
+        cpu = (cpu_baseline(w, args.cpu_budget)
+               if (world == 1 and args.cpu_budget > 0 and not too_big) else None)
         line = {
             "metric": METRIC,
             "value": main["value"],
