@@ -83,6 +83,8 @@ __device__ __forceinline__ double gauss_at(const Model& m, const InitBox& bx, co
     return exp(__dmul_rn(-0.5, q));
 }
 
+// Initial Gaussian (Sec. 5.1), pass 1: the largest density over the box of
+// candidate cells, which fixes the threshold p* = thr_rel * max p.
 template <int N>
 __global__ void __launch_bounds__(THREADS) k_init_max(const Model m, Bufs b, const InitBox bx) {
     double mx = 0.0;
@@ -96,6 +98,8 @@ __global__ void __launch_bounds__(THREADS) k_init_max(const Model m, Bufs b, con
     if (threadIdx.x == 0 && mx > 0.0) atomicMax(&b.sc->tmp_ord, ord_key(mx));
 }
 
+// Initial Gaussian, pass 2: per-block counts of the box cells above p*, the
+// offsets of the write pass.
 template <int N>
 __global__ void __launch_bounds__(THREADS) k_init_count(const Model m, Bufs b, const InitBox bx) {
     long long c0, c1;
@@ -269,6 +273,9 @@ __global__ void __launch_bounds__(THREADS) k_grow_waves(const Model m, Bufs b) {
     grow_rates(sc, r);
 }
 
+// Flux update, pass 2: the flux through every face that touches an active
+// cell: donor cell (Eq. 7), the transverse terms of Algorithm 1 read from the
+// upwind cell's wave row, and the limited high-resolution term.
 template <int N, int DYN, typename T>
 __global__ void __launch_bounds__(THREADS) k_faces(const Model m, Bufs b) {
     DevScalars* sc = b.sc;
@@ -276,6 +283,9 @@ __global__ void __launch_bounds__(THREADS) k_faces(const Model m, Bufs b) {
     faces_body<N, DYN, T>(m, b, view_of(m, sc));
 }
 
+// Flux update, pass 3: the conservative update of every active cell from the
+// fluxes of its 2n faces, divided by the last normaliser; exact per-block
+// partial sums and maximum for the next one; the last block ends the step.
 template <int N, typename T>
 __global__ void __launch_bounds__(THREADS) k_apply(const Model m, Bufs b) {
     DevScalars* sc = b.sc;
@@ -346,24 +356,32 @@ __device__ __forceinline__ bool prune_due(const DevScalars* sc) {
     return *(volatile int*)&sc->prune_now && !*(volatile int*)&sc->error;
 }
 
+// Prune (Algorithm 3), pass 1: mark the significant cells S.
 template <typename T>
 __global__ void __launch_bounds__(THREADS) k_prune_mark(const Model m, Bufs b) {
     if (!prune_due(b.sc)) return;
     prune_mark_body<T>(m, b, view_of(m, b.sc));
 }
 
+// Prune, pass 2: mark the downwind set D(S) of every significant cell (the
+// directional rule of Sec. 3.3).
 template <int N, typename T>
 __global__ void __launch_bounds__(THREADS) k_prune_scatter(const Model m, Bufs b) {
     if (!prune_due(b.sc)) return;
     prune_scatter_body<N, T>(m, b, view_of(m, b.sc));
 }
 
+// Prune, pass 3: the status of every entry (active, halo or dropped) and the
+// per-block counts of the survivors.
 template <int N>
 __global__ void __launch_bounds__(THREADS) k_prune_count(const Model m, Bufs b) {
     if (!prune_due(b.sc)) return;
     prune_count_body<N>(m, b, view_of(m, b.sc));
 }
 
+// Prune, pass 4: write the survivors into the other buffer set in key order
+// (the permutation of the radix sort), active cells first, with exact partial
+// sums, maximum and CFL rates for the step scalars.
 template <int N, typename T>
 __global__ void __launch_bounds__(THREADS) k_prune_compact_sorted(const Model m, Bufs b) {
     DevScalars* sc = b.sc;
@@ -404,6 +422,8 @@ __device__ __forceinline__ void finish_prune(const Model& m, DevScalars* sc, con
     sc->ticket = 0;
 }
 
+// Prune, pass 5: rehash the survivors and rebuild their links (Sec. 4.4.2);
+// the last block swaps the buffer sets and sets the step scalars.
 template <int N>
 __global__ void __launch_bounds__(THREADS) k_prune_relink(const Model m, Bufs b, int nblk_compact) {
     DevScalars* sc = b.sc;

@@ -15,6 +15,7 @@ __global__ void k_begin(DevScalars* sc, double t_target) {
     sc->updates_call = 0;
 }
 
+// Normalisation scalars of a new grid (one thread).
 __global__ void k_finalise(const Model m, DevScalars* sc, int mode) { finalise_norm(m, sc, mode); }
 
 // Start a batched propagate call: k_begin for every grid of the batch.
@@ -61,6 +62,7 @@ __global__ void k_loop_ctl(DevScalars* sc, cudaGraphConditionalHandle h_while, c
     cudaGraphSetConditional(h_while, (!sc->done && !err && it < max_iter) ? 1u : 0u);
 }
 
+// Empty every hashtable slot.
 __global__ void k_table_clear(const Model m, Bufs b) {
     const unsigned long long T = m.tmask + 1;
     for (unsigned long long s = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; s < T;
@@ -143,6 +145,7 @@ __global__ void k_set_count_from_new(DevScalars* sc) {
     sc->n_act = 0;
 }
 
+// Counts and step number of a grid loaded from explicit cells.
 __global__ void k_set_count(DevScalars* sc, long long count, long long step0) {
     sc->N = count;
     sc->NA = count;
@@ -310,6 +313,7 @@ __global__ void __launch_bounds__(THREADS) k_readout_count(const Model m, Bufs b
     if (threadIdx.x == 0) b.blk[blockIdx.x] = t;
 }
 
+// Zero the exact accumulators of the moments.
 __global__ void k_moments_clear(DevScalars* sc) {
     for (int i = threadIdx.x; i < 28 * NDIG; i += blockDim.x) (&sc->mom[0][0])[i] = 0;
 }
