@@ -136,3 +136,23 @@ def test_a_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(gbees.load_library, "__defaults__", (missing,))
     with pytest.raises(RuntimeError, match="not built"):
         gbees.gbees_batch_workspace_bytes(1)
+
+
+def test_the_product_never_imports_or_includes_the_oracle():
+    """The library and its binding do not route through the oracle: no module
+    of the package imports it and no CUDA source includes anything of it."""
+    import ast
+    import glob
+
+    pkg = os.path.join(ROOT, "paper_2508_13986_gb300")
+    for path in glob.glob(os.path.join(pkg, "*.py")):
+        tree = ast.parse(open(path).read())
+        for node in ast.walk(tree):
+            if isinstance(node, ast.Import):
+                assert all(not a.name.startswith("oracle") for a in node.names), path
+            elif isinstance(node, ast.ImportFrom):
+                assert not (node.module or "").startswith("oracle"), path
+    for path in glob.glob(os.path.join(pkg, "csrc", "*")):
+        for line in open(path):
+            if line.lstrip().startswith("#include"):
+                assert "oracle" not in line, (path, line)
