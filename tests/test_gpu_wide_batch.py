@@ -44,3 +44,30 @@ def test_queue_mode_batch_equals_one_by_one_runs():
         a.close()
     for g in gs:
         g.close()
+
+
+def test_bench_batch_workload_grids_equal_their_one_by_one_runs():
+    """The bench's batched workload (256 ragged Lorenz '63 grids, FP32, the
+    bench's capacities and launch; end times capped at 0.25 to keep the test
+    short): sampled grids, the largest among them, end bit for bit as their
+    one-by-one runs."""
+    ws = [w.with_(t_end=min(w.t_end, 0.25)) for w in W.lorenz63_batch(count=256)]
+    gs = []
+    for w in ws:
+        g = gbees.grid_for_workload(w, precision=gbees.GBEES_FP32, max_cells=W.capacity_for(w))
+        g.init_gaussian(w.mean, w.cov)
+        gs.append(g)
+    n0 = [g.count() for g in gs]
+    st = gbees.propagate_batch(gs, [w.t_end for w in ws])
+    largest = int(np.argmax(n0))
+    for i in sorted({0, 97, 255, largest}):
+        a = gbees.grid_for_workload(ws[i], precision=gbees.GBEES_FP32, max_cells=W.capacity_for(ws[i]))
+        a.init_gaussian(ws[i].mean, ws[i].cov)
+        sa = a.propagate(ws[i].t_end)
+        assert sa.steps == st[i].steps and sa.t == st[i].t and sa.cell_updates == st[i].cell_updates
+        ia, pa = a.read_cells()
+        ib, pb = gs[i].read_cells()
+        assert np.array_equal(ia, ib) and np.array_equal(pa, pb)
+        a.close()
+    for g in gs:
+        g.close()
