@@ -221,7 +221,7 @@ enum {
     GBEES_PHASE_LINK = 2,    /* neighbour links of the new entries, CFL step (Sec. 4.1, Eq. 8) */
     GBEES_PHASE_FACES = 3,   /* face fluxes: DCU + CTU + high-resolution term (Eq. 7, Algorithm 1) */
     GBEES_PHASE_APPLY = 4,   /* conservative update, normalisation partials */
-    GBEES_PHASE_PRUNE = 5,   /* mark, status, key-order sort (graph and direct launch modes),
+    GBEES_PHASE_PRUNE = 5,   /* mark, status, Morton-order sort (graph and direct launch modes),
                                 compaction, relink and rehash (Algorithm 3) */
     GBEES_PHASE_CORRECT = 6, /* Bayesian update (Eq. 4) */
     GBEES_PHASE_OTHER = 7,   /* init, read-out, moments */

@@ -402,10 +402,11 @@ void launch_list(gbees_ctx* ctx, void* const* f, int nf) {
     for (int i = 0; i < nf; ++i) cudaLaunchKernel(f[i], dim3(ctx->grid), dim3(THREADS), args, 0, ctx->stream);
 }
 
-// The prune of Algorithm 3 (directional marking, status, key-order sort,
+// The prune of Algorithm 3 (directional marking, status, Morton-order sort,
 // compaction, relink, rehash). It runs only when the device flag prune_now is
-// set. The graph and direct paths put the survivors in key order (active cells
-// first), which keeps the neighbour rows of large grids close together.
+// set. The graph and direct paths put the survivors in Morton order of their
+// cell indices (active cells first), which keeps the neighbour rows of large
+// grids close together.
 constexpr int kSortPasses = 8;                          // 8-bit digits of the 64-bit sort key
 constexpr int kPruneKernels = 3 + 1 + 3 * kSortPasses + 1 + 2;
 

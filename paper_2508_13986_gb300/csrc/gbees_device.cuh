@@ -164,7 +164,7 @@ struct Bufs {
     DevScalars* sc;
     long long* blk;  // per-block counts (active cells)
     long long* blk2; // per-block counts (halo cells)
-    unsigned int* sorthist;  // digit histograms of the prune's key-order sort
+    unsigned int* sorthist;  // digit histograms of the prune's radix sort
     void* wv_u;  // update scratch in the storage type
     void* wv_g;
     void* fl;

@@ -379,8 +379,8 @@ __global__ void __launch_bounds__(THREADS) k_prune_count(const Model m, Bufs b) 
     prune_count_body<N>(m, b, view_of(m, b.sc));
 }
 
-// Prune, pass 4: write the survivors into the other buffer set in key order
-// (the permutation of the radix sort), active cells first, with exact partial
+// Prune, pass 4: write the survivors into the other buffer set in the order
+// of the radix sort (Morton order of the cell indices), active cells first, with exact partial
 // sums, maximum and CFL rates for the step scalars.
 template <int N, typename T>
 __global__ void __launch_bounds__(THREADS) k_prune_compact_sorted(const Model m, Bufs b) {

@@ -42,6 +42,18 @@ GBEES_HD void unpack_key_bits(int b, unsigned long long k, int* I) {
     }
 }
 
+// Morton (Z-order) code of a packed key of n fields of b bits: the bits of
+// the n indices interleaved, from the most significant bit of every field
+// down, dimension 0 first within each bit. A bijection of the n*b-bit keys
+// that keeps cells near one another in all n dimensions near one another in
+// code order (key order keeps them near only along the last dimension).
+GBEES_HD unsigned long long morton_code(unsigned long long k, int n, int b) {
+    unsigned long long out = 0;
+    for (int bit = b - 1; bit >= 0; --bit)
+        for (int j = 0; j < n; ++j) out = (out << 1) | ((k >> ((n - 1 - j) * b + bit)) & 1ull);
+    return out;
+}
+
 // murmur3 64-bit finaliser (a bijection of u64); the table slot of a key is
 // mix64(key) & (slots - 1)
 GBEES_HD unsigned long long mix64(unsigned long long x) {

@@ -154,11 +154,12 @@ __global__ void k_set_count(DevScalars* sc, long long count, long long step0) {
     sc->step = step0;
 }
 
-// ------------------------------------------------------------------ key order at a prune
-// The graph and direct paths give the survivors of a prune their key order
-// (active cells first, then the halo; each in key order) with a stable LSD
-// radix sort of (region bit | key, old index), 8 bits per pass, so that the
-// neighbour rows a sweep reads are mostly near each other (L2 hits). Scratch:
+// ------------------------------------------------------------------ storage order at a prune
+// The graph and direct paths give the survivors of a prune a new storage
+// order (active cells first, then the halo; each in Morton order of the cell
+// indices) with a stable LSD radix sort of (region bit | code, old index), 8
+// bits per pass, so that the neighbour rows a sweep reads are mostly near each
+// other (L2 hits). Scratch:
 // the other generation's key/slot arrays (A), its link/value arrays (B), the
 // velocity scratch (histograms), all free until the compaction writes them.
 
@@ -179,7 +180,12 @@ __device__ __forceinline__ SortBufs sort_bufs(const Bufs& b, const StepView& v) 
 }
 
 // keep[c] = status (0 drop, 1 active, 2 halo, from the status pass in map);
-// A = (sort key, c): dropped entries last, halo cells after the active ones.
+// A = (sort key, c): dropped entries last, halo cells after the active ones,
+// each group in Morton order of the cell indices, so that a cell's face
+// neighbours tend to lie near it in the pool (the order affects speed only:
+// every result is independent of the storage order). A live entry's code is
+// below 2^63: only an all-ones key has an all-ones code, and no cell that
+// survives a prune has that key.
 __global__ void __launch_bounds__(THREADS) k_sort_init(const Model m, Bufs b) {
     if (!prune_due(b.sc)) return;
     const StepView v = view_of(m, b.sc);
@@ -190,7 +196,7 @@ __global__ void __launch_bounds__(THREADS) k_sort_init(const Model m, Bufs b) {
     for (long long c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
         const int st = b.map[c];
         b.keep[c] = (unsigned char)st;
-        sb.key[0][c] = st == 0 ? ~0ull : ((st == 2 ? (1ull << 63) : 0ull) | key[c]);
+        sb.key[0][c] = st == 0 ? ~0ull : ((st == 2 ? (1ull << 63) : 0ull) | morton_code(key[c], m.n, m.key_bits));
         sb.val[0][c] = (unsigned int)c;
     }
 }

@@ -843,7 +843,7 @@ __device__ __forceinline__ void prune_compact_body(const Model& m, const Bufs& b
 }
 
 // The compaction of the graph and direct paths: every survivor goes to the
-// place map[c] that the key-order sort gave it (status in keep); the same
+// place map[c] that the prune's sort gave it (status in keep); the same
 // values, rescaling and partials as prune_compact_body.
 template <int N, typename T>
 __device__ __forceinline__ void prune_compact_sorted_body(const Model& m, const Bufs& b, const StepView& v,

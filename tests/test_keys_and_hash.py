@@ -1,9 +1,11 @@
-"""The CUDA path's cell keys and table hash (csrc/gbees_keys.cuh), built for
-the host: the packing round trip and its range, key order = lexicographic
-order of the index vectors (what the key-order sort and the sorted read-out
-rely on), the hash as a bijection of u64, and the probe lengths of linear
-probing with this hash on the workloads' cell sets against Knuth's expected
-values for a random hash (Sec. 4.2 sizes the table for load factor 1/2)."""
+"""The CUDA path's cell keys, table hash and Morton code (csrc/gbees_keys.cuh),
+built for the host: the packing round trip and its range, key order =
+lexicographic order of the index vectors, the Morton code as a bijection that
+traces the Z curve and keeps face neighbours closer than key order (the order
+the prune's sort gives the pool), the hash as a bijection of u64, and the
+probe lengths of linear probing with this hash on the workloads' cell sets
+against Knuth's expected values for a random hash (Sec. 4.2 sizes the table
+for load factor 1/2)."""
 import ctypes
 import itertools
 import os
@@ -26,6 +28,7 @@ def lib(tmp_path_factory):
                             ctypes.c_void_p]
     L.keys_unpack.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
     L.keys_mix.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
+    L.keys_morton.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
     L.probe_lengths.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int,
                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     L.probe_lengths.restype = ctypes.c_longlong
@@ -89,6 +92,65 @@ def test_key_order_is_lexicographic_order(lib, n):
     by_key = np.argsort(keys, kind="stable")
     lex = np.lexsort(idx.T[::-1])                 # dimension 0 most significant
     assert np.array_equal(idx[by_key], idx[lex])
+
+
+def morton(lib, keys, n, b):
+    keys = np.ascontiguousarray(keys, dtype=U64)
+    out = np.zeros_like(keys)
+    lib.keys_morton(keys.ctypes.data, keys.shape[0], n, b, out.ctypes.data)
+    return out
+
+
+def test_morton_order_of_a_4x4_grid_is_the_z_curve(lib):
+    """Worked example: the 16 cells of a 4 x 4 grid (2 bits per field,
+    dimension 0 the major bit) in code order trace the Z curve quadrant by
+    quadrant."""
+    cells = [(x, y) for x in range(4) for y in range(4)]
+    keys = np.array([(x << 2) | y for x, y in cells], dtype=U64)
+    codes = morton(lib, keys, 2, 2)
+    got = [cells[i] for i in np.argsort(codes)]
+    assert got == [(0, 0), (0, 1), (1, 0), (1, 1), (0, 2), (0, 3), (1, 2), (1, 3),
+                   (2, 0), (2, 1), (3, 0), (3, 1), (2, 2), (2, 3), (3, 2), (3, 3)]
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 6])
+def test_morton_code_is_a_bijection_of_the_keys(lib, n):
+    """Distinct keys get distinct codes within n*b bits; all-ones maps to
+    all-ones (the prune's sort relies on codes below 2^63 for live entries,
+    and only an all-ones key reaches the top)."""
+    b = key_bits(n)
+    rng = np.random.default_rng(90 + n)
+    keys = np.unique(rng.integers(0, 1 << (n * b), size=20000, dtype=np.uint64, endpoint=False))
+    codes = morton(lib, keys, n, b)
+    assert np.unique(codes).size == keys.size
+    assert int(codes.max()) < (1 << (n * b))
+    ones = np.array([(1 << (n * b)) - 1, 0], dtype=U64)
+    assert [int(c) for c in morton(lib, ones, n, b)] == [(1 << (n * b)) - 1, 0]
+    if n == 1:
+        assert np.array_equal(codes, keys)                      # one field: the key itself
+
+
+def test_morton_order_keeps_face_neighbours_closer_than_key_order(lib):
+    """On the 6-D initial set with its halo, the median distance in sort order
+    from a cell to its face neighbours is smaller in code order."""
+    idx = ellipsoid_cells(6, 1.0, 1e-6)
+    pool = np.concatenate([idx, face_halo(idx)])
+    keys, ok = pack(lib, pool)
+    assert ok.all()
+    med = {}
+    for name, sort_key in (("key", keys), ("morton", morton(lib, keys, 6, key_bits(6)))):
+        rank = np.empty(keys.size, dtype=np.int64)
+        rank[np.argsort(sort_key, kind="stable")] = np.arange(keys.size)
+        by_key = dict(zip(keys.tolist(), rank.tolist()))
+        d = []
+        for j in range(6):
+            for s_ in (-1, 1):
+                nb = idx.copy()
+                nb[:, j] += s_
+                nk, _ = pack(lib, nb)
+                d.extend(abs(by_key[k] - by_key[c]) for k, c in zip(nk.tolist(), keys[: idx.shape[0]].tolist()))
+        med[name] = float(np.median(d))
+    assert med["morton"] < 0.5 * med["key"], med
 
 
 def unmix(y):
