@@ -156,3 +156,37 @@ def test_the_product_never_imports_or_includes_the_oracle():
         for line in open(path):
             if line.lstrip().startswith("#include"):
                 assert "oracle" not in line, (path, line)
+
+
+C_CALLER = r"""
+#include <stdio.h>
+#include "gbees.h"
+int main(void) {
+    gbees_config c = {0};
+    c.n = 3; c.dynamics = GBEES_DYN_LORENZ63;
+    c.params[0] = 10; c.params[1] = 28; c.params[2] = 8.0 / 3.0;
+    for (int j = 0; j < 3; ++j) c.h[j] = 0.5;
+    c.thr_rel = 1e-7; c.cfl = 0.9; c.prune_interval = 20; c.max_cells = 1000;
+    size_t b = gbees_workspace_bytes(&c);
+    gbees_ctx* ctx = 0;
+    int rc = gbees_create(&c, 0, b, 0, &ctx);   /* no workspace: refused before any CUDA call */
+    printf("%zu %d %d\n", b, rc, gbees_get_status(0));
+    return !(b > 0 && rc == GBEES_EINVAL && ctx == 0 && gbees_get_status(0) == GBEES_EINVAL);
+}
+"""
+
+
+def test_the_header_is_c99_and_a_c_program_links_the_library(lib, tmp_path):
+    """The boundary is a C ABI: gbees.h compiles as strict C99 and a plain C
+    caller links the library and makes host-only calls."""
+    inc = os.path.join(ROOT, "include")
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only", "-x", "c",
+                    os.path.join(inc, "gbees.h")], check=True)
+    src = tmp_path / "caller.c"
+    src.write_text(C_CALLER)
+    exe = tmp_path / "caller"
+    libdir = os.path.dirname(LIB)
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", inc, str(src), "-L", libdir, "-lgbees_gb300",
+                    f"-Wl,-rpath,{libdir}", "-o", str(exe)], check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stdout + r.stderr
