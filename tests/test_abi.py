@@ -190,3 +190,27 @@ def test_the_header_is_c99_and_a_c_program_links_the_library(lib, tmp_path):
                     f"-Wl,-rpath,{libdir}", "-o", str(exe)], check=True)
     r = subprocess.run([str(exe)], capture_output=True, text=True)
     assert r.returncode == 0, r.stdout + r.stderr
+
+
+def test_binding_structs_match_the_c_layout(tmp_path):
+    """sizeof and offsetof of every field of gbees_config, gbees_stats and
+    gbees_profile, from a C compile of gbees.h, equal the ctypes layouts of
+    the binding."""
+    structs = {"gbees_config": gbees.gbees_config, "gbees_stats": gbees.gbees_stats,
+               "gbees_profile": gbees.gbees_profile}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "gbees.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'    printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'    printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    c_layout = {tuple(ln.split()[:2]): int(ln.split()[2]) for ln in out if ln.strip()}
+    for name, cls in structs.items():
+        assert c_layout[(name, "size")] == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert c_layout[(name, field)] == getattr(cls, field).offset, (name, field)
