@@ -650,6 +650,23 @@ def test_first_order_mass_loss_per_step_is_small_and_never_a_gain():
             assert 0.0 <= 1.0 - mass() < 1e-6
     assert o.read_cells()[1].min() >= 0.0
 
+
+@pytest.mark.parametrize("lim", [LIM_MC, LIM_NONE])
+def test_zero_drift_takes_one_step_to_the_target_and_keeps_the_density(lim):
+    """Degenerate case of Eq. 8: with f = 0 every CFL rate is zero, so one step
+    reaches the target (R2); no face carries flux, grow adds no cell, and the
+    density is unchanged (to the rounding of the normalisation)."""
+    idx, p = W.random_cells(3, 300, 4, seed=64)
+    p = p / (0.125 * p.sum())
+    o = const_oracle([0.0, 0.0, 0.0], [0.5, 0.5, 0.5], limiter=lim, K=1)
+    o.init_cells(idx, p)
+    st = o.propagate(0.7)
+    assert st.steps == 1 and o.t == 0.7 and st.last_dt == 0.7
+    gi, gp = o.read_cells()
+    order = np.lexsort(idx.T[::-1])
+    assert np.array_equal(gi, idx[order])
+    np.testing.assert_allclose(gp, p[order], rtol=1e-15, atol=0)
+
 # ---------------------------------------------------------------- symmetries of the whole step
 
 def _run_const(idx, p, c, h, limiter, t_end, K=3):
