@@ -15,7 +15,7 @@ import pytest
 import scipy.linalg
 
 from oracle.oracle import (DYN_CONSTANT, DYN_LINEAR, DYN_LORENZ63, DYN_LORENZ63_SHIFTED, DYN_LORENZ96,
-                           LIM_LW, LIM_MC, LIM_NONE, Oracle, exact_sum)
+                           LIM_LW, LIM_MC, LIM_NONE, Oracle, OracleError, exact_sum)
 from paper_2508_13986_gb300 import workloads as W
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -666,6 +666,16 @@ def test_zero_drift_takes_one_step_to_the_target_and_keeps_the_density(lim):
     order = np.lexsort(idx.T[::-1])
     assert np.array_equal(gi, idx[order])
     np.testing.assert_allclose(gp, p[order], rtol=1e-15, atol=0)
+
+
+def test_a_measurement_with_no_weight_is_degenerate():
+    """C = 0 in Eq. 4 (the likelihood underflows at every cell) is an error, not
+    a division by zero."""
+    w = W.config("lorenz63_h0.5")
+    o = Oracle(w.n, w.dynamics, w.params, w.h, w.x0, w.thr_rel, w.cfl, w.prune_interval, w.limiter)
+    o.init_gaussian(w.mean, w.cov)
+    with pytest.raises(OracleError):
+        o.correct_gaussian(np.array([1e6, 1e6, 1e6]), 0.25 * np.eye(3), np.arange(3, dtype=np.int32))
 
 # ---------------------------------------------------------------- symmetries of the whole step
 
