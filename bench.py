@@ -44,6 +44,15 @@ TRAFFIC_BYTES_PER_CELL = {
     # 9.268 MB read + 1.092 MB written
     "lorenz63_h0.25/f64": {"bytes_per_cell": 10.360832e6 / 2118979, "src": "c00cd41fc877901a"},
 }
+# The paper's own throughput on its two cases, in this benchmark's unit (cells
+# per second, total cell computations over the runtime): the fastest GPU row of
+# its Lorenz '63 table (Table 3, H100) and of its Lorenz '96 table (Table 4,
+# H200). vs_baseline divides by them on those workloads only; another machine's
+# number, context rather than a target.
+PAPER_CELLS_PER_S = {
+    "paper_e1": (28.8e6, "Table 3, NVIDIA H100: 226 ms, 28.8 M cells/s"),
+    "paper_e2": (40.6e6, "Table 4, NVIDIA H200: 739 s, 40.6 M cells/s"),
+}
 DEVICE_SOURCES = [os.path.join(ROOT, "paper_2508_13986_gb300", "csrc", f)
                   for f in ("gbees_keys.cuh", "gbees_device.cuh", "gbees_phases.cuh", "gbees_kernels.cuh",
                             "gbees_misc_kernels.cuh", "gbees_persistent.cuh")]
@@ -586,7 +595,8 @@ def main_ours(args):
             "ms_per_step": main["ms_per_step"],
             "higher_is_better": True,
             "scaling": "weak",
-            "vs_baseline": None,
+            "vs_baseline": (main["value"] / PAPER_CELLS_PER_S[args.workload][0]
+                            if args.workload in PAPER_CELLS_PER_S else None),
             "dtype": args.precision,
             "data": "synthetic",
             "config": {"workload": args.workload, **cfg_extra, "parallelism": f"replicas{world}",
@@ -596,7 +606,9 @@ def main_ours(args):
                        "cell_updates_per_step": main["updates_per_step"],
                        "time_steps_per_run": main["time_steps_per_run"],
                        "time_steps_per_s": main["time_steps_per_s"],
-                       "peak_cells": main["peak_cells"]},
+                       "peak_cells": main["peak_cells"],
+                       **({"paper_baseline": PAPER_CELLS_PER_S[args.workload][1]}
+                          if args.workload in PAPER_CELLS_PER_S else {})},
             "e2e": main["e2e"],
             "roofline": main["roofline"],
             "cpu_baseline": cpu,
