@@ -1,7 +1,7 @@
 /*
  * GBEES oracle -- TEST INFRASTRUCTURE ONLY.
  *
- * A plain, slow, single-threaded FP64 CPU implementation of the per-step
+ * A plain, slow FP64 CPU implementation of the per-step
  * propagation of a probability density on a sparse Cartesian grid, as
  * described in "GBEES-GPU: An efficient parallel GPU algorithm for
  * high-dimensional nonlinear uncertainty propagation" (Hanson, Rubio,
@@ -59,6 +59,15 @@
  *   - The grid origin x0 is part of the configuration; cell i has centre
  *     x0 + i * h and its lower face in dimension j sits at x0_j + (i_j - 1/2) h_j.
  *
+ * Threads: loops over cells and faces may run in parallel (OpenMP, when the
+ * library is built with it). Each parallel iteration writes only its own slot,
+ * maxima are order-free, the exact sums are merged digit by digit, and every
+ * floating-point sum whose rounding depends on its order is accumulated in
+ * the order of the single-threaded program (the transverse corrections of one
+ * flux array by one thread, in the order of the faces that emit them; cells
+ * and faces are inserted into the maps in the same order). The results are
+ * therefore the same for any number of threads.
+ *
  * Compile with -ffp-contract=off so that no multiply-add is fused.
  */
 #include <algorithm>
@@ -68,7 +77,12 @@
 #include <cstring>
 #include <string>
 #include <unordered_map>
+#include <unordered_set>
 #include <vector>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 namespace {
 
@@ -144,6 +158,11 @@ struct ExactSum {
         for (int q = 0; q < 3 && k + q < NDIG; ++q) {
             d[k + q] += sgn * (int64_t)(uint32_t)(v >> (32 * q));
         }
+    }
+
+    /* add another exact sum (digit by digit: exact, in any order) */
+    void merge(const ExactSum& o) {
+        for (int q = 0; q < NDIG; ++q) d[q] += o.d[q];
     }
 
     double value() const {
@@ -254,9 +273,26 @@ inline double get(const Field& P, const Idx& X) {
     return it == P.end() ? 0.0 : it->second;
 }
 
+/* The cells of P in its iteration order (for loops that run in parallel). */
+std::vector<std::pair<const Idx, double>*> cell_list(Field& P) {
+    std::vector<std::pair<const Idx, double>*> v;
+    v.reserve(P.size());
+    for (auto& kv : P) v.push_back(&kv);
+    return v;
+}
+std::vector<const std::pair<const Idx, double>*> cell_list(const Field& P) {
+    std::vector<const std::pair<const Idx, double>*> v;
+    v.reserve(P.size());
+    for (auto& kv : P) v.push_back(&kv);
+    return v;
+}
+
 double max_p(const Field& P) {
+    const auto cells = cell_list(P);
+    const int64_t N = (int64_t)cells.size();
     double m = -INFINITY;
-    for (auto& kv : P) m = std::max(m, kv.second);
+#pragma omp parallel for reduction(max : m) schedule(static)
+    for (int64_t i = 0; i < N; ++i) m = std::max(m, cells[i]->second);
     return m;
 }
 
@@ -276,24 +312,37 @@ std::vector<Idx> downwind(const Oracle& o, const Idx& i) {
     return d;
 }
 
-/* Grow: insert D(S) with p = 0, S = {p > thr_rel max p}. */
+/* Grow: insert D(S) with p = 0, S = {p > thr_rel max p}. The downwind sets
+ * are found in parallel; the cells missing from the grid are inserted in the
+ * order of the significant cells that name them. */
 void grow(Oracle& o) {
     double pstar = o.c.thr_rel * max_p(o.P);
-    std::vector<Idx> add;
-    for (auto& kv : o.P)
-        if (kv.second > pstar)
-            for (auto& d : downwind(o, kv.first)) add.push_back(d);
-    for (auto& d : add) o.P.emplace(d, 0.0);
+    const auto cells = cell_list(o.P);
+    const int64_t N = (int64_t)cells.size();
+    std::vector<std::vector<Idx>> add(N);
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t i = 0; i < N; ++i)
+        if (cells[i]->second > pstar)
+            for (auto& d : downwind(o, cells[i]->first))
+                if (!o.P.count(d)) add[i].push_back(d);
+    for (int64_t i = 0; i < N; ++i)
+        for (auto& d : add[i]) o.P.emplace(d, 0.0);
 }
 
 /* Prune (Algorithm 3 with the directional rule of Sec. 3.3): keep S u D(S). */
 void prune(Oracle& o) {
     double pstar = o.c.thr_rel * max_p(o.P);
-    std::unordered_map<Idx, char, IdxHash> keep;
-    for (auto& kv : o.P)
-        if (kv.second > pstar) {
-            keep[kv.first] = 1;
-            for (auto& d : downwind(o, kv.first)) keep[d] = 1;
+    const auto cells = cell_list(o.P);
+    const int64_t N = (int64_t)cells.size();
+    std::vector<std::vector<Idx>> down(N);
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t i = 0; i < N; ++i)
+        if (cells[i]->second > pstar) down[i] = downwind(o, cells[i]->first);
+    std::unordered_set<Idx, IdxHash> keep;
+    for (int64_t i = 0; i < N; ++i)
+        if (cells[i]->second > pstar) {
+            keep.insert(cells[i]->first);
+            for (auto& d : down[i]) keep.insert(d);
         }
     for (auto it = o.P.begin(); it != o.P.end();) {
         if (keep.count(it->first)) ++it;
@@ -308,11 +357,35 @@ double cfl_rate(const Oracle& o, const Idx& i) {
     return r;
 }
 
+/* max_i of the CFL rates over the grid (order-free). */
+double max_rate(const Oracle& o) {
+    const auto cells = cell_list(o.P);
+    const int64_t N = (int64_t)cells.size();
+    double r = 0.0;
+#pragma omp parallel for reduction(max : r) schedule(static)
+    for (int64_t i = 0; i < N; ++i) r = std::max(r, cfl_rate(o, cells[i]->first));
+    return r;
+}
+
 double limiter(int kind, double theta) {
     if (kind == LIM_NONE) return 0.0;
     if (kind == LIM_LW) return 1.0;
     return std::max(0.0, std::min(std::min((1.0 + theta) / 2.0, 2.0), 2.0 * theta)); /* MC */
 }
+
+/* The faces of one dimension j that touch an active cell: the lower j-face of
+ * every active cell X and of X + e_j, numbered in order of first appearance,
+ * with the velocity through each face, the jump of P across it and the flux
+ * being assembled. */
+struct FaceSet {
+    std::vector<Idx> X;                           /* face k is the lower j-face of cell X[k] */
+    std::unordered_map<Idx, int64_t, IdxHash> at; /* X[k] -> k */
+    std::vector<double> u, W, F;                  /* f_j on the face, P_X - P_{X-e_j}, flux */
+    int64_t find(const Idx& Y) const {
+        auto it = at.find(Y);
+        return it == at.end() ? -1 : it->second;
+    }
+};
 
 /* One DCU + CTU + high-resolution update of every active cell with time step
  * dt (Eq. 7, Algorithm 1, Sec. 2.1). Returns the new values of the active
@@ -320,72 +393,114 @@ double limiter(int kind, double theta) {
 Field ctu_update(const Oracle& o, const Field& P, double dt) {
     const int n = o.c.n;
     const double* h = o.c.h;
-    /* F[j][X] = flux through the lower face of X in dimension j */
-    std::vector<Field> F(n);
-    std::vector<std::vector<Idx>> faces(n);
+    const auto cells = cell_list(P);
+    const int64_t N = (int64_t)cells.size();
+    std::vector<FaceSet> fs(n);
+#pragma omp parallel for schedule(static, 1)
     for (int j = 0; j < n; ++j) {
-        F[j].reserve(2 * P.size());
-        for (auto& kv : P) {
+        FaceSet& f = fs[j];
+        f.at.reserve(2 * N);
+        for (int64_t i = 0; i < N; ++i)
             for (int s = 0; s < 2; ++s) {
-                Idx X = shifted(kv.first, j, s);
-                if (F[j].emplace(X, 0.0).second) faces[j].push_back(X);
+                Idx X = shifted(cells[i]->first, j, s);
+                if (f.at.emplace(X, (int64_t)f.X.size()).second) f.X.push_back(X);
+            }
+        f.u.resize(f.X.size());
+        f.W.resize(f.X.size());
+        f.F.resize(f.X.size());
+    }
+    /* Eq. 7: donor cell upwind, with the face velocity and the jump kept */
+    for (int j = 0; j < n; ++j) {
+        FaceSet& f = fs[j];
+        const int64_t M = (int64_t)f.X.size();
+#pragma omp parallel for schedule(static)
+        for (int64_t k = 0; k < M; ++k) {
+            const Idx& X = f.X[k];
+            const double u = face_velocity(o, X, j);
+            const double Pl = get(P, shifted(X, j, -1)), Pr = get(P, X);
+            f.u[k] = u;
+            f.W[k] = Pr - Pl;
+            f.F[k] = std::max(u, 0.0) * Pl + std::min(u, 0.0) * Pr;
+        }
+    }
+    /* Algorithm 1, restated per wave: the jump W across the lower j-face of X
+     * crosses that face in the direction of its velocity u, into the cell Y = X
+     * (u > 0) or Y = X - e_j (u < 0). Inside Y the transverse velocity of
+     * dimension l != j carries it on, through the upper l-face of Y where the
+     * velocity there is positive and through the lower l-face of Y where it is
+     * negative; each such flux loses u v dt / (2 h_j) W. One thread owns the
+     * flux array of each dimension l and adds the waves in the order of the
+     * emitting faces (j, then k). */
+#pragma omp parallel for schedule(static, 1)
+    for (int l = 0; l < n; ++l) {
+        FaceSet& T = fs[l];
+        for (int j = 0; j < n; ++j) {
+            if (j == l) continue;
+            const FaceSet& f = fs[j];
+            for (size_t k = 0; k < f.X.size(); ++k) {
+                const double u = f.u[k];
+                if (u == 0.0) continue;
+                const Idx Y = u > 0.0 ? f.X[k] : shifted(f.X[k], j, -1);
+                const double Fstar = dt / (2.0 * h[j]) * f.W[k];
+                const Idx Yup = shifted(Y, l, +1);
+                const int64_t a = T.find(Yup), b = T.find(Y);
+                if (a >= 0) T.F[a] -= u * std::max(face_velocity(o, Yup, l), 0.0) * Fstar;
+                if (b >= 0) T.F[b] -= u * std::min(face_velocity(o, Y, l), 0.0) * Fstar;
             }
         }
     }
-    /* Eq. 7: donor cell upwind */
-    for (int j = 0; j < n; ++j)
-        for (auto& X : faces[j]) {
-            double u = face_velocity(o, X, j);
-            F[j][X] = std::max(u, 0.0) * get(P, shifted(X, j, -1)) + std::min(u, 0.0) * get(P, X);
-        }
-    /* Algorithm 1: the wave at the lower j-face of cell i = X is carried
-     * across the l-faces of i (when f_j > 0) or of i - e_j (when f_j < 0). */
-    for (int j = 0; j < n; ++j)
-        for (auto& X : faces[j]) {
-            double Fstar = dt / (2.0 * h[j]) * (get(P, X) - get(P, shifted(X, j, -1)));
-            double uj = face_velocity(o, X, j);
-            double ujp = std::max(uj, 0.0), ujm = std::min(uj, 0.0);
-            Idx Xm = shifted(X, j, -1);
-            for (int l = 0; l < n; ++l) {
-                if (l == j) continue;
-                Idx a = shifted(X, l, +1), b = X, c = shifted(Xm, l, +1), d = Xm;
-                F[l][a] -= ujp * std::max(face_velocity(o, a, l), 0.0) * Fstar;
-                F[l][b] -= ujp * std::min(face_velocity(o, b, l), 0.0) * Fstar;
-                F[l][c] -= ujm * std::max(face_velocity(o, c, l), 0.0) * Fstar;
-                F[l][d] -= ujm * std::min(face_velocity(o, d, l), 0.0) * Fstar;
-            }
-        }
     /* High-resolution correction with a limited wave */
     if (o.c.limiter != LIM_NONE)
-        for (int j = 0; j < n; ++j)
-            for (auto& X : faces[j]) {
-                double W = get(P, X) - get(P, shifted(X, j, -1));
+        for (int j = 0; j < n; ++j) {
+            FaceSet& f = fs[j];
+            const int64_t M = (int64_t)f.X.size();
+#pragma omp parallel for schedule(static)
+            for (int64_t k = 0; k < M; ++k) {
+                const Idx& X = f.X[k];
+                double W = f.W[k];
                 if (W == 0.0) continue;
-                double u = face_velocity(o, X, j);
+                double u = f.u[k];
                 double Wup = u > 0.0 ? get(P, shifted(X, j, -1)) - get(P, shifted(X, j, -2))
                                      : get(P, shifted(X, j, +1)) - get(P, X);
                 double theta = Wup / W;
                 double au = std::fabs(u);
-                F[j][X] += 0.5 * au * (1.0 - dt * au / h[j]) * limiter(o.c.limiter, theta) * W;
+                f.F[k] += 0.5 * au * (1.0 - dt * au / h[j]) * limiter(o.c.limiter, theta) * W;
             }
+        }
     /* conservative update of the active cells */
-    Field out;
-    out.reserve(P.size());
-    for (auto& kv : P) {
+    std::vector<double> val(N);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < N; ++i) {
+        const Idx& X = cells[i]->first;
         double acc = 0.0;
         for (int j = 0; j < n; ++j)
-            acc += dt / h[j] * (F[j][shifted(kv.first, j, +1)] - F[j][kv.first]);
-        out.emplace(kv.first, kv.second - acc);
+            acc += dt / h[j] * (fs[j].F[fs[j].find(shifted(X, j, +1))] - fs[j].F[fs[j].find(X)]);
+        val[i] = cells[i]->second - acc;
     }
+    Field out;
+    out.reserve(P.size());
+    for (int64_t i = 0; i < N; ++i) out.emplace(cells[i]->first, val[i]);
     return out;
 }
 
-/* (prod h) * sum p, summed exactly */
-double mass(const Oracle& o) {
-    ExactSum s;
-    for (auto& kv : o.P) s.add(kv.second);
-    return o.prod_h * s.value();
+/* Exact sum of the stored values (per-thread partial sums, merged exactly). */
+ExactSum exact_total(const Field& P) {
+    const auto cells = cell_list(P);
+    const int64_t N = (int64_t)cells.size();
+    ExactSum total;
+#pragma omp parallel
+    {
+        ExactSum part;
+#pragma omp for schedule(static)
+        for (int64_t i = 0; i < N; ++i) part.add(cells[i]->second);
+#pragma omp critical
+        total.merge(part);
+    }
+    return total;
 }
+
+/* (prod h) * sum p, summed exactly */
+double mass(const Oracle& o) { return o.prod_h * exact_total(o.P).value(); }
 
 /* p <- p / ((prod h) sum p) */
 int normalise(Oracle& o) {
@@ -394,7 +509,10 @@ int normalise(Oracle& o) {
         o.err = "degenerate: total probability is not positive";
         return ORC_EDEGENERATE;
     }
-    for (auto& kv : o.P) kv.second = kv.second / w;
+    const auto cells = cell_list(o.P);
+    const int64_t N = (int64_t)cells.size();
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < N; ++i) cells[i]->second = cells[i]->second / w;
     return ORC_OK;
 }
 
@@ -426,8 +544,7 @@ bool invert(int m, const double* A, double* Ainv) {
 
 int one_step(Oracle& o, double t_target, int64_t* updates) {
     grow(o);
-    double rmax = 0.0;
-    for (auto& kv : o.P) rmax = std::max(rmax, cfl_rate(o, kv.first));
+    double rmax = max_rate(o);
     double remaining = t_target - o.t;
     double dt = rmax > 0.0 ? o.c.cfl / rmax : INFINITY;
     double t_new;
@@ -492,33 +609,48 @@ int orc_init_gaussian(void* h, const double* mean, const double* cov, double t0)
     };
     int ctr[6];
     for (int k = 0; k < n; ++k) ctr[k] = (int)std::lround((mean[k] - o.c.x0[k]) / o.c.h[k]);
-    auto scan_box = [&](double r2, auto&& visit) {
-        int lo[6], hi[6];
+    /* the box of half-width ceil(sqrt(r2 cov_kk) / h_k) + 1 around the mean's
+     * cell, visited in lexicographic order (dimension 0 slowest) in chunks of
+     * consecutive cells; visit(chunk, cell) */
+    auto scan_box = [&](double r2, int64_t chunks, auto&& visit) {
+        int lo[6];
+        int64_t dims[6], total = 1;
         for (int k = 0; k < n; ++k) {
             int hw = (int)std::ceil(std::sqrt(r2 * cov[k * n + k]) / o.c.h[k]) + 1;
             lo[k] = ctr[k] - hw;
-            hi[k] = ctr[k] + hw;
+            dims[k] = 2 * (int64_t)hw + 1;
+            total *= dims[k];
         }
-        Idx i{0, 0, 0, 0, 0, 0};
-        for (int k = 0; k < n; ++k) i[k] = lo[k];
-        while (true) {
-            visit(i);
-            int k = n - 1;
-            while (k >= 0 && i[k] == hi[k]) { i[k] = lo[k]; --k; }
-            if (k < 0) break;
-            ++i[k];
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int64_t c = 0; c < chunks; ++c) {
+            const int64_t a = total * c / chunks, b = total * (c + 1) / chunks;
+            for (int64_t lin = a; lin < b; ++lin) {
+                Idx i{0, 0, 0, 0, 0, 0};
+                int64_t r = lin;
+                for (int k = n - 1; k >= 0; --k) {
+                    i[k] = lo[k] + (int32_t)(r % dims[k]);
+                    r /= dims[k];
+                }
+                visit(c, i);
+            }
         }
     };
     double thr = o.c.thr_rel > 0.0 ? o.c.thr_rel : 1e-300;
+    const int64_t chunks = 1024;
+    std::vector<double> cmax(chunks, 0.0);
+    scan_box(-2.0 * std::log(thr), chunks, [&](int64_t c, const Idx& i) { cmax[c] = std::max(cmax[c], gauss(i)); });
     double gmax = 0.0;
-    scan_box(-2.0 * std::log(thr), [&](const Idx& i) { gmax = std::max(gmax, gauss(i)); });
+    for (double v : cmax) gmax = std::max(gmax, v);
     if (!(gmax > 0.0)) { o.err = "initial density underflows on the grid"; return ORC_EDEGENERATE; }
     double pstar = o.c.thr_rel * gmax;
     o.P.clear();
-    scan_box(-2.0 * std::log(thr * gmax), [&](const Idx& i) {
+    std::vector<std::vector<std::pair<Idx, double>>> kept(chunks);
+    scan_box(-2.0 * std::log(thr * gmax), chunks, [&](int64_t c, const Idx& i) {
         double g = gauss(i);
-        if (g > pstar) o.P[i] = g;
+        if (g > pstar) kept[c].push_back({i, g});
     });
+    for (auto& part : kept)
+        for (auto& kv : part) o.P[kv.first] = kv.second;
     o.t = t0;
     o.step = 0;
     return normalise(o);
@@ -569,7 +701,11 @@ int orc_correct_gaussian(void* h, const double* y, const double* R, const int32_
     if (m < 1 || m > 6 || !invert(m, R, Rinv)) { o.err = "bad measurement"; return ORC_EINVAL; }
     for (int a = 0; a < m; ++a)
         if (H_idx[a] < 0 || H_idx[a] >= o.c.n) { o.err = "bad measurement index"; return ORC_EINVAL; }
-    for (auto& kv : o.P) {
+    const auto cells = cell_list(o.P);
+    const int64_t N = (int64_t)cells.size();
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < N; ++i) {
+        auto& kv = *cells[i];
         double r[6];
         for (int a = 0; a < m; ++a) r[a] = y[a] - centre(o, kv.first, H_idx[a]);
         double q = 0.0;
@@ -602,18 +738,30 @@ int64_t orc_read_cells(void* h, int32_t* idx, double* p, int64_t cap) {
 void orc_moments(void* h, double* mean, double* cov) {
     Oracle& o = *(Oracle*)h;
     const int n = o.c.n;
-    for (int a = 0; a < n; ++a) {
-        ExactSum s;
-        for (auto& kv : o.P) s.add(centre(o, kv.first, a) * kv.second);
-        mean[a] = o.prod_h * s.value();
-    }
-    for (int a = 0; a < n; ++a)
-        for (int b = 0; b < n; ++b) {
-            ExactSum s;
-            for (auto& kv : o.P)
-                s.add((centre(o, kv.first, a) - mean[a]) * (centre(o, kv.first, b) - mean[b]) * kv.second);
-            cov[a * n + b] = o.prod_h * s.value();
+    const auto cells = cell_list(o.P);
+    const int64_t N = (int64_t)cells.size();
+    /* sum over the cells of term(cell), exactly, for each of `count` terms */
+    auto exact = [&](int count, auto&& term, double* out) {
+        std::vector<ExactSum> tot(count);
+#pragma omp parallel
+        {
+            std::vector<ExactSum> part(count);
+#pragma omp for schedule(static)
+            for (int64_t i = 0; i < N; ++i)
+                for (int q = 0; q < count; ++q) part[q].add(term(*cells[i], q));
+#pragma omp critical
+            for (int q = 0; q < count; ++q) tot[q].merge(part[q]);
         }
+        for (int q = 0; q < count; ++q) out[q] = o.prod_h * tot[q].value();
+    };
+    exact(n, [&](const std::pair<const Idx, double>& kv, int a) { return centre(o, kv.first, a) * kv.second; },
+          mean);
+    exact(n * n,
+          [&](const std::pair<const Idx, double>& kv, int q) {
+              const int a = q / n, b = q % n;
+              return (centre(o, kv.first, a) - mean[a]) * (centre(o, kv.first, b) - mean[b]) * kv.second;
+          },
+          cov);
 }
 
 /* ---- single pieces of the step, for the pins in tests/ ---- */
@@ -633,8 +781,7 @@ int orc_normalise(void* h) { return normalise(*(Oracle*)h); }
 /* dt the next step would take towards t_target (after its grow). */
 double orc_cfl_dt(void* h) {
     Oracle& o = *(Oracle*)h;
-    double rmax = 0.0;
-    for (auto& kv : o.P) rmax = std::max(rmax, cfl_rate(o, kv.first));
+    double rmax = max_rate(o);
     return rmax > 0.0 ? o.c.cfl / rmax : INFINITY;
 }
 
@@ -674,6 +821,7 @@ double orc_exact_sum(const double* x, int64_t m) {
 int orc_ctu_sample(void* h, double dt, const int32_t* idx, int64_t m, double* out) {
     Oracle& o = *(Oracle*)h;
     const int n = o.c.n;
+#pragma omp parallel for schedule(dynamic, 16)
     for (int64_t q = 0; q < m; ++q) {
         Idx i{0, 0, 0, 0, 0, 0};
         for (int k = 0; k < n; ++k) i[k] = idx[q * n + k];
@@ -694,6 +842,18 @@ int orc_ctu_sample(void* h, double dt, const int32_t* idx, int64_t m, double* ou
         out[q] = res[i];
     }
     return ORC_OK;
+}
+
+/* Threads of the parallel loops (0: the OpenMP default); returns the number
+ * in use afterwards (1 in a build without OpenMP). Results do not depend on it. */
+int32_t orc_set_threads(int32_t k) {
+#ifdef _OPENMP
+    if (k > 0) omp_set_num_threads(k);
+    return (int32_t)omp_get_max_threads();
+#else
+    (void)k;
+    return 1;
+#endif
 }
 
 double orc_time(void* h) { return ((Oracle*)h)->t; }

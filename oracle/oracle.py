@@ -1,6 +1,6 @@
 """Python handle on the GBEES oracle -- TEST INFRASTRUCTURE ONLY.
 
-The oracle is a plain single-threaded FP64 CPU implementation of the GBEES
+The oracle is a plain FP64 CPU implementation of the GBEES
 propagation step (DCU, Eq. 7; CTU, Algorithm 1; high-resolution correction;
 CFL time step, Eq. 8; directional grow and prune, Sec. 3.3 / Algorithm 3;
 Bayesian update, Eq. 4), written in `gbees_oracle.cpp`. Only the tests, the
@@ -58,6 +58,17 @@ class _Stats(ctypes.Structure):
     ]
 
 
+_FLAGS = ["-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC"]
+
+
+def _compile(src: str, out: str, check_output: bool = False) -> None:
+    """g++ with the oracle's flags, with OpenMP when the compiler has it (the
+    results do not depend on the number of threads)."""
+    r = subprocess.run(["g++", *_FLAGS, "-fopenmp", src, "-o", out], capture_output=True, text=True)
+    if r.returncode != 0:
+        subprocess.run(["g++", *_FLAGS, src, "-o", out], check=True, capture_output=check_output)
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle into oracle/_lib (g++, -O2, no fused multiply-add)."""
     with _lock:
@@ -65,9 +76,7 @@ def build(force: bool = False) -> str:
             return _LIB
         os.makedirs(_LIBDIR, exist_ok=True)
         tmp = _LIB + f".tmp{os.getpid()}"
-        cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC",
-               _SRC, "-o", tmp]
-        subprocess.run(cmd, check=True)
+        _compile(_SRC, tmp)
         os.replace(tmp, _LIB)
         return _LIB
 
@@ -81,9 +90,7 @@ def compile_variant(old: str, new: str, out_path: str) -> str:
     tmp_src = out_path + ".cpp"
     with open(tmp_src, "w") as f:
         f.write(src.replace(old, new))
-    cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC",
-           tmp_src, "-o", out_path]
-    subprocess.run(cmd, check=True, capture_output=True)
+    _compile(tmp_src, out_path, check_output=True)
     return out_path
 
 
@@ -118,6 +125,7 @@ def _lib():
             "orc_exact_sum": (d, [P(d), i64]),
             "orc_ctu_sample": (ctypes.c_int, [vp, d, P(i32), i64, P(d)]),
             "orc_time": (d, [vp]),
+            "orc_set_threads": (i32, [i32]),
             "orc_steps": (i64, [vp]),
         }
         for name, (res, args) in sig.items():
@@ -134,6 +142,12 @@ def _dp(a: np.ndarray):
 
 def _ip(a: np.ndarray):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+def set_threads(k: int = 0) -> int:
+    """Threads of the oracle's parallel loops (0: the OpenMP default, all
+    cores); returns the number in use. The results do not depend on it."""
+    return int(_lib().orc_set_threads(int(k)))
 
 
 def exact_sum(x: Sequence[float]) -> float:
