@@ -265,11 +265,10 @@ void gbees_destroy(gbees_ctx* ctx);
 
 /* Propagation without any device allocation by the caller or the library.
  * The paper has no counterpart: this entry point exists for callers that
- * cannot call cudaMalloc -- code that runs while a stream is being captured
- * into a CUDA graph (an allocation there is illegal or breaks the capture),
- * real-time loops that cannot afford the implicit synchronisation and latency
- * of an allocation, and host applications that own all device memory through
- * their own allocator and forbid side allocations.
+ * cannot call cudaMalloc -- real-time loops that cannot afford the implicit
+ * synchronisation and latency of an allocation, and host applications that
+ * own all device memory through their own allocator and forbid side
+ * allocations.
  *
  * It does what gbees_create + gbees_init_cells + gbees_propagate +
  * gbees_read_cells(sorted = 0) do, but its workspace is a file-scope device
@@ -280,7 +279,13 @@ void gbees_destroy(gbees_ctx* ctx);
  * gbees_propagate; the active cells at t_end are written in storage order to
  * idx_out (cap_out x n) and p_out (cap_out, normalised densities), their count
  * to *n_out; stats may be NULL. cuda_stream: the stream to work on (NULL =
- * legacy default stream); the call returns after its work completed.
+ * legacy default stream).
+ *
+ * Synchronisation: like the calls it mirrors, it synchronises cuda_stream
+ * (it reads the device scalars back between its phases and before it
+ * returns), so it must not be called while cuda_stream is being captured
+ * into a CUDA graph, nor while any stream is captured in global capture
+ * mode. It returns after its work has completed.
  *
  * Errors: GBEES_ECAPACITY when gbees_workspace_bytes(cfg) exceeds
  * GBEES_NOALLOC_SCRATCH_BYTES (use the regular entry points with your own
@@ -288,13 +293,16 @@ void gbees_destroy(gbees_ctx* ctx);
  * result cells (the first cap_out are written), and any status of the
  * calls it mirrors. No context outlives the call, so no error message is kept.
  *
- * The first call on a device looks up the device address of the array for
- * the device that is current (once per device); make that first call before
- * any stream capture starts. Every call on a device uses the same array and
- * the array keeps the last call's contents; each call clears what has to
- * start empty (the scalars and the hashtable) before using it. Calls whose
- * work overlaps on one GPU (other host threads, other streams) race on the
- * array and corrupt each other: serialise them. */
+ * The first call on a device looks up the device address of the array on
+ * that device (once per device, while it is current) and keeps it for the
+ * rest of the process. A device reset (cudaDeviceReset, or any other
+ * teardown of the device's primary context) invalidates that address: after
+ * one, do not call this entry point again in the same process. Every call
+ * on a device uses the same array and the array keeps the last call's
+ * contents; each call clears what has to start empty (the scalars and the
+ * hashtable) before using it. Calls whose work overlaps on one GPU (other
+ * host threads, other streams) race on the array and corrupt each other:
+ * serialise them. */
 int gbees_propagate_cells_noalloc(const gbees_config* cfg, const int32_t* idx, const double* p, int64_t N,
                                   double t0, int64_t step0, double t_end, void* cuda_stream, int32_t* idx_out,
                                   double* p_out, int64_t cap_out, int64_t* n_out, gbees_stats* stats);

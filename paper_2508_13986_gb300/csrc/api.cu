@@ -1,7 +1,7 @@
 // Host side of the GBEES C ABI (include/gbees.h): configuration checks,
 // workspace layout, the per-step launch sequence and the host<->device
 // transfers of the public calls. All arithmetic of the method runs in the
-// kernels of gbees_kernels.cuh and gbees_ctu.cuh.
+// kernels of gbees_kernels.cuh, gbees_phases.cuh and gbees_persistent.cuh.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -1279,7 +1279,8 @@ int gbees_moments(gbees_ctx* ctx, double* mean, double* cov) {
 // The workspace of gbees_propagate_cells_noalloc lives in this file-scope device
 // array. Host code must not pass the array's name to a kernel: on the host it is
 // only a stand-in symbol. Its device address is looked up once per device with
-// cudaGetSymbolAddress while that device is current.
+// cudaGetSymbolAddress while that device is current, and kept for the life of
+// the process (a device reset would invalidate it; the header says so).
 
 namespace {
 

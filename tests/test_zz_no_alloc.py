@@ -1,8 +1,8 @@
 """The entry point that allocates nothing, against the regular entry points.
 
-Some callers cannot allocate device memory: code that runs while a stream is
-captured into a CUDA graph, real-time loops that cannot pay for an allocation,
-and hosts whose own allocator owns every byte of device memory. For them
+Some callers cannot allocate device memory: real-time loops that cannot pay
+for the synchronisation and latency of an allocation, and hosts whose own
+allocator owns every byte of device memory. For them
 gbees_propagate_cells_noalloc uses a fixed scratch array built into the
 library. This test calls it through the C ABI twice in a row and checks each
 result against create + init_cells + propagate + read_cells on a workspace the
