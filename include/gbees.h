@@ -107,7 +107,18 @@ typedef struct {
     int64_t max_cells;      /* fixed capacity of active plus halo cells (Sec. 4.1) */
     double table_factor;    /* hashtable slots per cell of capacity, >= 1.25 (0 = 2.0, Sec. 4.2) */
     int32_t launch_mode;    /* GBEES_LAUNCH_*: how propagate drives the time steps */
+    int32_t storage_order;  /* GBEES_ORDER_*: order of the pool after a prune of a large grid */
 } gbees_config;
+
+/* Storage order of the pool entries after a prune of a grid of more than
+ * 2^18 entries (smaller grids keep their order; the results never depend on
+ * it, only the speed of the neighbour gathers does):
+ *   KEY     lexicographic order of the cell indices (dimension 0 slowest), so
+ *           that the neighbours of a warp's consecutive cells in any dimension
+ *           are consecutive too
+ *   MORTON  Morton (Z-curve) order of the cell indices
+ *   NONE    the survivors keep their order (active cells first, then halo) */
+enum { GBEES_ORDER_KEY = 0, GBEES_ORDER_MORTON = 1, GBEES_ORDER_NONE = 2 };
 
 /* Launch modes of gbees_propagate (all give bit-identical results):
  *   AUTO        persistent kernel while the grid is small, CUDA graph beyond
@@ -251,6 +262,17 @@ typedef struct {
 /* enable != 0 turns event timing on; reset != 0 zeroes the counters. */
 int gbees_profile_control(gbees_ctx* ctx, int32_t enable, int32_t reset);
 int gbees_profile_read(gbees_ctx* ctx, gbees_profile* out);
+
+/* Bound of the device-side waits of the context's multi-block launches (the
+ * grid barriers of the persistent kernel and of a batch's teams): a barrier
+ * gives up after `spins` polls of its generation word (2^26 by default, about
+ * two seconds), records GBEES_ETIMEOUT in the device scalars and every block
+ * leaves the launch; the call then returns GBEES_ETIMEOUT with the context
+ * poisoned until the next init, and the device stays usable.
+ * extra_arrivals (0 in normal use) makes every grid barrier wait for that
+ * many blocks beyond those launched, so that no barrier can complete: a way
+ * to exercise the bounded wait and its error path. spins >= 1. */
+int gbees_set_wait_limit(gbees_ctx* ctx, int64_t spins, int32_t extra_arrivals);
 
 /* Last error status and message of the context (never NULL). */
 int gbees_get_status(gbees_ctx* ctx);

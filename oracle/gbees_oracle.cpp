@@ -673,11 +673,15 @@ int orc_init_cells(void* h, const int32_t* idx, const double* p, int64_t N, doub
 
 /* Propagate until t == t_end: steps of grow, dt (Eq. 8), flux update, prune
  * (when due) and normalisation, without measurements. */
-int orc_propagate(void* h, double t_end, orc_stats* st) {
+int orc_propagate_steps(void* h, double t_end, int64_t max_steps, orc_stats* st);
+int orc_propagate(void* h, double t_end, orc_stats* st) { return orc_propagate_steps(h, t_end, -1, st); }
+
+/* The same, but at most max_steps steps (max_steps < 0: no cap). */
+int orc_propagate_steps(void* h, double t_end, int64_t max_steps, orc_stats* st) {
     Oracle& o = *(Oracle*)h;
     int64_t steps = 0, updates = 0;
     int rc = ORC_OK;
-    while (o.t < t_end) {
+    while (o.t < t_end && (max_steps < 0 || steps < max_steps)) {
         rc = one_step(o, t_end, &updates);
         ++steps;
         if (rc) break;

@@ -110,6 +110,7 @@ def _lib():
             "orc_init_gaussian": (ctypes.c_int, [vp, P(d), P(d), d]),
             "orc_init_cells": (ctypes.c_int, [vp, P(i32), P(d), i64, d, i64]),
             "orc_propagate": (ctypes.c_int, [vp, d, P(_Stats)]),
+            "orc_propagate_steps": (ctypes.c_int, [vp, d, i64, P(_Stats)]),
             "orc_correct_gaussian": (ctypes.c_int, [vp, P(d), P(d), P(i32), i32]),
             "orc_count": (i64, [vp]),
             "orc_read_cells": (i64, [vp, P(i32), P(d), i64]),
@@ -209,9 +210,10 @@ class Oracle:
         P = np.ascontiguousarray(p, dtype=np.float64)
         self._check(_lib().orc_init_cells(self._h, _ip(I), _dp(P), I.shape[0], float(t0), int(step0)))
 
-    def propagate(self, t_end: float) -> OracleStats:
+    def propagate(self, t_end: float, max_steps: int = -1) -> OracleStats:
+        """Steps towards t_end until it is reached (or max_steps steps, if >= 0)."""
         st = _Stats()
-        self._check(_lib().orc_propagate(self._h, float(t_end), ctypes.byref(st)))
+        self._check(_lib().orc_propagate_steps(self._h, float(t_end), int(max_steps), ctypes.byref(st)))
         return OracleStats(st.steps, st.cell_updates, st.t, st.last_dt, st.total_steps)
 
     def correct_gaussian(self, y, R, H_idx):

@@ -98,7 +98,8 @@ constexpr size_t ALIGN = 256;
 size_t align_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
 
 struct Layout {
-    size_t sc, blk, part, sorthist, key[2], q[2], link[2], om[2], slot[2], keep, map, table, wv_u, wv_g, fl, total;
+    size_t sc, blk, part, sorthist, key[2], q[2], link[2], om[2], slot[2], u[2], keep, map, table, wl, wg, tg, fl,
+        total;
     unsigned long long slots;
 };
 
@@ -140,6 +141,7 @@ bool config_ok(const gbees_config* c, std::string* why) {
     if (c->max_cells < 1 || c->max_cells > 0x7fffffffll) return fail("max_cells must be in 1..2^31-1");
     if (!(c->table_factor == 0.0 || c->table_factor >= 1.25)) return fail("table_factor must be 0 or >= 1.25");
     if (c->launch_mode < GBEES_LAUNCH_AUTO || c->launch_mode > GBEES_LAUNCH_DIRECT) return fail("unknown launch_mode");
+    if (c->storage_order < GBEES_ORDER_KEY || c->storage_order > GBEES_ORDER_NONE) return fail("unknown storage_order");
     return true;
 }
 
@@ -163,16 +165,19 @@ bool make_layout(const gbees_config* c, Layout* L) {
     L->sorthist = take(sizeof(unsigned int) * 256 * SORT_BLOCKS);
     for (int g = 0; g < 2; ++g) L->key[g] = take(8 * cap);
     for (int g = 0; g < 2; ++g) L->q[g] = take(S * cap);
-    for (int g = 0; g < 2; ++g) L->link[g] = take((size_t)4 * lrow_of(c->n) * cap);
+    for (int g = 0; g < 2; ++g) L->link[g] = take((size_t)4 * 2 * c->n * std::max<size_t>(cap, 1));
     for (int g = 0; g < 2; ++g) L->om[g] = take(2 * cap);
     for (int g = 0; g < 2; ++g) L->slot[g] = take(4 * cap);
     L->keep = take(cap);
     L->map = take(4 * cap);
     L->table = take(sizeof(Slot) * slots);
-    // scratch of the three-pass update, storage type
-    const size_t rows = S * (size_t)wrow_of(c->n) * cap;
-    L->wv_u = take(rows);
-    L->wv_g = take(rows);
+    // face velocities (two generations) and the scratch of the three-pass
+    // update, storage type, n values per entry (one for tg)
+    const size_t rows = S * (size_t)c->n * cap;
+    for (int g = 0; g < 2; ++g) L->u[g] = take(rows);
+    L->wl = take(rows);
+    L->wg = take(rows);
+    L->tg = take(S * cap);
     L->fl = take(rows);
     L->total = off;
     L->slots = slots;
@@ -194,6 +199,9 @@ void bind_context(gbees_ctx* ctx, const gbees_config* cfg, const Layout& L, void
     m.key_bits = key_bits_for(cfg->n);
     m.prune_interval = cfg->prune_interval;
     m.probe_width = cfg->probe_width ? cfg->probe_width : 1;
+    m.sort_order = cfg->storage_order;
+    m.bar_extra = 0;
+    m.spin_limit = BARRIER_SPIN_LIMIT;
     m.cap = cfg->max_cells;
     m.tmask = L.slots - 1;
     std::memcpy(m.a, cfg->params, sizeof m.a);
@@ -229,8 +237,10 @@ void bind_context(gbees_ctx* ctx, const gbees_config* cfg, const Layout& L, void
     b.keep = (unsigned char*)(base + L.keep);
     b.map = (int*)(base + L.map);
     b.table = (Slot*)(base + L.table);
-    b.wv_u = (void*)(base + L.wv_u);
-    b.wv_g = (void*)(base + L.wv_g);
+    for (int g = 0; g < 2; ++g) b.u[g] = (void*)(base + L.u[g]);
+    b.wl = (void*)(base + L.wl);
+    b.wg = (void*)(base + L.wg);
+    b.tg = (void*)(base + L.tg);
     b.fl = (void*)(base + L.fl);
 }
 
@@ -366,23 +376,23 @@ void with_nt(const gbees_ctx* ctx, F&& f) {
     }
 }
 
-template <int N>
+template <int N, typename T>
 void* link_kernel(int probe_width) {
     switch (probe_width) {
-        case 2: return (void*)k_link<N, 2>;
-        case 4: return (void*)k_link<N, 4>;
-        case 8: return (void*)k_link<N, 8>;
-        case 16: return (void*)k_link<N, 16>;
-        case 32: return (void*)k_link<N, 32>;
-        default: return (void*)k_link<N, 1>;
+        case 2: return (void*)k_link<N, 2, T>;
+        case 4: return (void*)k_link<N, 4, T>;
+        case 8: return (void*)k_link<N, 8, T>;
+        case 16: return (void*)k_link<N, 16, T>;
+        case 32: return (void*)k_link<N, 32, T>;
+        default: return (void*)k_link<N, 1, T>;
     }
 }
 
 // step != 0: the link of a time step (its last block also fixes dt).
-template <int N>
+template <int N, typename T>
 void launch_link(gbees_ctx* ctx, int step) {
     void* args[] = {&ctx->m, &ctx->b, &step};
-    cudaLaunchKernel(link_kernel<N>(ctx->m.probe_width), dim3(ctx->grid), dim3(THREADS), args, 0, ctx->stream);
+    cudaLaunchKernel(link_kernel<N, T>(ctx->m.probe_width), dim3(ctx->grid), dim3(THREADS), args, 0, ctx->stream);
 }
 
 void resolve_update_kernels(gbees_ctx* ctx) {
@@ -402,33 +412,52 @@ void launch_list(gbees_ctx* ctx, void* const* f, int nf) {
     for (int i = 0; i < nf; ++i) cudaLaunchKernel(f[i], dim3(ctx->grid), dim3(THREADS), args, 0, ctx->stream);
 }
 
-// The prune of Algorithm 3 (directional marking, status, Morton-order sort,
-// compaction, relink, rehash). It runs only when the device flag prune_now is
-// set. The graph and direct paths put the survivors in Morton order of their
-// cell indices (active cells first), which keeps the neighbour rows of large
-// grids close together.
+// The prune of Algorithm 3 (directional marking, status, compaction, relink,
+// rehash). It runs only when the device flag prune_now is set. A large grid's
+// survivors are sorted into the configured storage order (key or Morton order
+// of the cell indices), which keeps the neighbour gathers of a sweep close
+// together; a grid that fits in L2 keeps its order (stream compaction).
 constexpr int kSortPasses = 8;                          // 8-bit digits of the 64-bit sort key
-constexpr int kPruneKernels = 3 + 1 + 3 * kSortPasses + 1 + 2;
+constexpr int kPruneKernelsSorted = 3 + 1 + 3 * kSortPasses + 1 + 2;
+constexpr int kPruneKernelsPlain = 3 + 1 + 1;
+constexpr long long kSortMinEntries = 1ll << 18;        // smaller pools are not sorted
+
+bool sorts(const gbees_ctx* ctx) { return ctx->cfg.storage_order != GBEES_ORDER_NONE; }
+
+// Blocks of the sort kernels for a pool of N entries: about 16 tiles of
+// THREADS entries per block, at most SORT_BLOCKS.
+int sort_blocks(long long N) {
+    const long long per = (long long)THREADS * 16;
+    return (int)std::max(1ll, std::min<long long>(SORT_BLOCKS, (N + per - 1) / per));
+}
 
 void launch_prune(gbees_ctx* ctx) {
     const int G = ctx->grid;
-    const int Gs = std::min(G, SORT_BLOCKS);
     cudaStream_t s = ctx->stream;
-    Phase ph(ctx, GBEES_PHASE_PRUNE, kPruneKernels);
+    // the host's copy of the pool size (possibly a few steps old: it only
+    // decides the storage order, which no result depends on)
+    const long long N = ctx->hs.N;
+    const bool sorted = sorts(ctx) && N > kSortMinEntries;
+    const int Gs = sort_blocks(N);
+    Phase ph(ctx, GBEES_PHASE_PRUNE, sorted ? kPruneKernelsSorted : kPruneKernelsPlain);
     with_nt(ctx, [&](auto NN, auto TT) {
         constexpr int N = decltype(NN)::value;
         using T = decltype(TT);
         k_prune_mark<T><<<G, THREADS, 0, s>>>(ctx->m, ctx->b);
         k_prune_scatter<N, T><<<G, THREADS, 0, s>>>(ctx->m, ctx->b);
         k_prune_count<N><<<G, THREADS, 0, s>>>(ctx->m, ctx->b);
-        k_sort_init<<<G, THREADS, 0, s>>>(ctx->m, ctx->b);
-        for (int pass = 0; pass < kSortPasses; ++pass) {
-            k_sort_hist<<<Gs, THREADS, 0, s>>>(ctx->m, ctx->b, pass & 1, 8 * pass);
-            k_sort_scan<<<1, THREADS, 0, s>>>(ctx->m, ctx->b, Gs);
-            k_sort_scatter<<<Gs, THREADS, 0, s>>>(ctx->m, ctx->b, pass & 1, 8 * pass);
+        if (sorted) {
+            k_sort_init<<<G, THREADS, 0, s>>>(ctx->m, ctx->b);
+            for (int pass = 0; pass < kSortPasses; ++pass) {
+                k_sort_hist<<<Gs, THREADS, 0, s>>>(ctx->m, ctx->b, pass & 1, 8 * pass);
+                k_sort_scan<<<1, SCAN_THREADS, 0, s>>>(ctx->m, ctx->b, Gs);
+                k_sort_scatter<<<Gs, THREADS, 0, s>>>(ctx->m, ctx->b, pass & 1, 8 * pass);
+            }
+            k_sort_map<<<G, THREADS, 0, s>>>(ctx->m, ctx->b);
+            k_prune_compact_sorted<N, T><<<G, THREADS, 0, s>>>(ctx->m, ctx->b);
+        } else {
+            k_prune_compact<N, T><<<G, THREADS, 0, s>>>(ctx->m, ctx->b);
         }
-        k_sort_map<<<G, THREADS, 0, s>>>(ctx->m, ctx->b);
-        k_prune_compact_sorted<N, T><<<G, THREADS, 0, s>>>(ctx->m, ctx->b);
         k_prune_relink<N><<<G, THREADS, 0, s>>>(ctx->m, ctx->b, G);
     });
 }
@@ -460,9 +489,9 @@ void launch_step(gbees_ctx* ctx) {
     }
     {
         Phase ph(ctx, GBEES_PHASE_LINK, 1);
-        with_nt(ctx, [&](auto NN, auto) {
+        with_nt(ctx, [&](auto NN, auto TT) {
             constexpr int N = decltype(NN)::value;
-            launch_link<N>(ctx, 1);
+            launch_link<N, decltype(TT)>(ctx, 1);
         });
     }
     {
@@ -519,12 +548,12 @@ void graph_nodes(gbees_ctx* ctx, GraphBuilder& gb, cudaGraph_t body, cudaGraphCo
     resolve_update_kernels(ctx);
     cudaGraphNode_t n = nullptr;
     for (int i = 0; i < ctx->kern.npre; ++i) n = gb.add(body, n, ctx->kern.pre[i], G, THREADS, mb);
-    n = gb.add(body, n, link_kernel<N>(ctx->m.probe_width), G, THREADS, link_args);
+    n = gb.add(body, n, link_kernel<N, T>(ctx->m.probe_width), G, THREADS, link_args);
     for (int i = 0; i < ctx->kern.npost; ++i) n = gb.add(body, n, ctx->kern.post[i], G, THREADS, mb);
     DevScalars* sc = ctx->b.sc;
     long long maxit = kGraphMaxIter;
     int step_kernels = ctx->kern.npre + 1 + ctx->kern.npost + 1;
-    int prune_kernels = kPruneKernels;
+    int prune_kernels = sorts(ctx) ? kPruneKernelsSorted : kPruneKernelsPlain;
     void* ctl_args[] = {&sc, &hw, &hp, &maxit, &step_kernels, &prune_kernels};
     n = gb.add(body, n, (void*)k_loop_ctl, 1, 1, ctl_args);
     cudaGraph_t pb = nullptr;
@@ -540,16 +569,20 @@ void graph_nodes(gbees_ctx* ctx, GraphBuilder& gb, cudaGraph_t body, cudaGraphCo
     cudaGraphNode_t q = gb.add(pb, nullptr, (void*)k_prune_mark<T>, G, THREADS, mb);
     q = gb.add(pb, q, (void*)k_prune_scatter<N, T>, G, THREADS, mb);
     q = gb.add(pb, q, (void*)k_prune_count<N>, G, THREADS, mb);
-    q = gb.add(pb, q, (void*)k_sort_init, G, THREADS, mb);
-    for (int pass = 0; pass < kSortPasses; ++pass) {
-        void* pass_args[] = {m, b, &srcs[pass & 1], &shifts[pass]};
-        void* scan_args[] = {m, b, &nsort};
-        q = gb.add(pb, q, (void*)k_sort_hist, Gs, THREADS, pass_args);
-        q = gb.add(pb, q, (void*)k_sort_scan, 1, THREADS, scan_args);
-        q = gb.add(pb, q, (void*)k_sort_scatter, Gs, THREADS, pass_args);
+    if (sorts(ctx)) {
+        q = gb.add(pb, q, (void*)k_sort_init, G, THREADS, mb);
+        for (int pass = 0; pass < kSortPasses; ++pass) {
+            void* pass_args[] = {m, b, &srcs[pass & 1], &shifts[pass]};
+            void* scan_args[] = {m, b, &nsort};
+            q = gb.add(pb, q, (void*)k_sort_hist, Gs, THREADS, pass_args);
+            q = gb.add(pb, q, (void*)k_sort_scan, 1, SCAN_THREADS, scan_args);
+            q = gb.add(pb, q, (void*)k_sort_scatter, Gs, THREADS, pass_args);
+        }
+        q = gb.add(pb, q, (void*)k_sort_map, G, THREADS, mb);
+        q = gb.add(pb, q, (void*)k_prune_compact_sorted<N, T>, G, THREADS, mb);
+    } else {
+        q = gb.add(pb, q, (void*)k_prune_compact<N, T>, G, THREADS, mb);
     }
-    q = gb.add(pb, q, (void*)k_sort_map, G, THREADS, mb);
-    q = gb.add(pb, q, (void*)k_prune_compact_sorted<N, T>, G, THREADS, mb);
     gb.add(pb, q, (void*)k_prune_relink<N>, G, THREADS, relink_args);
 }
 
@@ -712,6 +745,13 @@ int gbees_profile_read(gbees_ctx* ctx, gbees_profile* out) {
     return GBEES_OK;
 }
 
+int gbees_set_wait_limit(gbees_ctx* ctx, int64_t spins, int32_t extra_arrivals) {
+    if (!ctx || spins < 1 || extra_arrivals < 0 || extra_arrivals > GRID_MAX) return GBEES_EINVAL;
+    ctx->m.spin_limit = spins;
+    ctx->m.bar_extra = extra_arrivals;
+    return GBEES_OK;
+}
+
 int gbees_get_status(gbees_ctx* ctx) { return ctx ? ctx->status : GBEES_EINVAL; }
 
 const char* gbees_last_error(gbees_ctx* ctx) {
@@ -786,7 +826,7 @@ int gbees_init_gaussian(gbees_ctx* ctx, const double* mean, const double* cov, d
             constexpr int N = decltype(NN)::value;
             using T = decltype(TT);
             k_halo<N, T, 0><<<G, THREADS, 0, s>>>(ctx->m, ctx->b);
-            launch_link<N>(ctx, 0);
+            launch_link<N, T>(ctx, 0);
         });
         k_finalise<<<1, 1, 0, s>>>(ctx->m, ctx->b.sc, 0);
     }
@@ -833,7 +873,7 @@ int gbees_init_cells(gbees_ctx* ctx, const int32_t* idx, const double* p, int64_
         constexpr int NC = decltype(NN)::value;
         using T = decltype(TT);
         k_halo<NC, T, 0><<<G, THREADS, 0, s>>>(ctx->m, ctx->b);
-        launch_link<NC>(ctx, 0);
+        launch_link<NC, T>(ctx, 0);
     });
     k_finalise<<<1, 1, 0, s>>>(ctx->m, ctx->b.sc, 2);
     if (!sync_scalars(ctx, "init_cells")) return ctx->status;

@@ -102,6 +102,9 @@ struct Model {
     int key_bits;
     int prune_interval;
     int probe_width;
+    int sort_order;              // storage order after a sorting prune (GBEES_ORDER_*)
+    int bar_extra;               // arrivals a grid barrier waits for beyond its blocks (0; > 0 only to test the bounded wait)
+    long long spin_limit;        // polls of a grid barrier before it gives up with ST_ETIMEOUT
     long long cap;               // cell capacity
     unsigned long long tmask;    // hashtable slots - 1
     double a[64];                // model parameters
@@ -138,10 +141,11 @@ struct alignas(64) Partial {
 // every face neighbour of an active cell that is not active itself is kept as
 // a halo cell (p = 0, never updated, never counted), so that all cells of the
 // update stencil (face neighbours, their face neighbours, the second
-// neighbours) are reached through links. link[g] holds one row of LROW int32
-// per entry: entry c * LROW + 2j + s is the index of the neighbour of entry c
-// one step down (s = 0) or up (s = 1) in dimension j, or -1 when it is not in
-// the pool.
+// neighbours) are reached through links. link[g] holds 2n direction-major
+// int32 arrays of cap entries: link[g][(2j + s) * cap + c] is the index of the
+// neighbour of entry c one step down (s = 0) or up (s = 1) in dimension j, or
+// -1 when it is not in the pool (a warp's consecutive entries read one
+// direction with one coalesced load).
 //
 // om[g][c]: bits 0..2n-1 are the outward directions of cell c (bit 2j+1: the
 // flow leaves through the upper j-face, bit 2j: through the lower j-face),
@@ -149,9 +153,16 @@ struct alignas(64) Partial {
 // halo cell; bit 15 marks an active cell whose downwind set is known to be
 // active (cleared by every prune).
 //
-// Update scratch (one row of WROW values of the storage type per entry):
-// wv_u[c, j] lower-face velocity, wv_g[c, d] d-direction wave entering the
-// cell, fl[c, j] flux through the lower j-face.
+// Face velocities (storage type, dimension-major: u[g][j * cap + c]): f_j at
+// the centre of the lower j-face of entry c (Eq. 7), evaluated once in FP64 when
+// the entry is created (the drift does not depend on time) and carried along
+// by the prune's compaction.
+//
+// Update scratch of the three-pass flux update (storage type, dimension-major:
+// element d * cap + c, so that a warp's 32 consecutive entries read and write
+// whole sectors): wl[d] the jump P_c - P_{c-e_d} across the lower d-face, wg[d]
+// the d-direction wave entering the cell, tg the sum over d of wg[d] / (2 h_d)
+// (one value per entry), fl[j] the flux through the lower j-face.
 struct Bufs {
     unsigned long long* key[2];
     void* q[2];
@@ -165,22 +176,14 @@ struct Bufs {
     long long* blk;  // per-block counts (active cells)
     long long* blk2; // per-block counts (halo cells)
     unsigned int* sorthist;  // digit histograms of the prune's radix sort
-    void* wv_u;  // update scratch in the storage type
-    void* wv_g;
+    void* u[2];  // face velocities (two generations, like the keys)
+    void* wl;    // update scratch in the storage type
+    void* wg;
+    void* tg;
     void* fl;
     Partial* part;   // GRID_MAX per-block partials
 };
 
-// Rows of the per-entry arrays (cell-major, so that the links or the FP64
-// scratch of one entry share one or two 32-byte sectors): LROW<N> int32 per
-// link row (2n rounded up to a power of two), WROW<N> doubles per scratch row
-// (n rounded up to a power of two).
-template <int N>
-constexpr int LROW = (2 * N <= 2) ? 2 : (2 * N <= 4) ? 4 : (2 * N <= 8) ? 8 : 16;
-template <int N>
-constexpr int WROW = (N <= 1) ? 1 : (N <= 2) ? 2 : (N <= 4) ? 4 : 8;
-__host__ __device__ constexpr int lrow_of(int n) { return (2 * n <= 2) ? 2 : (2 * n <= 4) ? 4 : (2 * n <= 8) ? 8 : 16; }
-__host__ __device__ constexpr int wrow_of(int n) { return (n <= 1) ? 1 : (n <= 2) ? 2 : (n <= 4) ? 4 : 8; }
 
 constexpr unsigned short OM_COMPLETE = 0x8000;
 constexpr unsigned short OM_GHOST = 0x4000;
@@ -400,29 +403,80 @@ __device__ __forceinline__ double cfl_rate64(const Model& m, const int* I) {
     return r;
 }
 
-// Velocity f_d at the lower (face = -1) or upper (face = +1) d-face of the cell
-// whose centre is xc shifted by s cells in dimension js (js < 0: no shift).
-// Positions are formed from the centre, so they may differ from the exact
-// x0 + (i - 1/2) h in the last bit; only the flux update uses this form.
-template <int N, int DYN, typename T>
-__device__ __forceinline__ T vel_at(const Model& m, const T* xc, const T* h, int js, int s, int d, int face) {
-    T y[N];
-#pragma unroll
-    for (int k = 0; k < N; ++k) y[k] = xc[k];
-    if (js >= 0) y[js] += (T)s * h[js];
-    y[d] += (T)face * (T)0.5 * h[d];
-    return drift<T, N>(m, DYN, y, d);
+// Sign tests, positive and negative parts. FP64 arithmetic is scarce on this
+// chip, so for doubles they work on the bit pattern in the integer pipe (a
+// finite double is > 0 exactly when its bits, read as a signed integer, are
+// > 0; -0 reads as the smallest integer).
+__device__ __forceinline__ bool gt0(double x) { return __double_as_longlong(x) > 0; }
+__device__ __forceinline__ bool lt0(double x) {
+    const long long b = __double_as_longlong(x);
+    return b < 0 && (b << 1) != 0;
 }
+__device__ __forceinline__ bool gt0(float x) { return x > 0.0f; }
+__device__ __forceinline__ bool lt0(float x) { return x < 0.0f; }
+template <typename T>
+__device__ __forceinline__ T pos_part(T x) { return gt0(x) ? x : (T)0; }
+template <typename T>
+__device__ __forceinline__ T neg_part(T x) { return lt0(x) ? x : (T)0; }
+__device__ __forceinline__ double abs_bits(double x) {
+    return __longlong_as_double(__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFll);
+}
+__device__ __forceinline__ float abs_bits(float x) { return fabsf(x); }
+// min of two non-negative finite values (integer order of the bits for doubles)
+__device__ __forceinline__ double min_nonneg(double a, double b) {
+    return __longlong_as_double(min(__double_as_longlong(a), __double_as_longlong(b)));
+}
+__device__ __forceinline__ float min_nonneg(float a, float b) { return fminf(a, b); }
+
+// The significance test p > p* (p* >= 0) of a stored value, decided exactly
+// as (double)p > p* but without FP64 arithmetic: for doubles on the bit
+// patterns (signed integer order equals the order of doubles when one side is
+// non-negative), for floats against the largest float not above p*.
+template <typename T>
+struct Above;
+template <>
+struct Above<double> {
+    long long pb;
+    __device__ __forceinline__ explicit Above(double pstar) { pb = __double_as_longlong(pstar); }
+    __device__ __forceinline__ bool operator()(double q) const { return __double_as_longlong(q) > pb; }
+};
+template <>
+struct Above<float> {
+    float pf;
+    __device__ __forceinline__ explicit Above(double pstar) {
+        pf = (float)pstar;
+        if ((double)pf > pstar) pf = nextafterf(pf, -INFINITY);  // round towards -inf
+    }
+    __device__ __forceinline__ bool operator()(float q) const { return q > pf; }
+};
+
+// 2x and x/2 of a non-negative double, exact, as IEEE arithmetic gives them;
+// for normal values by the exponent field in the integer pipe.
+__device__ __forceinline__ double twice_nonneg(double x) {
+    const long long b = __double_as_longlong(x);
+    const long long e = b >> 52;
+    if (e == 0) return __longlong_as_double(b << 1);                 // subnormal (or 0)
+    if (e <= 2045) return __longlong_as_double(b + (1ll << 52));
+    return x + x;                                                     // overflow, inf
+}
+__device__ __forceinline__ double half_nonneg(double x) {
+    const long long b = __double_as_longlong(x);
+    if ((b >> 52) >= 2) return __longlong_as_double(b - (1ll << 52));
+    return x * 0.5;                                                   // result subnormal (or 0)
+}
+__device__ __forceinline__ float twice_nonneg(float x) { return x + x; }
+__device__ __forceinline__ float half_nonneg(float x) { return 0.5f * x; }
 
 template <typename T>
 __device__ __forceinline__ T limited_wave(int lim, T W, T Wup) {
     if (lim == LIM_LW) return W;
     // MC limiter phi(theta) = max(0, min((1+theta)/2, 2, 2 theta)) with theta = Wup / W,
-    // multiplied by W and written without the division.
-    if ((W > (T)0 && Wup > (T)0) || (W < (T)0 && Wup < (T)0)) {
-        T aW = fabs(W), aU = fabs(Wup);
-        T v = fmin(fmin((T)0.5 * (aW + aU), (T)2 * aW), (T)2 * aU);
-        return W > (T)0 ? v : -v;
+    // multiplied by W and written without the division: zero unless W and Wup
+    // have the same sign, else sign(W) min(|W + Wup| / 2, 2 |W|, 2 |Wup|).
+    if ((gt0(W) && gt0(Wup)) || (lt0(W) && lt0(Wup))) {
+        const T aW = abs_bits(W), aU = abs_bits(Wup);
+        const T v = min_nonneg(min_nonneg(half_nonneg(aW + aU), twice_nonneg(aW)), twice_nonneg(aU));
+        return gt0(W) ? v : -v;
     }
     return (T)0;
 }
@@ -748,13 +802,14 @@ __device__ __forceinline__ Combined combine_partials(const Partial* part, int nb
 }
 
 // Grid-wide barrier of a cooperative launch (all blocks resident). The wait is
-// bounded: it gives up when another block has set an error or after about
-// two seconds, sets ST_ETIMEOUT, and returns false; callers then leave.
+// bounded: it gives up when another block has set an error or after
+// spin_limit polls (BARRIER_SPIN_LIMIT by default: about two seconds), sets
+// ST_ETIMEOUT, and returns false; callers then leave.
 constexpr long long BARRIER_SPIN_LIMIT = 1ll << 26;
 // Barrier of the nb blocks that share the grid whose scalars are sc (the whole
 // launch, or a team of a batched launch); every block of the team must be
 // resident (cooperative launch). Bounded: gives up with ST_ETIMEOUT.
-__device__ __forceinline__ bool grid_barrier(DevScalars* sc, int nb) {
+__device__ __forceinline__ bool grid_barrier(DevScalars* sc, int nb, long long spin_limit = BARRIER_SPIN_LIMIT) {
     __shared__ int s_ok;
     unsigned int* bar = &sc->bar_count;
     __syncthreads();
@@ -772,7 +827,7 @@ __device__ __forceinline__ bool grid_barrier(DevScalars* sc, int nb) {
             long long spins = 0;
             while (*vgen == gen) {
                 if (*(volatile int*)&sc->error) { ok = 0; break; }
-                if (++spins > BARRIER_SPIN_LIMIT) {
+                if (++spins > spin_limit) {
                     set_error(sc, ST_ETIMEOUT);
                     ok = 0;
                     break;

@@ -33,14 +33,14 @@ __device__ __forceinline__ void finish_link(const Model& m, DevScalars* sc, cons
 // Link entries [N_prev, N) (neighbour references of Sec. 4.1), set their outward
 // masks and rates; with step != 0 the last block also fixes dt (Eq. 8).
 // W lanes probe the hashtable together (warp-cooperative probing).
-template <int N, int W>
+template <int N, int W, typename T>
 __global__ void __launch_bounds__(THREADS) k_link(const Model m, Bufs b, int step) {
     DevScalars* sc = b.sc;
     if (*(volatile int*)&sc->error) return;
     if (step && *(volatile int*)&sc->done) return;
     const StepView v = view_of(m, sc);
-    const double r = (W == 1) ? link_body<N>(m, b, v.N_prev, v.N, v.g, v.nb, v.bi)
-                              : link_body_tile<N, W>(m, b, v.N_prev, v.N, v.g, v.nb, v.bi);
+    const double r = (W == 1) ? link_body<N, T>(m, b, v.N_prev, v.N, v.g, v.nb, v.bi)
+                              : link_body_tile<N, W, T>(m, b, v.N_prev, v.N, v.g, v.nb, v.bi);
     long long zero[NDIG] = {0, 0, 0, 0, 0, 0};
     block_partial(b.part, zero, -INFINITY, r);
     if (last_block(sc)) {
@@ -396,6 +396,27 @@ __global__ void __launch_bounds__(THREADS) k_prune_compact_sorted(const Model m,
     double mx = -INFINITY, rmax = 0.0;
     int err = 0;
     prune_compact_sorted_body<N, T>(m, b, v, d, mx, rmax, err);
+    if (err) set_error(sc, ST_EDEGENERATE);
+    block_partial(b.part, d, mx, rmax);
+}
+
+// Prune, pass 4 without a sort: write the survivors into the other buffer set
+// in storage order, active cells first, then the halo (stream compaction), with
+// the same partials as the sorted form.
+template <int N, typename T>
+__global__ void __launch_bounds__(THREADS) k_prune_compact(const Model m, Bufs b) {
+    DevScalars* sc = b.sc;
+    if (!prune_due(sc)) return;
+    const StepView v = view_of(m, sc);
+    const Survivors sv = block_offsets(b, v.nb, v.bi);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        sc->N_new = sv.total_a + sv.total_g;
+        sc->NA_new = sv.total_a;
+    }
+    long long d[NDIG] = {0, 0, 0, 0, 0, 0};
+    double mx = -INFINITY, rmax = 0.0;
+    int err = 0;
+    prune_compact_body<N, T>(m, b, v, sv, d, mx, rmax, err);
     if (err) set_error(sc, ST_EDEGENERATE);
     block_partial(b.part, d, mx, rmax);
 }

@@ -155,15 +155,17 @@ __global__ void k_set_count(DevScalars* sc, long long count, long long step0) {
 }
 
 // ------------------------------------------------------------------ storage order at a prune
-// The graph and direct paths give the survivors of a prune a new storage
-// order (active cells first, then the halo; each in Morton order of the cell
-// indices) with a stable LSD radix sort of (region bit | code, old index), 8
-// bits per pass, so that the neighbour rows a sweep reads are mostly near each
-// other (L2 hits). Scratch:
-// the other generation's key/slot arrays (A), its link/value arrays (B), the
-// velocity scratch (histograms), all free until the compaction writes them.
+// The prune of a large grid gives the survivors a new storage order with a
+// stable LSD radix sort of (order key, old index), 8 bits per pass: the
+// lexicographic order of the cell indices (the packed key itself, dimension 0
+// most significant), so that the face neighbours of a warp's consecutive cells
+// in any dimension are consecutive too and the neighbour gathers coalesce, or
+// the Morton order of the indices. Scratch: the other generation's key/slot
+// arrays (A) and its link/value arrays (B), free until the compaction writes
+// them.
 
 constexpr int SORT_BLOCKS = 1024;  // blocks of the sort kernels at most (histogram rows)
+constexpr int SCAN_THREADS = 1024; // threads of the histogram scan
 
 struct SortBufs {
     unsigned long long* key[2];
@@ -180,12 +182,10 @@ __device__ __forceinline__ SortBufs sort_bufs(const Bufs& b, const StepView& v) 
 }
 
 // keep[c] = status (0 drop, 1 active, 2 halo, from the status pass in map);
-// A = (sort key, c): dropped entries last, halo cells after the active ones,
-// each group in Morton order of the cell indices, so that a cell's face
-// neighbours tend to lie near it in the pool (the order affects speed only:
-// every result is independent of the storage order). A live entry's code is
-// below 2^63: only an all-ones key has an all-ones code, and no cell that
-// survives a prune has that key.
+// A = (order key, c), dropped entries last (every result is independent of
+// the storage order; only the speed depends on it). A live entry's order key
+// is below 2^63: keys use at most 63 bits, and only an all-ones key has an
+// all-ones Morton code, a key no cell that survives a prune has.
 __global__ void __launch_bounds__(THREADS) k_sort_init(const Model m, Bufs b) {
     if (!prune_due(b.sc)) return;
     const StepView v = view_of(m, b.sc);
@@ -193,10 +193,11 @@ __global__ void __launch_bounds__(THREADS) k_sort_init(const Model m, Bufs b) {
     const unsigned long long* key = b.key[v.g];
     long long c0, c1;
     block_chunk(v.N, c0, c1);
+    const bool morton = m.sort_order == 1;
     for (long long c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
         const int st = b.map[c];
         b.keep[c] = (unsigned char)st;
-        sb.key[0][c] = st == 0 ? ~0ull : ((st == 2 ? (1ull << 63) : 0ull) | morton_code(key[c], m.n, m.key_bits));
+        sb.key[0][c] = st == 0 ? ~0ull : (morton ? morton_code(key[c], m.n, m.key_bits) : key[c]);
         sb.val[0][c] = (unsigned int)c;
     }
 }
@@ -218,32 +219,44 @@ __global__ void __launch_bounds__(THREADS) k_sort_hist(const Model m, Bufs b, in
     for (int d = threadIdx.x; d < 256; d += blockDim.x) b.sorthist[(long long)d * gridDim.x + blockIdx.x] = cnt[d];
 }
 
-// Exclusive scan of the 256 x nblk histogram in place (one block).
-__global__ void __launch_bounds__(THREADS) k_sort_scan(const Model m, Bufs b, int nblk) {
+// Exclusive scan of the 256 x nblk histogram in place (one block of
+// SCAN_THREADS threads: each sums a run of counters, a block-wide scan of the
+// run totals, then each writes its run's offsets).
+__global__ void __launch_bounds__(SCAN_THREADS) k_sort_scan(const Model m, Bufs b, int nblk) {
     if (!prune_due(b.sc)) return;
-    __shared__ unsigned long long part[THREADS];
+    __shared__ unsigned long long s_warp[SCAN_THREADS / 32];
     unsigned int* hist = b.sorthist;
     const long long total = 256ll * nblk;
     const long long per = (total + blockDim.x - 1) / blockDim.x;
     const long long i0 = min(total, threadIdx.x * per), i1 = min(total, i0 + per);
     unsigned long long sum = 0;
     for (long long i = i0; i < i1; ++i) sum += hist[i];
-    part[threadIdx.x] = sum;
+    // inclusive scan of the run totals: within the warp, then over the warps
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned long long x = sum;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, off);
+        if (lane >= off) x += y;
+    }
+    if (lane == 31) s_warp[wid] = x;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long run = 0;
-        for (int t = 0; t < (int)blockDim.x; ++t) {
-            const unsigned long long x = part[t];
-            part[t] = run;
-            run += x;
+    if (wid == 0) {
+        const int nw = blockDim.x >> 5;
+        unsigned long long w = lane < nw ? s_warp[lane] : 0ull;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, w, off);
+            if (lane >= off) w += y;
         }
+        if (lane < nw) s_warp[lane] = w;
     }
     __syncthreads();
-    unsigned long long run = part[threadIdx.x];
+    unsigned long long run = x - sum + (wid > 0 ? s_warp[wid - 1] : 0ull);
     for (long long i = i0; i < i1; ++i) {
-        const unsigned int x = hist[i];
+        const unsigned int c = hist[i];
         hist[i] = (unsigned int)run;
-        run += x;
+        run += c;
     }
 }
 

@@ -54,7 +54,7 @@ __device__ __forceinline__ void step_loop(const Model& m, const Bufs& b, long lo
     // barriers would then pair with the wrong ones).
     auto barrier = [&]() -> bool {
         if (nb == 1) return __syncthreads_and(!*(volatile int*)&sc->error) != 0;
-        return grid_barrier(sc, nb);
+        return grid_barrier(sc, nb + m.bar_extra, m.spin_limit);
     };
     StepView v = view_of(m, sc);
     v.nb = nb;
@@ -97,7 +97,7 @@ __device__ __forceinline__ void step_loop(const Model& m, const Bufs& b, long lo
         v.N = min(n_ins + *(volatile long long*)&sc->n_halo, m.cap);
         // link the new entries; CFL rates of the new active cells
         {
-            const double r = fmax(rg, link_body<N>(m, b, v.N_prev, v.N, v.g, nb, bi));
+            const double r = fmax(rg, link_body<N, T>(m, b, v.N_prev, v.N, v.g, nb, bi));
             long long zero[NDIG] = {0, 0, 0, 0, 0, 0};
             block_partial(b.part, zero, -INFINITY, r, bi);
         }

@@ -74,6 +74,12 @@ __device__ __forceinline__ StepTime step_time(const Model& m, double rate, doubl
     s.dt = dt;
     s.last = last;
     s.t_new = last ? tt : __dadd_rn(t, dt);
+    // t + dt can round onto the target although dt < tt - t: that step ends
+    // the call too (as the loop 'while t < t_target' of the method does)
+    if (!last && !(s.t_new < tt)) {
+        s.last = 1;
+        s.t_new = tt;
+    }
     return s;
 }
 
@@ -94,37 +100,26 @@ __device__ __forceinline__ unsigned outward_mask(const Model& m, const int* I) {
     return msk;
 }
 
-// Index of cell c + s1 e_j + s2 e_d (j != d) through the links (L: the link
-// row of c), -1 when it is not in the pool. For an active cell c the face
+// Index of cell c + s1 e_j + s2 e_d (j != d) through the links (L: the links
+// of c), -1 when it is not in the pool. For an active cell c the face
 // neighbour c + s1 e_j is in the pool, so its link decides; -2 only when both
 // intermediate cells are missing.
 template <int N>
-__device__ __forceinline__ int edge_by_links(const int* link, const int* L, int j, int s1, int d, int s2) {
+__device__ __forceinline__ int edge_by_links(const int* link, long long cap, const int* L, int j, int s1, int d,
+                                             int s2) {
     int a = L[2 * j + s1];
-    if (a >= 0) return __ldcg(link + (long long)a * LROW<N> + 2 * d + s2);
+    if (a >= 0) return __ldcg(link + (long long)(2 * d + s2) * cap + a);
     int b = L[2 * d + s2];
-    if (b >= 0) return __ldcg(link + (long long)b * LROW<N> + 2 * j + s1);
+    if (b >= 0) return __ldcg(link + (long long)(2 * j + s1) * cap + b);
     return -2;
 }
 
-// The 2n links of entry c (one row, loaded as 16-byte vectors where it can).
+// The 2n links of entry c (direction-major arrays: one coalesced load per
+// direction across a warp of consecutive entries).
 template <int N>
-__device__ __forceinline__ void load_links(const int* link, long long c, int* L) {
-    const int* row = link + c * LROW<N>;
-    if constexpr (LROW<N> >= 4) {
+__device__ __forceinline__ void load_links(const int* link, long long cap, long long c, int* L) {
 #pragma unroll
-        for (int q = 0; q < (2 * N + 3) / 4; ++q) {
-            const int4 v = *reinterpret_cast<const int4*>(row + 4 * q);
-            if (4 * q + 0 < 2 * N) L[4 * q + 0] = v.x;
-            if (4 * q + 1 < 2 * N) L[4 * q + 1] = v.y;
-            if (4 * q + 2 < 2 * N) L[4 * q + 2] = v.z;
-            if (4 * q + 3 < 2 * N) L[4 * q + 3] = v.w;
-        }
-    } else {
-        const int2 v = *reinterpret_cast<const int2*>(row);
-        L[0] = v.x;
-        L[1] = v.y;
-    }
+    for (int d = 0; d < 2 * N; ++d) L[d] = link[(long long)d * cap + c];
 }
 
 // Insert cell c (key k) into the table; the key must be new. slots[c]
@@ -222,6 +217,7 @@ __device__ __forceinline__ double grow_body(const Model& m, const Bufs& b, const
     DevScalars* sc = b.sc;
     const long long ncell = v.N_prev;
     const double pstar = m.thr_rel * v.maxq;
+    const Above<T> above(pstar);
     const T* Q = static_cast<const T*>(b.q[v.pb]);
     const unsigned long long* key = b.key[v.g];
     const int* link = b.link[v.g];
@@ -261,15 +257,15 @@ __device__ __forceinline__ double grow_body(const Model& m, const Bufs& b, const
             d2 = 2 * (j + 1 + rem) + ((e >> 1) & 1);
         }
         if (!((out >> d1) & 1u) || (d2 >= 0 && !((out >> d2) & 1u))) return;
-        const int a = link[(long long)cc * LROW<N> + d1];
+        const int a = link[(long long)d1 * cap + cc];
         long long e;
         if (d2 < 0) {
             e = a;
         } else if (a >= 0) {
-            e = link[(long long)a * LROW<N> + d2];
+            e = link[(long long)d2 * cap + a];
         } else {
-            const int a2 = link[(long long)cc * LROW<N> + d2];
-            e = a2 >= 0 ? link[(long long)a2 * LROW<N> + d1] : -1;
+            const int a2 = link[(long long)d2 * cap + cc];
+            e = a2 >= 0 ? link[(long long)d1 * cap + a2] : -1;
         }
         if (e >= 0) {
             make_active(e);
@@ -291,7 +287,7 @@ __device__ __forceinline__ double grow_body(const Model& m, const Bufs& b, const
         const long long c = k * 32 + (threadIdx.x & 31);
         unsigned f = 0;
         bool q = false;
-        if (k < runs && c < ncell && (double)Q[c] > pstar) {
+        if (k < runs && c < ncell && above(Q[c])) {
             f = om[c];
             q = !(f & (OM_COMPLETE | OM_GHOST)) && (f & 0xfffu);
         }
@@ -339,7 +335,7 @@ __device__ __forceinline__ void halo_body(const Model& m, const Bufs& b, const S
             x = lo + q;
         } else {
             x = b.map[q - ni];
-            if (link[(long long)x * LROW<N> + d] >= 0) continue;
+            if (link[(long long)d * cap + x] >= 0) continue;
         }
         int I[N];
         unpack_key<N>(m, key[x], I);
@@ -350,12 +346,15 @@ __device__ __forceinline__ void halo_body(const Model& m, const Bufs& b, const S
 
 // ------------------------------------------------------------------ link
 
-// Outward masks of the new entries [lo, hi) (added to the flags their inserter
-// wrote) and the largest CFL rate among the active ones.
-template <int N>
+// Face velocities and outward masks of the new entries [lo, hi) (the mask is
+// added to the flags their inserter wrote), and the largest CFL rate among the
+// active ones (Eq. 8: the same IEEE operations as cfl_rate64).
+template <int N, typename T>
 __device__ __forceinline__ double link_masks(const Model& m, const Bufs& b, long long lo, long long hi, int g,
                                               int nb, int bi) {
     const unsigned long long* key = b.key[g];
+    T* U = static_cast<T*>(b.u[g]);
+    const long long cap = m.cap;
     const long long tid = (long long)bi * blockDim.x + threadIdx.x;
     const long long nth = (long long)nb * blockDim.x;
     double rmax = 0.0;
@@ -363,8 +362,21 @@ __device__ __forceinline__ double link_masks(const Model& m, const Bufs& b, long
         int I[N];
         unpack_key<N>(m, key[c], I);
         const unsigned short f = b.om[g][c];
-        b.om[g][c] = (unsigned short)(f | outward_mask<N>(m, I));
-        if (!(f & OM_GHOST)) rmax = fmax(rmax, cfl_rate64<N>(m, I));
+        unsigned msk = 0;
+        double r = 0.0;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            int J[N];
+#pragma unroll
+            for (int k = 0; k < N; ++k) J[k] = I[k] + (k == j ? 1 : 0);
+            const double ul = face_velocity64<N>(m, I, j);
+            if (face_velocity64<N>(m, J, j) > 0.0) msk |= 1u << (2 * j + 1);
+            if (ul < 0.0) msk |= 1u << (2 * j);
+            U[j * cap + c] = (T)ul;
+            r = __dadd_rn(r, __ddiv_rn(fabs(ul), m.h[j]));
+        }
+        b.om[g][c] = (unsigned short)(f | msk);
+        if (!(f & OM_GHOST)) rmax = fmax(rmax, r);
     }
     return rmax;
 }
@@ -373,7 +385,7 @@ __device__ __forceinline__ double link_masks(const Model& m, const Bufs& b, long
 // thread and direction), write the reverse links into the neighbours, and set
 // their outward masks; returns this thread's largest CFL rate among the active
 // ones.
-template <int N>
+template <int N, typename T>
 __device__ __forceinline__ double link_body(const Model& m, const Bufs& b, long long lo, long long hi, int g, int nb,
                                              int bi) {
     const unsigned long long* key = b.key[g];
@@ -391,14 +403,14 @@ __device__ __forceinline__ double link_body(const Model& m, const Bufs& b, long 
         I[j] += s ? 1 : -1;
         unsigned long long k;
         int nb = pack_key<N>(m, I, k) ? table_find(m, b.table, k) : -1;
-        link[(long long)c * LROW<N> + dir] = nb;
-        if (nb >= 0) link[(long long)nb * LROW<N> + (2 * j + (1 - s))] = (int)c;
+        link[(long long)dir * cap + c] = nb;
+        if (nb >= 0) link[(long long)(2 * j + (1 - s)) * cap + nb] = (int)c;
     }
-    return link_masks<N>(m, b, lo, hi, g, nb, bi);
+    return link_masks<N, T>(m, b, lo, hi, g, nb, bi);
 }
 
 // Cooperative variant: W lanes probe W consecutive slots together.
-template <int N, int W>
+template <int N, int W, typename T>
 __device__ __forceinline__ double link_body_tile(const Model& m, const Bufs& b, long long lo, long long hi, int g,
                                                   int nb, int bi) {
     const unsigned long long* key = b.key[g];
@@ -418,11 +430,11 @@ __device__ __forceinline__ double link_body_tile(const Model& m, const Bufs& b, 
         unsigned long long k;
         int nb = pack_key<N>(m, I, k) ? table_find_tile<W>(m, b.table, k, tile) : -1;
         if (tile.thread_rank() == 0) {
-            link[(long long)c * LROW<N> + dir] = nb;
-            if (nb >= 0) link[(long long)nb * LROW<N> + (2 * j + (1 - s))] = (int)c;
+            link[(long long)dir * cap + c] = nb;
+            if (nb >= 0) link[(long long)(2 * j + (1 - s)) * cap + nb] = (int)c;
         }
     }
-    return link_masks<N>(m, b, lo, hi, g, nb, bi);
+    return link_masks<N, T>(m, b, lo, hi, g, nb, bi);
 }
 
 // ------------------------------------------------------------------ three-pass update
@@ -434,168 +446,143 @@ __device__ __forceinline__ T q_or_zero(const T* Q, int i) {
 
 __device__ __forceinline__ bool is_halo(const unsigned short* om, long long i) { return (om[i] & OM_GHOST) != 0; }
 
-// Cell widths, origin and step coefficients in the arithmetic type T (float
-// copies for the FP32 mode, so that nothing converts per use).
+// The entering wave of entry y in dimension d,
+//   G_d(y) = max(u_lo, 0) (P_y - P_{y-e_d}) + min(u_hi, 0) (P_{y+e_d} - P_y),
+// u_lo, u_hi the velocities at its lower and upper d-face (the upper one is the
+// lower one of the neighbour above; a missing neighbour above of a halo cell
+// leaves both P at 0), with the jump across the lower face in wlo.
 template <int N, typename T>
-struct Geo {
-    T h[N], x0[N], ch[N], dth[N];
-    __device__ __forceinline__ Geo(const Model& m, const StepView& v) {
-#pragma unroll
-        for (int k = 0; k < N; ++k) {
-            h[k] = sizeof(T) == 4 ? (T)m.hf[k] : (T)m.h[k];
-            x0[k] = sizeof(T) == 4 ? (T)m.x0f[k] : (T)m.x0[k];
-            ch[k] = (T)v.ch[k];
-            dth[k] = (T)v.dth[k];
-        }
-    }
-    __device__ __forceinline__ void centre(const int* I, T* xc) const {
-#pragma unroll
-        for (int k = 0; k < N; ++k) xc[k] = x0[k] + (T)I[k] * h[k];
-    }
-};
+__device__ __forceinline__ T wave_of(const T* Q, const T* U, long long cap, const int* L, long long y, T Py, int d,
+                                     T& wlo) {
+    const int dn = L[2 * d], up = L[2 * d + 1];
+    const T Pm = q_or_zero<T>(Q, dn);
+    const T Pp = q_or_zero<T>(Q, up);
+    const T ul = U[d * cap + y];
+    const T uh = up >= 0 ? U[d * cap + up] : (T)0;
+    wlo = Py - Pm;
+    return fma(neg_part(uh), Pp - Py, pos_part(ul) * wlo);
+}
 
-// Pass 1, one work item per (entry, dimension d) of the entries [0, ncell)
-// (active and halo): the lower-face velocity u_d and the entering wave
-//   G_d = max(u_d, 0) (P - P_{-e_d}) + min(u_{d, upper}, 0) (P_{+e_d} - P).
-// Entries added by this step's grow and halo phases are left out: they have
-// p = 0, and their waves are formed on the spot (waves_of). Runs beside grow:
-// a cell that grow or halo adds has p = 0 like the missing cell it replaces,
-// so these waves do not change.
+// Pass 1, one thread per entry c of [0, ncell) (active and halo), all
+// dimensions d: the jump wl[d] = P - P_{-e_d}, the entering wave wg[d] and
+// tg = sum_d wg[d] / (2 h_d). Entries added by this step's grow and halo phases
+// are left out: they have p = 0, and their waves are formed on the spot. Runs
+// beside grow: a cell that grow or halo adds has p = 0 like the missing cell it
+// replaces, so these waves do not change.
 template <int N, int DYN, typename T>
 __device__ __forceinline__ void waves_body(const Model& m, const Bufs& b, const StepView& v, long long ncell) {
     const T* Q = static_cast<const T*>(b.q[v.pb]);
-    const unsigned long long* key = b.key[v.g];
     const int* link = b.link[v.g];
-    T* wu = static_cast<T*>(b.wv_u);
-    T* wg = static_cast<T*>(b.wv_g);
-    const Geo<N, T> geo(m, v);
-    const long long items = ncell * N;
-    for (WarpRuns wr(items, v.nb, v.bi); wr.next();) {
-        const long long it = wr.c;
-        if (it >= items) continue;
-        const long long c = it / N;
-        const int d = (int)(it - c * N);
-        int I[N];
-        unpack_key<N>(m, key[c], I);
+    const T* U = static_cast<const T*>(b.u[v.g]);
+    T* wl = static_cast<T*>(b.wl);
+    T* wg = static_cast<T*>(b.wg);
+    T* tg = static_cast<T*>(b.tg);
+    const long long cap = m.cap;
+    for (WarpRuns wr(ncell, v.nb, v.bi); wr.next();) {
+        const long long c = wr.c;
+        if (c >= ncell) continue;
+        int L[2 * N];
+        load_links<N>(link, cap, c, L);
         const T P0 = Q[c];
-        const T Pm = q_or_zero<T>(Q, link[c * LROW<N> + 2 * d]);
-        const T Pp = q_or_zero<T>(Q, link[c * LROW<N> + 2 * d + 1]);
-        T xc[N];
-        geo.centre(I, xc);
-        T ul = (T)0, uh = (T)0;
+        T t = (T)0;
 #pragma unroll
-        for (int dd = 0; dd < N; ++dd)
-            if (dd == d) {
-                ul = vel_at<N, DYN, T>(m, xc, geo.h, -1, 0, dd, -1);
-                uh = vel_at<N, DYN, T>(m, xc, geo.h, -1, 0, dd, +1);
-            }
-        wu[c * WROW<N> + d] = ul;
-        wg[c * WROW<N> + d] = fmax(ul, (T)0) * (P0 - Pm) + fmin(uh, (T)0) * (Pp - P0);
+        for (int d = 0; d < N; ++d) {
+            T wlo;
+            const T G = wave_of<N, T>(Q, U, cap, L, c, P0, d, wlo);
+            wl[d * cap + c] = wlo;
+            wg[d * cap + c] = G;
+            t = fma(G, (T)m.inv_2h[d], t);
+        }
+        tg[c] = t;
     }
 }
 
-// sum_{d != j} dt/(2 h_d) G_d(Y) for the pool entry y = Y = c + s e_j (s = -1
-// or 0; xc is the centre of c), formed on the spot from Y's links; 0 when Y is
-// not in the pool (a cell without a key: it and its neighbours have p = 0).
-template <int N, int DYN, typename T>
-__device__ __forceinline__ T waves_of(const Model& m, const T* Q, const int* link, long long y, const T* xc,
-                                      const Geo<N, T>& geo, int j, int s) {
-    if (y < 0) return (T)0;
-    const T PY = Q[y];
+// sum_{d != j} G_d(y) / (2 h_d) of a new pool entry y (p = 0, no pass-1 values),
+// formed on the spot from its links.
+template <int N, typename T>
+__device__ __forceinline__ T waves_new(const Model& m, const T* Q, const T* U, const int* link, long long y, int j) {
+    const long long cap = m.cap;
+    int L[2 * N];
+    load_links<N>(link, cap, y, L);
     T S = (T)0;
 #pragma unroll
     for (int d = 0; d < N; ++d) {
         if (d == j) continue;
-        const T Pm = q_or_zero<T>(Q, link[y * LROW<N> + 2 * d]);
-        const T Pp = q_or_zero<T>(Q, link[y * LROW<N> + 2 * d + 1]);
-        const T ul = vel_at<N, DYN, T>(m, xc, geo.h, s ? j : -1, s, d, -1);
-        const T uh = vel_at<N, DYN, T>(m, xc, geo.h, s ? j : -1, s, d, +1);
-        S += geo.ch[d] * (fmax(ul, (T)0) * (PY - Pm) + fmin(uh, (T)0) * (Pp - PY));
+        T wlo;
+        S = fma(wave_of<N, T>(Q, U, cap, L, y, (T)0, d, wlo), (T)m.inv_2h[d], S);
     }
     return S;
 }
 
-// Pass 2, one work item per (entry c, dimension j): the flux through the lower
+// Pass 2, one thread per entry c, all dimensions j: the flux through the lower
 // j-face of c (Eq. 7, the corrections of Algorithm 1 gathered onto the face,
 // the limited HR term), for every face with an active cell on at least one
 // side. The corrections that Algorithm 1 scatters onto face (X, j) add up to
-//   -u_j(X) sum_{d != j} dt/(2 h_d) G_d(Y),  Y the cell upwind of the face.
-// The upper face of an active cell is the lower face of its upper neighbour,
-// which is in the pool (active or halo).
+//   -u_j(X) dt sum_{d != j} G_d(Y) / (2 h_d),  Y the cell upwind of the face,
+// and sum_{d != j} = tg(Y) - G_j(Y) / (2 h_j). The upper face of an active cell
+// is the lower face of its upper neighbour, which is in the pool (active or
+// halo).
 template <int N, int DYN, typename T>
 __device__ __forceinline__ void faces_body(const Model& m, const Bufs& b, const StepView& v) {
     const long long ncell = v.N;
     const long long nold = v.N_prev;
+    const long long cap = m.cap;
     const T* Q = static_cast<const T*>(b.q[v.pb]);
-    const unsigned long long* key = b.key[v.g];
     const int* link = b.link[v.g];
     const unsigned short* om = b.om[v.g];
-    const T* wu = static_cast<const T*>(b.wv_u);
-    const T* wg = static_cast<const T*>(b.wv_g);
+    const T* U = static_cast<const T*>(b.u[v.g]);
+    const T* wl = static_cast<const T*>(b.wl);
+    const T* wg = static_cast<const T*>(b.wg);
+    const T* tg = static_cast<const T*>(b.tg);
     T* fl = static_cast<T*>(b.fl);
     const int lim = m.limiter;
-    const Geo<N, T> geo(m, v);
-    const long long items = ncell * N;
-    for (WarpRuns wr(items, v.nb, v.bi); wr.next();) {
-        const long long it = wr.c;
-        if (it >= items) continue;
-        const long long c = it / N;
-        const int j = (int)(it - c * N);
-        const int Llo = link[c * LROW<N> + 2 * j];
-        if (is_halo(om, c) && (Llo < 0 || is_halo(om, Llo))) continue;  // no active cell on this face
+    const T dt = (T)v.dt;
+    for (WarpRuns wr(ncell, v.nb, v.bi); wr.next();) {
+        const long long c = wr.c;
+        if (c >= ncell) continue;
+        const bool halo_c = is_halo(om, c);
+        const bool old_c = c < nold;
+        int L[2 * N];
+        load_links<N>(link, cap, c, L);
         const T P0 = Q[c];
-        const T PL = q_or_zero<T>(Q, Llo);
-        T dthj = (T)0;
 #pragma unroll
-        for (int k = 0; k < N; ++k)
-            if (k == j) dthj = geo.dth[k];
-        T xc[N];
-        bool have_pos = false;
-        auto pos = [&]() {
-            if (!have_pos) {
-                int I[N];
-                unpack_key<N>(m, key[c], I);
-                geo.centre(I, xc);
-                have_pos = true;
-            }
-        };
-        T u = (T)0;
-        if (c < nold) {
-            u = wu[c * WROW<N> + j];
-        } else {
-            pos();
-#pragma unroll
-            for (int dd = 0; dd < N; ++dd)
-                if (dd == j) u = vel_at<N, DYN, T>(m, xc, geo.h, -1, 0, dd, -1);
-        }
-        T f = (T)0;
-        if (u != (T)0) {
-            f = fmax(u, (T)0) * PL + fmin(u, (T)0) * P0;  // Eq. 7
-            // transverse sum of the cell upwind of the face
-            const long long y = u > (T)0 ? (long long)Llo : c;
-            T S = (T)0;
-            if (y >= 0 && y < nold) {
-#pragma unroll
-                for (int d = 0; d < N; ++d)
-                    if (d != j) S += geo.ch[d] * wg[y * WROW<N> + d];
-            } else {
-                pos();
-                S = waves_of<N, DYN, T>(m, Q, link, y, xc, geo, j, u > (T)0 ? -1 : 0);
-            }
-            f -= u * S;  // Algorithm 1, gathered
-            const T W = P0 - PL;
-            if (lim != LIM_NONE && W != (T)0) {
-                T Wup;
-                if (u > (T)0) {
-                    Wup = PL - q_or_zero<T>(Q, Llo >= 0 ? link[(long long)Llo * LROW<N> + 2 * j] : -1);
+        for (int j = 0; j < N; ++j) {
+            const int Llo = L[2 * j];
+            if (halo_c && (Llo < 0 || is_halo(om, Llo))) continue;  // no active cell on this face
+            const T u = U[j * cap + c];
+            T f = (T)0;
+            if (gt0(u) || lt0(u)) {
+                const bool up = gt0(u);  // the flow crosses the face upwards: the upwind cell is Llo
+                const T W = old_c ? wl[j * cap + c] : P0 - q_or_zero<T>(Q, Llo);
+                // transverse sum of the cell upwind of the face
+                const long long y = up ? (long long)Llo : c;
+                T S;
+                if (y < nold) {
+                    S = fma(-(T)m.inv_2h[j], wg[j * cap + y], tg[y]);
                 } else {
-                    Wup = q_or_zero<T>(Q, link[c * LROW<N> + 2 * j + 1]) - P0;
+                    S = waves_new<N, T>(m, Q, U, link, y, j);
                 }
-                const T au = fabs(u);
-                f += (T)0.5 * au * ((T)1 - dthj * au) * limited_wave<T>(lim, W, Wup);
+                // Eq. 7 (donor cell) and the corrections of Algorithm 1, gathered
+                f = u * fma(-dt, S, up ? q_or_zero<T>(Q, Llo) : P0);
+                if (lim != LIM_NONE && (gt0(W) || lt0(W))) {
+                    T Wup;
+                    if (up) {  // jump across the lower face of Llo
+                        if (Llo < nold) {
+                            Wup = wl[j * cap + Llo];
+                        } else {
+                            Wup = q_or_zero<T>(Q, Llo) - q_or_zero<T>(Q, link[(long long)(2 * j) * cap + Llo]);
+                        }
+                    } else {  // jump across the upper face of c
+                        const int Lup = L[2 * j + 1];
+                        Wup = (Lup >= 0 && Lup < nold) ? wl[j * cap + Lup] : q_or_zero<T>(Q, Lup) - P0;
+                    }
+                    // the limited high-resolution term 1/2 |u| (1 - dt |u| / h_j) phi W
+                    const T au = abs_bits(u);
+                    f = fma(half_nonneg(au) * fma(-(T)v.dth[j], au, (T)1), limited_wave<T>(lim, W, Wup), f);
+                }
             }
+            fl[j * cap + c] = f;
         }
-        fl[c * WROW<N> + j] = f;
     }
 }
 
@@ -606,6 +593,7 @@ template <int N, typename T>
 __device__ __forceinline__ void apply_body(const Model& m, const Bufs& b, const StepView& v, long long (&dacc)[NDIG],
                                            double& mx, int& err) {
     const long long ncell = v.N;
+    const long long cap = m.cap;
     const T* Q = static_cast<const T*>(b.q[v.pb]);
     T* Qn = static_cast<T*>(b.q[v.pb ^ 1]);
     const int* link = b.link[v.g];
@@ -624,13 +612,13 @@ __device__ __forceinline__ void apply_body(const Model& m, const Bufs& b, const 
             continue;
         }
         int L[2 * N];
-        load_links<N>(link, c, L);
+        load_links<N>(link, cap, c, L);
         T upd = (T)0;
 #pragma unroll
         for (int j = 0; j < N; ++j) {
             const int up = L[2 * j + 1];
-            const T Fhi = up >= 0 ? fl[(long long)up * WROW<N> + j] : (T)0;
-            upd += dth[j] * (Fhi - fl[c * WROW<N> + j]);
+            const T Fhi = up >= 0 ? fl[j * cap + up] : (T)0;
+            upd = fma(dth[j], Fhi - fl[j * cap + c], upd);
         }
         const T qn = (Q[c] - upd) * scale;
         Qn[c] = qn;
@@ -646,11 +634,12 @@ __device__ __forceinline__ void apply_body(const Model& m, const Bufs& b, const 
 template <typename T>
 __device__ __forceinline__ void prune_mark_body(const Model& m, const Bufs& b, const StepView& v) {
     const double pstar = m.thr_rel * v.maxq;
+    const Above<T> above(pstar);
     const T* Q = static_cast<const T*>(b.q[v.pb]);
     const unsigned short* om = b.om[v.g];
     for (WarpRuns r(v.N, v.nb, v.bi); r.next();) {
         const long long c = r.c;
-        if (c < v.N) b.keep[c] = !is_halo(om, c) && (double)Q[c] > pstar;
+        if (c < v.N) b.keep[c] = !is_halo(om, c) && above(Q[c]);
     }
 }
 
@@ -659,6 +648,7 @@ __device__ __forceinline__ void prune_mark_body(const Model& m, const Bufs& b, c
 template <int N, typename T>
 __device__ __forceinline__ void prune_scatter_body(const Model& m, const Bufs& b, const StepView& v) {
     const double pstar = m.thr_rel * v.maxq;
+    const Above<T> above(pstar);
     const T* Q = static_cast<const T*>(b.q[v.pb]);
     const int* link = b.link[v.g];
     const unsigned short* om = b.om[v.g];
@@ -667,11 +657,11 @@ __device__ __forceinline__ void prune_scatter_body(const Model& m, const Bufs& b
         const long long c = r.c;
         if (c >= v.N) continue;
         const unsigned f = om[c];
-        if ((f & OM_GHOST) || !((double)Q[c] > pstar)) continue;
+        if ((f & OM_GHOST) || !above(Q[c])) continue;
         const unsigned out = f & 0xfffu;
         if (!out) continue;
         int L[2 * N];
-        load_links<N>(link, c, L);
+        load_links<N>(link, cap, c, L);
 #pragma unroll
         for (int d = 0; d < 2 * N; ++d)
             if (((out >> d) & 1u) && L[d] >= 0) b.keep[L[d]] = 1;
@@ -681,7 +671,7 @@ __device__ __forceinline__ void prune_scatter_body(const Model& m, const Bufs& b
 #pragma unroll
             for (int d2 = 0; d2 < 2 * N; ++d2) {
                 if ((d2 >> 1) <= (d1 >> 1) || !((out >> d2) & 1u)) continue;
-                const int e = edge_by_links<N>(link, L, d1 >> 1, d1 & 1, d2 >> 1, d2 & 1);
+                const int e = edge_by_links<N>(link, cap, L, d1 >> 1, d1 & 1, d2 >> 1, d2 & 1);
                 if (e >= 0) b.keep[e] = 1;
             }
         }
@@ -729,7 +719,7 @@ __device__ __forceinline__ void prune_count_body(const Model& m, const Bufs& b, 
             st = 1;
         } else {
             int L[2 * N];
-            load_links<N>(link, c, L);
+            load_links<N>(link, cap, c, L);
 #pragma unroll
             for (int d = 0; d < 2 * N; ++d)
                 if (L[d] >= 0 && b.keep[L[d]] && !is_halo(om, L[d])) st = 2;
@@ -786,6 +776,15 @@ __device__ __forceinline__ Survivors block_offsets(const Bufs& b, int nb, int bi
     return r;
 }
 
+// The face velocities of entry c (generation g) move to nc of the other generation.
+template <int N, typename T>
+__device__ __forceinline__ void copy_velocities(const Model& m, const Bufs& b, int g, long long c, long long nc) {
+    const T* U = static_cast<const T*>(b.u[g]);
+    T* Uo = static_cast<T*>(b.u[g ^ 1]);
+#pragma unroll
+    for (int j = 0; j < N; ++j) Uo[j * m.cap + nc] = U[j * m.cap + c];
+}
+
 // Stream compaction of the survivors in storage order into the other buffer
 // set: the kept active cells at [0, total_a), the halo cells after them;
 // map[c] = new index or -1. Values of active cells are rescaled by an exact
@@ -821,6 +820,7 @@ __device__ __forceinline__ void prune_compact_body(const Model& m, const Bufs& b
                 keyo[nc] = k;
                 Qo[nc] = val;
                 omo[nc] = (unsigned short)(om[c] & 0xfffu);
+                copy_velocities<N, T>(m, b, v.g, c, nc);
                 b.map[c] = (int)nc;
                 acc_add(d, (double)val, err);
                 mx = fmax(mx, (double)val);
@@ -832,6 +832,7 @@ __device__ __forceinline__ void prune_compact_body(const Model& m, const Bufs& b
                 keyo[nc] = k;
                 Qo[nc] = (T)0;
                 omo[nc] = (unsigned short)((om[c] & 0xfffu) | OM_GHOST);
+                copy_velocities<N, T>(m, b, v.g, c, nc);
                 b.map[c] = (int)nc;
             } else {
                 b.map[c] = -1;
@@ -865,6 +866,7 @@ __device__ __forceinline__ void prune_compact_sorted_body(const Model& m, const 
         const long long nc = b.map[c];
         const unsigned long long k = key[c];
         keyo[nc] = k;
+        copy_velocities<N, T>(m, b, v.g, c, nc);
         if (st == 1) {
             const T val = (T)((double)Q[c] * s2);
             Qo[nc] = val;
@@ -894,9 +896,9 @@ __device__ __forceinline__ void prune_relink_body(const Model& m, const Bufs& b,
         const int nc = b.map[c];
         if (nc < 0) continue;
         int L[2 * N];
-        load_links<N>(link, c, L);
+        load_links<N>(link, cap, c, L);
 #pragma unroll
-        for (int d = 0; d < 2 * N; ++d) linko[(long long)nc * LROW<N> + d] = L[d] >= 0 ? b.map[L[d]] : -1;
+        for (int d = 0; d < 2 * N; ++d) linko[(long long)d * cap + nc] = L[d] >= 0 ? b.map[L[d]] : -1;
         table_insert_new(m, b, keyo[nc], nc, b.slot[v.g ^ 1]);
     }
 }

@@ -27,6 +27,7 @@ GBEES_DYN_CONSTANT, GBEES_DYN_LINEAR, GBEES_DYN_LORENZ63, GBEES_DYN_LORENZ63_SHI
 GBEES_LIM_MC, GBEES_LIM_NONE, GBEES_LIM_LW = range(3)
 GBEES_FP64, GBEES_FP32 = 0, 1
 GBEES_LAUNCH_AUTO, GBEES_LAUNCH_PERSISTENT, GBEES_LAUNCH_GRAPH, GBEES_LAUNCH_DIRECT = range(4)
+GBEES_ORDER_KEY, GBEES_ORDER_MORTON, GBEES_ORDER_NONE = range(3)
 
 
 class gbees_config(ctypes.Structure):
@@ -45,6 +46,7 @@ class gbees_config(ctypes.Structure):
         ("max_cells", ctypes.c_int64),
         ("table_factor", ctypes.c_double),
         ("launch_mode", ctypes.c_int32),
+        ("storage_order", ctypes.c_int32),
     ]
 
 
@@ -95,6 +97,7 @@ _SIGNATURES = {
     "gbees_moments": (ctypes.c_int, [_vp, _P(_d), _P(_d)]),
     "gbees_get_stats": (ctypes.c_int, [_vp, _P(gbees_stats)]),
     "gbees_get_status": (ctypes.c_int, [_vp]),
+    "gbees_set_wait_limit": (ctypes.c_int, [_vp, _i64, _i32]),
     "gbees_profile_control": (ctypes.c_int, [_vp, _i32, _i32]),
     "gbees_profile_read": (ctypes.c_int, [_vp, _P(gbees_profile)]),
     "gbees_last_error": (ctypes.c_char_p, [_vp]),
@@ -177,6 +180,10 @@ def gbees_get_stats(ctx: int, stats: gbees_stats) -> int:
     return _f("gbees_get_stats")(_vp(ctx), ctypes.byref(stats))
 
 
+def gbees_set_wait_limit(ctx: int, spins: int, extra_arrivals: int = 0) -> int:
+    return int(_f("gbees_set_wait_limit")(_vp(ctx), int(spins), int(extra_arrivals)))
+
+
 def gbees_get_status(ctx: int) -> int:
     return _f("gbees_get_status")(_vp(ctx))
 
@@ -256,7 +263,8 @@ class Stats:
 def make_config(n: int, dynamics: int, params: Sequence[float], h: Sequence[float], x0: Sequence[float],
                 thr_rel: float = 1e-7, cfl: float = 0.9, prune_interval: int = 20, precision: int = GBEES_FP64,
                 limiter: int = GBEES_LIM_MC, max_cells: int = 1 << 20, table_factor: float = 2.0,
-                probe_width: int = 1, launch_mode: int = GBEES_LAUNCH_AUTO) -> gbees_config:
+                probe_width: int = 1, launch_mode: int = GBEES_LAUNCH_AUTO,
+                storage_order: int = GBEES_ORDER_KEY) -> gbees_config:
     c = gbees_config()
     c.n, c.dynamics = int(n), int(dynamics)
     for k, v in enumerate(params):
@@ -268,6 +276,7 @@ def make_config(n: int, dynamics: int, params: Sequence[float], h: Sequence[floa
     c.prune_interval, c.precision, c.limiter = int(prune_interval), int(precision), int(limiter)
     c.probe_width, c.max_cells, c.table_factor = int(probe_width), int(max_cells), float(table_factor)
     c.launch_mode = int(launch_mode)
+    c.storage_order = int(storage_order)
     return c
 
 
@@ -424,8 +433,9 @@ def propagate_batch(grids: Sequence["Grid"], t_end: Sequence[float], max_steps: 
 
 
 def grid_for_workload(w, precision: int = GBEES_FP64, max_cells: int = 1 << 20, device: str = "cuda:0",
-                      probe_width: int = 1, table_factor: float = 2.0, launch_mode: int = GBEES_LAUNCH_AUTO) -> Grid:
+                      probe_width: int = 1, table_factor: float = 2.0, launch_mode: int = GBEES_LAUNCH_AUTO,
+                      storage_order: int = GBEES_ORDER_KEY) -> Grid:
     """A Grid configured for a paper_2508_13986_gb300.workloads.Workload."""
     cfg = make_config(w.n, w.dynamics, w.params, w.h, w.x0, w.thr_rel, w.cfl, w.prune_interval, precision,
-                      w.limiter, max_cells, table_factor, probe_width, launch_mode)
+                      w.limiter, max_cells, table_factor, probe_width, launch_mode, storage_order)
     return Grid(cfg, device)

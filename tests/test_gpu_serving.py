@@ -1,7 +1,13 @@
 """The continuous-batching request loop: each result equals the same request
-served alone; admission respects the memory budget; a timed stream completes."""
+served alone and the oracle's run of that request; admission respects the
+memory budget; a timed stream completes."""
+import math
+
 import numpy as np
 import pytest
+
+from oracle.oracle import Oracle
+from parity_helpers import FP64_L1
 
 from paper_2508_13986_gb300 import gbees
 from paper_2508_13986_gb300 import workloads as W
@@ -34,6 +40,34 @@ def test_each_result_is_the_same_alone_and_in_the_mix(prec):
         assert a.steps == b.steps and a.cell_updates == b.cell_updates
         assert np.array_equal(a.idx, b.idx) and np.array_equal(a.p, b.p)
         assert np.array_equal(a.mean, b.mean) and np.array_equal(a.cov, b.cov)
+
+
+def test_served_results_match_the_oracle_grid_by_grid():
+    """A mixed stream (Lorenz '63 and Lorenz '96 requests, each with its
+    measurement updates) served in batched FP64 rounds: every request's final
+    density equals the oracle's run of that request alone (identical active
+    set, L1 within the FP64 bar, the same steps)."""
+    stream = small_stream(8, seed=24)
+    assert {w.n for _, w in stream} == {3, 6}
+    res = sorted(Server(precision=gbees.GBEES_FP64, realtime=False, keep_density=True, round_steps=5).run(stream),
+                 key=lambda r: r.rid)
+    assert len(res) == len(stream)
+    for (_, w), r in zip(stream, res):
+        assert r.error is None
+        o = Oracle(w.n, w.dynamics, w.params, w.h, w.x0, w.thr_rel, w.cfl, w.prune_interval, w.limiter)
+        o.init_gaussian(w.mean, w.cov)
+        steps = 0
+        for t, meas in w.segments():
+            steps += o.propagate(t).steps
+            if meas is not None:
+                o.correct_gaussian(meas.y, meas.R, meas.H_idx)
+        oi, op = o.read_cells()
+        order = np.lexsort(r.idx.T[::-1])
+        gi, gp = r.idx[order], r.p[order]
+        assert r.steps == steps
+        assert np.array_equal(gi, oi), (w.name, len(gi), len(oi))
+        l1 = math.prod(w.h) * math.fsum(np.abs(gp - op).tolist())
+        assert l1 <= FP64_L1, (w.name, l1)
 
 
 def test_admission_respects_the_memory_budget():
