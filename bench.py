@@ -168,18 +168,19 @@ class ClockSampler:
 
 def auto_max_cells(w, precision, dev) -> int:
     """Pool capacity for a single-grid workload: 24 times its initial set
-    (growth measured up to 18x over the 6-D horizons, with the halo), a power
-    of two, at least 2^22, and halved while the workspace would take more than
-    80 % of the device memory."""
+    (growth measured up to 18x over the 6-D h = 0.25 horizon, with the halo), a
+    power of two, at least 2^24 (coarser grids grow more in relative terms),
+    and halved while the workspace would take more than 80 % of the device
+    memory."""
     import torch
 
     from paper_2508_13986_gb300 import gbees, workloads
 
-    cap = 1 << 22
+    cap = 1 << 24
     while cap < 24 * workloads.initial_cells_estimate(w):
         cap <<= 1
     total = torch.cuda.get_device_properties(dev).total_memory
-    while cap > (1 << 22):
+    while cap > (1 << 24):
         cfg = gbees.make_config(w.n, w.dynamics, w.params, w.h, w.x0, w.thr_rel, w.cfl, w.prune_interval, precision,
                                 w.limiter, cap)
         if gbees.gbees_workspace_bytes(cfg) <= 0.8 * total:

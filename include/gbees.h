@@ -113,12 +113,14 @@ typedef struct {
 /* Storage order of the pool entries after a prune of a grid of more than
  * 2^18 entries (smaller grids keep their order; the results never depend on
  * it, only the speed of the neighbour gathers does):
- *   KEY     lexicographic order of the cell indices (dimension 0 slowest), so
- *           that the neighbours of a warp's consecutive cells in any dimension
- *           are consecutive too
- *   MORTON  Morton (Z-curve) order of the cell indices
- *   NONE    the survivors keep their order (active cells first, then halo) */
-enum { GBEES_ORDER_KEY = 0, GBEES_ORDER_MORTON = 1, GBEES_ORDER_NONE = 2 };
+ *   KEY        active cells first, then the halo cells, each in lexicographic
+ *              order of the cell indices (dimension 0 slowest), so that the
+ *              neighbours of a warp's consecutive cells in any dimension are
+ *              consecutive too
+ *   MORTON     the same split, each part in Morton (Z-curve) order
+ *   NONE       the survivors keep their order (active cells first, then halo)
+ *   KEY_MIXED  active and halo cells interleaved in lexicographic order */
+enum { GBEES_ORDER_KEY = 0, GBEES_ORDER_MORTON = 1, GBEES_ORDER_NONE = 2, GBEES_ORDER_KEY_MIXED = 3 };
 
 /* Launch modes of gbees_propagate (all give bit-identical results):
  *   AUTO        persistent kernel while the grid is small, CUDA graph beyond
@@ -196,6 +198,14 @@ int gbees_propagate(gbees_ctx* ctx, double t_end, gbees_stats* stats);
 size_t gbees_batch_workspace_bytes(int32_t count);
 int gbees_batch_propagate(gbees_ctx* const* ctxs, int32_t count, const double* t_end, int64_t max_steps,
                           void* d_scratch, size_t scratch_bytes, gbees_stats* stats);
+
+/* Blocks of a batched launch whose first context is ctx, at most (0, the
+ * default: as many as the GPU holds resident). Batches issued concurrently on
+ * different streams (one per model family of a serving loop) share the GPU
+ * when each is capped to its part: a team launch is cooperative and waits
+ * until all its blocks fit. A batch with more grids than blocks runs in the
+ * queue form. max_blocks >= 0. */
+int gbees_set_batch_blocks(gbees_ctx* ctx, int32_t max_blocks);
 
 /* Bayesian measurement update (Eq. 4) with the Gaussian likelihood
  * exp(-1/2 (y - x_H)^T R^{-1} (y - x_H)) of m measured components

@@ -76,6 +76,11 @@ struct gbees_ctx {
     bool kern_ok = false;
     int persist_grid = 0;
     long long persist_max_cells = 1ll << 18;
+    int batch_blocks = 0;  // blocks of a batched launch led by this context at most (0: all resident)
+    // blocks of the step kernels of the graph and direct paths: as many as the
+    // GPU holds resident for each (SMs x blocks per SM by occupancy), so that one
+    // wave covers the grid-stride loops: pre[0..npre), link, post[0..npost)
+    int pre_grid[2] = {0, 0}, link_grid = 0, post_grid[3] = {0, 0, 0};
     // device time of every persistent launch (always measured: few launches)
     cudaEvent_t pev[2] = {nullptr, nullptr};
     ~gbees_ctx() {
@@ -98,8 +103,8 @@ constexpr size_t ALIGN = 256;
 size_t align_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
 
 struct Layout {
-    size_t sc, blk, part, sorthist, key[2], q[2], link[2], om[2], slot[2], u[2], keep, map, table, wl, wg, tg, fl,
-        total;
+    size_t sc, blk, part, sorthist, key[2], q[2], link[2], om[2], slot[2], u[2], rate[2], keep, map, table, wl, wg,
+        tg, fl, total;
     unsigned long long slots;
 };
 
@@ -141,7 +146,8 @@ bool config_ok(const gbees_config* c, std::string* why) {
     if (c->max_cells < 1 || c->max_cells > 0x7fffffffll) return fail("max_cells must be in 1..2^31-1");
     if (!(c->table_factor == 0.0 || c->table_factor >= 1.25)) return fail("table_factor must be 0 or >= 1.25");
     if (c->launch_mode < GBEES_LAUNCH_AUTO || c->launch_mode > GBEES_LAUNCH_DIRECT) return fail("unknown launch_mode");
-    if (c->storage_order < GBEES_ORDER_KEY || c->storage_order > GBEES_ORDER_NONE) return fail("unknown storage_order");
+    if (c->storage_order < GBEES_ORDER_KEY || c->storage_order > GBEES_ORDER_KEY_MIXED)
+        return fail("unknown storage_order");
     return true;
 }
 
@@ -175,6 +181,7 @@ bool make_layout(const gbees_config* c, Layout* L) {
     // update, storage type, n values per entry (one for tg)
     const size_t rows = S * (size_t)c->n * cap;
     for (int g = 0; g < 2; ++g) L->u[g] = take(rows);
+    for (int g = 0; g < 2; ++g) L->rate[g] = take(8 * cap);
     L->wl = take(rows);
     L->wg = take(rows);
     L->tg = take(S * cap);
@@ -238,6 +245,7 @@ void bind_context(gbees_ctx* ctx, const gbees_config* cfg, const Layout& L, void
     b.map = (int*)(base + L.map);
     b.table = (Slot*)(base + L.table);
     for (int g = 0; g < 2; ++g) b.u[g] = (void*)(base + L.u[g]);
+    for (int g = 0; g < 2; ++g) b.rate[g] = (double*)(base + L.rate[g]);
     b.wl = (void*)(base + L.wl);
     b.wg = (void*)(base + L.wg);
     b.tg = (void*)(base + L.tg);
@@ -392,7 +400,21 @@ void* link_kernel(int probe_width) {
 template <int N, typename T>
 void launch_link(gbees_ctx* ctx, int step) {
     void* args[] = {&ctx->m, &ctx->b, &step};
-    cudaLaunchKernel(link_kernel<N, T>(ctx->m.probe_width), dim3(ctx->grid), dim3(THREADS), args, 0, ctx->stream);
+    const int G = ctx->link_grid > 0 ? ctx->link_grid : ctx->grid;
+    cudaLaunchKernel(link_kernel<N, T>(ctx->m.probe_width), dim3(G), dim3(THREADS), args, 0, ctx->stream);
+}
+
+// Blocks of a step kernel f: a resident wave (SMs x blocks per SM), and at
+// least the context's fixed grid (latency-bound kernels with few resident
+// blocks, such as the hashtable probes of the link phase, gain from a second
+// wave that overlaps the first one's tail).
+int resident_grid(gbees_ctx* ctx, const void* f, int sms) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, THREADS, 0) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        return ctx->grid;
+    }
+    return std::min(GRID_MAX, std::max(ctx->grid, sms * per_sm));
 }
 
 void resolve_update_kernels(gbees_ctx* ctx) {
@@ -400,16 +422,26 @@ void resolve_update_kernels(gbees_ctx* ctx) {
     ctx->kern_ok = update_kernels(ctx->m, ctx->cfg.precision == GBEES_FP32, &ctx->kern);
     int dev = 0, sms = 0, per_sm = 0;
     if (ctx->kern_ok && cudaGetDevice(&dev) == cudaSuccess &&
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ctx->kern.persist, THREADS, 0) == cudaSuccess &&
-        per_sm >= 1)
-        ctx->persist_grid = std::min(GRID_MAX, sms);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ctx->kern.persist, THREADS, 0) == cudaSuccess &&
+            per_sm >= 1)
+            ctx->persist_grid = std::min(GRID_MAX, sms);
+        for (int i = 0; i < ctx->kern.npre; ++i) ctx->pre_grid[i] = resident_grid(ctx, ctx->kern.pre[i], sms);
+        for (int i = 0; i < ctx->kern.npost; ++i) ctx->post_grid[i] = resident_grid(ctx, ctx->kern.post[i], sms);
+        with_nt(ctx, [&](auto NN, auto TT) {
+            constexpr int N = decltype(NN)::value;
+            ctx->link_grid = resident_grid(ctx, link_kernel<N, decltype(TT)>(ctx->m.probe_width), sms);
+        });
+    }
     cudaGetLastError();
 }
 
-void launch_list(gbees_ctx* ctx, void* const* f, int nf) {
+void launch_list(gbees_ctx* ctx, void* const* f, const int* grids, int nf) {
     void* args[] = {&ctx->m, &ctx->b};
-    for (int i = 0; i < nf; ++i) cudaLaunchKernel(f[i], dim3(ctx->grid), dim3(THREADS), args, 0, ctx->stream);
+    for (int i = 0; i < nf; ++i) {
+        const int G = grids[i] > 0 ? grids[i] : ctx->grid;
+        cudaLaunchKernel(f[i], dim3(G), dim3(THREADS), args, 0, ctx->stream);
+    }
 }
 
 // The prune of Algorithm 3 (directional marking, status, compaction, relink,
@@ -481,11 +513,11 @@ void launch_step(gbees_ctx* ctx) {
     resolve_update_kernels(ctx);
     {
         Phase ph(ctx, GBEES_PHASE_GROW, 1);
-        launch_list(ctx, ctx->kern.pre, 1);
+        launch_list(ctx, ctx->kern.pre, ctx->pre_grid, 1);
     }
     {
         Phase ph(ctx, GBEES_PHASE_HALO, 1);
-        launch_list(ctx, ctx->kern.pre + 1, 1);
+        launch_list(ctx, ctx->kern.pre + 1, ctx->pre_grid + 1, 1);
     }
     {
         Phase ph(ctx, GBEES_PHASE_LINK, 1);
@@ -496,10 +528,10 @@ void launch_step(gbees_ctx* ctx) {
     }
     {
         Phase ph(ctx, GBEES_PHASE_FACES, 1);
-        launch_list(ctx, ctx->kern.post, 1);
+        launch_list(ctx, ctx->kern.post, ctx->post_grid, 1);
     }
     Phase ph(ctx, GBEES_PHASE_APPLY, 1);
-    launch_list(ctx, ctx->kern.post + 1, 1);
+    launch_list(ctx, ctx->kern.post + 1, ctx->post_grid + 1, 1);
 }
 
 // ---- the step loop as a CUDA graph
@@ -547,9 +579,11 @@ void graph_nodes(gbees_ctx* ctx, GraphBuilder& gb, cudaGraph_t body, cudaGraphCo
     void* link_args[] = {m, b, &one};
     resolve_update_kernels(ctx);
     cudaGraphNode_t n = nullptr;
-    for (int i = 0; i < ctx->kern.npre; ++i) n = gb.add(body, n, ctx->kern.pre[i], G, THREADS, mb);
-    n = gb.add(body, n, link_kernel<N, T>(ctx->m.probe_width), G, THREADS, link_args);
-    for (int i = 0; i < ctx->kern.npost; ++i) n = gb.add(body, n, ctx->kern.post[i], G, THREADS, mb);
+    auto grid_or = [&](int g) { return g > 0 ? g : G; };
+    for (int i = 0; i < ctx->kern.npre; ++i) n = gb.add(body, n, ctx->kern.pre[i], grid_or(ctx->pre_grid[i]), THREADS, mb);
+    n = gb.add(body, n, link_kernel<N, T>(ctx->m.probe_width), grid_or(ctx->link_grid), THREADS, link_args);
+    for (int i = 0; i < ctx->kern.npost; ++i)
+        n = gb.add(body, n, ctx->kern.post[i], grid_or(ctx->post_grid[i]), THREADS, mb);
     DevScalars* sc = ctx->b.sc;
     long long maxit = kGraphMaxIter;
     int step_kernels = ctx->kern.npre + 1 + ctx->kern.npost + 1;
@@ -745,6 +779,12 @@ int gbees_profile_read(gbees_ctx* ctx, gbees_profile* out) {
     return GBEES_OK;
 }
 
+int gbees_set_batch_blocks(gbees_ctx* ctx, int32_t max_blocks) {
+    if (!ctx || max_blocks < 0) return GBEES_EINVAL;
+    ctx->batch_blocks = max_blocks;
+    return GBEES_OK;
+}
+
 int gbees_set_wait_limit(gbees_ctx* ctx, int64_t spins, int32_t extra_arrivals) {
     if (!ctx || spins < 1 || extra_arrivals < 0 || extra_arrivals > GRID_MAX) return GBEES_EINVAL;
     ctx->m.spin_limit = spins;
@@ -926,7 +966,8 @@ int gbees_propagate(gbees_ctx* ctx, double t_end, gbees_stats* stats) {
             const long long before = ctx->hs.steps_call;
             const long long upd_before = ctx->hs.updates_call;
             long long max_steps = kPersistSteps;
-            void* args[] = {&ctx->m, &ctx->b, &max_steps};
+            long long max_pool = limit;
+            void* args[] = {&ctx->m, &ctx->b, &max_steps, &max_pool};
             cudaEventRecord(ctx->pev[0], s);
             if (!cuda_ok(ctx, cudaLaunchCooperativeKernel(ctx->kern.persist, dim3(ctx->persist_grid), dim3(THREADS), args, 0, s),
                          "propagate"))
@@ -940,7 +981,7 @@ int gbees_propagate(gbees_ctx* ctx, double t_end, gbees_stats* stats) {
                 ctx->prof.persist_launches += 1;
                 ctx->prof.persist_updates += ctx->hs.updates_call - upd_before;
             }
-            if (!ctx->hs.done && ctx->hs.steps_call == before) {
+            if (!ctx->hs.done && ctx->hs.steps_call == before && ctx->hs.N <= limit) {
                 set_err(ctx, GBEES_ETIMEOUT, "propagate: a persistent launch made no progress");
                 return ctx->status;
             }
@@ -1112,16 +1153,17 @@ int gbees_batch_propagate(gbees_ctx* const* ctxs, int32_t count, const double* t
         !cuda_ok(c0, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, c0->kern.batch, THREADS, 0),
                  "batch_propagate"))
         return c0->status;
-    int G = std::max(1, std::min(count, sms * std::max(per_sm, 1)));
+    const int cap_blocks = c0->batch_blocks > 0 ? c0->batch_blocks : GRID_MAX;
+    int G = std::max(1, std::min({count, sms * std::max(per_sm, 1), cap_blocks}));
     // teams: every grid resident at once with blocks in proportion to its work
     int per_sm_team = 0;
     bool teams = c0->kern.batch_teams &&
                  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_team, c0->kern.batch_teams, THREADS, 0) ==
                      cudaSuccess &&
-                 per_sm_team >= 1 && count <= std::min(GRID_MAX, sms * per_sm_team);
+                 per_sm_team >= 1 && count <= std::min({GRID_MAX, sms * per_sm_team, cap_blocks});
     cudaGetLastError();
     if (teams) {
-        const int Gt = std::min(GRID_MAX, sms * per_sm_team);
+        const int Gt = std::min({GRID_MAX, sms * per_sm_team, cap_blocks});
         const std::vector<int> k = team_sizes(ctxs, count, t_end, Gt, max_steps > 0);
         std::vector<TeamSlot> h_slots;
         for (int32_t i = 0; i < count; ++i)

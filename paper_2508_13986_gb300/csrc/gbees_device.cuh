@@ -177,6 +177,7 @@ struct Bufs {
     long long* blk2; // per-block counts (halo cells)
     unsigned int* sorthist;  // digit histograms of the prune's radix sort
     void* u[2];  // face velocities (two generations, like the keys)
+    double* rate[2];  // CFL rate sum_j |f_j(x_{c-e_j/2})| / h_j of every entry (Eq. 8, FP64, fixed at creation)
     void* wl;    // update scratch in the storage type
     void* wg;
     void* tg;
@@ -403,6 +404,14 @@ __device__ __forceinline__ double cfl_rate64(const Model& m, const int* I) {
     return r;
 }
 
+// a * b + c rounded once, and the larger of two values, in the arithmetic
+// type itself (explicit single-precision forms for float, so that nothing is
+// widened to double).
+__device__ __forceinline__ double fmadd(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fmadd(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double vmax(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float vmax(float a, float b) { return fmaxf(a, b); }
+
 // Sign tests, positive and negative parts. FP64 arithmetic is scarce on this
 // chip, so for doubles they work on the bit pattern in the integer pipe (a
 // finite double is > 0 exactly when its bits, read as a signed integer, are
@@ -450,19 +459,28 @@ struct Above<float> {
     __device__ __forceinline__ bool operator()(float q) const { return q > pf; }
 };
 
-// 2x and x/2 of a non-negative double, exact, as IEEE arithmetic gives them;
-// for normal values by the exponent field in the integer pipe.
+// 2x and x/2 of a non-negative double with the results of IEEE x + x and
+// x * 0.5 (round to nearest even), in integer operations only (no FP64 pipe):
+// the exponent field moves by one; a subnormal or overflowing case is formed
+// on the bit pattern directly.
 __device__ __forceinline__ double twice_nonneg(double x) {
     const long long b = __double_as_longlong(x);
     const long long e = b >> 52;
-    if (e == 0) return __longlong_as_double(b << 1);                 // subnormal (or 0)
-    if (e <= 2045) return __longlong_as_double(b + (1ll << 52));
-    return x + x;                                                     // overflow, inf
+    long long r = e == 0 ? (b << 1)                                   // subnormal (or 0): the significand doubles
+                : e <= 2045 ? b + (1ll << 52)                         // one more in the exponent
+                : e == 2046 ? 0x7FF0000000000000ll                    // overflow to +inf
+                : b;                                                  // inf, NaN
+    return __longlong_as_double(r);
 }
 __device__ __forceinline__ double half_nonneg(double x) {
     const long long b = __double_as_longlong(x);
-    if ((b >> 52) >= 2) return __longlong_as_double(b - (1ll << 52));
-    return x * 0.5;                                                   // result subnormal (or 0)
+    const long long e = b >> 52;
+    if (e >= 2) return __longlong_as_double(b - (1ll << 52));         // one less in the exponent (inf, NaN stay)
+    // the result is subnormal: halve the significand, ties to even
+    const long long sig = e == 0 ? b : (b & 0xFFFFFFFFFFFFFll) | (1ll << 52);
+    long long q = sig >> 1;
+    if ((sig & 1) && (q & 1)) q += 1;
+    return __longlong_as_double(q);
 }
 __device__ __forceinline__ float twice_nonneg(float x) { return x + x; }
 __device__ __forceinline__ float half_nonneg(float x) { return 0.5f * x; }

@@ -182,8 +182,10 @@ __device__ __forceinline__ SortBufs sort_bufs(const Bufs& b, const StepView& v) 
 }
 
 // keep[c] = status (0 drop, 1 active, 2 halo, from the status pass in map);
-// A = (order key, c), dropped entries last (every result is independent of
-// the storage order; only the speed depends on it). A live entry's order key
+// A = (order key, c): active cells first, then the halo (each in the order of
+// the configured code), or both interleaved in key order; dropped entries
+// last (every result is independent of the storage order; only the speed
+// depends on it). A live entry's order key
 // is below 2^63: keys use at most 63 bits, and only an all-ones key has an
 // all-ones Morton code, a key no cell that survives a prune has.
 __global__ void __launch_bounds__(THREADS) k_sort_init(const Model m, Bufs b) {
@@ -194,10 +196,12 @@ __global__ void __launch_bounds__(THREADS) k_sort_init(const Model m, Bufs b) {
     long long c0, c1;
     block_chunk(v.N, c0, c1);
     const bool morton = m.sort_order == 1;
+    const bool mixed = m.sort_order == 3;  // halo cells among the active ones
     for (long long c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
         const int st = b.map[c];
         b.keep[c] = (unsigned char)st;
-        sb.key[0][c] = st == 0 ? ~0ull : (morton ? morton_code(key[c], m.n, m.key_bits) : key[c]);
+        const unsigned long long region = (st == 2 && !mixed) ? (1ull << 63) : 0ull;
+        sb.key[0][c] = st == 0 ? ~0ull : (region | (morton ? morton_code(key[c], m.n, m.key_bits) : key[c]));
         sb.val[0][c] = (unsigned int)c;
     }
 }

@@ -44,8 +44,12 @@ __device__ __forceinline__ void normalisation(const Model& m, const Combined& c,
 // Up to max_steps steps of the grid (m, b) by the nb blocks of index bi that
 // share it (the whole launch, a team of a batched launch, or one block): grid
 // barriers between the phases, block barriers when the block is alone.
+// max_pool: the loop also stops after a step that leaves more pool entries
+// than that (the persistent kernel hands a grown grid to the graph path; every
+// block sees the same count, so all leave together).
 template <int N, int DYN, typename T>
-__device__ __forceinline__ void step_loop(const Model& m, const Bufs& b, long long max_steps, int nb, int bi) {
+__device__ __forceinline__ void step_loop(const Model& m, const Bufs& b, long long max_steps, int nb, int bi,
+                                          long long max_pool = 0x7fffffffffffffffll) {
     __shared__ StepShared ss;
     DevScalars* sc = b.sc;
     // The result is the same for every thread of the block: a warp that read
@@ -215,6 +219,7 @@ __device__ __forceinline__ void step_loop(const Model& m, const Bufs& b, long lo
             v.g ^= 1;
             v.pb ^= 1;
         }
+        if (v.N > max_pool) break;
     }
     if (bi == 0 && threadIdx.x == 0) {
         sc->N = v.N;
@@ -241,8 +246,9 @@ __device__ __forceinline__ void step_loop(const Model& m, const Bufs& b, long lo
 
 
 template <int N, int DYN, typename T>
-__global__ void __launch_bounds__(THREADS, 1) k_persistent(const Model m, Bufs b, long long max_steps) {
-    step_loop<N, DYN, T>(m, b, max_steps, gridDim.x, blockIdx.x);
+__global__ void __launch_bounds__(THREADS, 1) k_persistent(const Model m, Bufs b, long long max_steps,
+                                                           long long max_pool) {
+    step_loop<N, DYN, T>(m, b, max_steps, gridDim.x, blockIdx.x, max_pool);
 }
 
 // Resident blocks per SM of the batch kernels: the register cap (64) spills a

@@ -230,9 +230,7 @@ __device__ __forceinline__ double grow_body(const Model& m, const Bufs& b, const
         if (!(om[e] & OM_GHOST) || !activate(om, e)) return;
         warp_aggregated_add(&sc->NA);
         b.map[warp_aggregated_add(&sc->n_act)] = (int)e;
-        int J[N];
-        unpack_key<N>(m, key[e], J);
-        rmax = fmax(rmax, cfl_rate64<N>(m, J));
+        rmax = fmax(rmax, b.rate[v.g][e]);  // fixed when the halo cell was linked
     };
     auto insert_active = [&](const int* J) {
         if (!interior<N>(m, J)) {
@@ -376,6 +374,7 @@ __device__ __forceinline__ double link_masks(const Model& m, const Bufs& b, long
             r = __dadd_rn(r, __ddiv_rn(fabs(ul), m.h[j]));
         }
         b.om[g][c] = (unsigned short)(f | msk);
+        b.rate[g][c] = r;
         if (!(f & OM_GHOST)) rmax = fmax(rmax, r);
     }
     return rmax;
@@ -460,7 +459,7 @@ __device__ __forceinline__ T wave_of(const T* Q, const T* U, long long cap, cons
     const T ul = U[d * cap + y];
     const T uh = up >= 0 ? U[d * cap + up] : (T)0;
     wlo = Py - Pm;
-    return fma(neg_part(uh), Pp - Py, pos_part(ul) * wlo);
+    return fmadd(neg_part(uh), Pp - Py, pos_part(ul) * wlo);
 }
 
 // Pass 1, one thread per entry c of [0, ncell) (active and halo), all
@@ -474,10 +473,15 @@ __device__ __forceinline__ void waves_body(const Model& m, const Bufs& b, const 
     const T* Q = static_cast<const T*>(b.q[v.pb]);
     const int* link = b.link[v.g];
     const T* U = static_cast<const T*>(b.u[v.g]);
-    T* wl = static_cast<T*>(b.wl);
-    T* wg = static_cast<T*>(b.wg);
-    T* tg = static_cast<T*>(b.tg);
+    // the outputs alias no input (restrict: loads may be scheduled ahead of the
+    // stores; no read-only cache path is implied)
+    T* __restrict__ wl = static_cast<T*>(b.wl);
+    T* __restrict__ wg = static_cast<T*>(b.wg);
+    T* __restrict__ tg = static_cast<T*>(b.tg);
     const long long cap = m.cap;
+    T i2h[N];  // 1 / (2 h_d) in the arithmetic type, converted once
+#pragma unroll
+    for (int d = 0; d < N; ++d) i2h[d] = (T)m.inv_2h[d];
     for (WarpRuns wr(ncell, v.nb, v.bi); wr.next();) {
         const long long c = wr.c;
         if (c >= ncell) continue;
@@ -491,7 +495,7 @@ __device__ __forceinline__ void waves_body(const Model& m, const Bufs& b, const 
             const T G = wave_of<N, T>(Q, U, cap, L, c, P0, d, wlo);
             wl[d * cap + c] = wlo;
             wg[d * cap + c] = G;
-            t = fma(G, (T)m.inv_2h[d], t);
+            t = fmadd(G, i2h[d], t);
         }
         tg[c] = t;
     }
@@ -509,7 +513,7 @@ __device__ __forceinline__ T waves_new(const Model& m, const T* Q, const T* U, c
     for (int d = 0; d < N; ++d) {
         if (d == j) continue;
         T wlo;
-        S = fma(wave_of<N, T>(Q, U, cap, L, y, (T)0, d, wlo), (T)m.inv_2h[d], S);
+        S = fmadd(wave_of<N, T>(Q, U, cap, L, y, (T)0, d, wlo), (T)m.inv_2h[d], S);
     }
     return S;
 }
@@ -534,9 +538,15 @@ __device__ __forceinline__ void faces_body(const Model& m, const Bufs& b, const 
     const T* wl = static_cast<const T*>(b.wl);
     const T* wg = static_cast<const T*>(b.wg);
     const T* tg = static_cast<const T*>(b.tg);
-    T* fl = static_cast<T*>(b.fl);
+    T* __restrict__ fl = static_cast<T*>(b.fl);  // aliases no input
     const int lim = m.limiter;
     const T dt = (T)v.dt;
+    T i2h[N], dth[N];  // 1 / (2 h_j) and dt / h_j in the arithmetic type, converted once
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        i2h[j] = (T)m.inv_2h[j];
+        dth[j] = (T)v.dth[j];
+    }
     for (WarpRuns wr(ncell, v.nb, v.bi); wr.next();) {
         const long long c = wr.c;
         if (c >= ncell) continue;
@@ -558,12 +568,12 @@ __device__ __forceinline__ void faces_body(const Model& m, const Bufs& b, const 
                 const long long y = up ? (long long)Llo : c;
                 T S;
                 if (y < nold) {
-                    S = fma(-(T)m.inv_2h[j], wg[j * cap + y], tg[y]);
+                    S = fmadd(-i2h[j], wg[j * cap + y], tg[y]);
                 } else {
                     S = waves_new<N, T>(m, Q, U, link, y, j);
                 }
                 // Eq. 7 (donor cell) and the corrections of Algorithm 1, gathered
-                f = u * fma(-dt, S, up ? q_or_zero<T>(Q, Llo) : P0);
+                f = u * fmadd(-dt, S, up ? q_or_zero<T>(Q, Llo) : P0);
                 if (lim != LIM_NONE && (gt0(W) || lt0(W))) {
                     T Wup;
                     if (up) {  // jump across the lower face of Llo
@@ -578,7 +588,7 @@ __device__ __forceinline__ void faces_body(const Model& m, const Bufs& b, const 
                     }
                     // the limited high-resolution term 1/2 |u| (1 - dt |u| / h_j) phi W
                     const T au = abs_bits(u);
-                    f = fma(half_nonneg(au) * fma(-(T)v.dth[j], au, (T)1), limited_wave<T>(lim, W, Wup), f);
+                    f = fmadd(half_nonneg(au) * fmadd(-dth[j], au, (T)1), limited_wave<T>(lim, W, Wup), f);
                 }
             }
             fl[j * cap + c] = f;
@@ -595,7 +605,7 @@ __device__ __forceinline__ void apply_body(const Model& m, const Bufs& b, const 
     const long long ncell = v.N;
     const long long cap = m.cap;
     const T* Q = static_cast<const T*>(b.q[v.pb]);
-    T* Qn = static_cast<T*>(b.q[v.pb ^ 1]);
+    T* __restrict__ Qn = static_cast<T*>(b.q[v.pb ^ 1]);  // aliases no input
     const int* link = b.link[v.g];
     const unsigned short* om = b.om[v.g];
     const T* fl = static_cast<const T*>(b.fl);
@@ -618,12 +628,12 @@ __device__ __forceinline__ void apply_body(const Model& m, const Bufs& b, const 
         for (int j = 0; j < N; ++j) {
             const int up = L[2 * j + 1];
             const T Fhi = up >= 0 ? fl[j * cap + up] : (T)0;
-            upd = fma(dth[j], Fhi - fl[j * cap + c], upd);
+            upd = fmadd(dth[j], Fhi - fl[j * cap + c], upd);
         }
         const T qn = (Q[c] - upd) * scale;
         Qn[c] = qn;
         acc_add(dacc, qn, err);
-        tmax = fmax(tmax, qn);
+        tmax = vmax(tmax, qn);
     }
     if (tmax > -INFINITY) mx = fmax(mx, (double)tmax);
 }
@@ -776,13 +786,15 @@ __device__ __forceinline__ Survivors block_offsets(const Bufs& b, int nb, int bi
     return r;
 }
 
-// The face velocities of entry c (generation g) move to nc of the other generation.
+// The face velocities and the CFL rate of entry c (generation g) move to nc of
+// the other generation.
 template <int N, typename T>
 __device__ __forceinline__ void copy_velocities(const Model& m, const Bufs& b, int g, long long c, long long nc) {
     const T* U = static_cast<const T*>(b.u[g]);
     T* Uo = static_cast<T*>(b.u[g ^ 1]);
 #pragma unroll
     for (int j = 0; j < N; ++j) Uo[j * m.cap + nc] = U[j * m.cap + c];
+    b.rate[g ^ 1][nc] = b.rate[g][c];
 }
 
 // Stream compaction of the survivors in storage order into the other buffer
@@ -824,9 +836,7 @@ __device__ __forceinline__ void prune_compact_body(const Model& m, const Bufs& b
                 b.map[c] = (int)nc;
                 acc_add(d, (double)val, err);
                 mx = fmax(mx, (double)val);
-                int I[N];
-                unpack_key<N>(m, k, I);
-                rmax = fmax(rmax, cfl_rate64<N>(m, I));
+                rmax = fmax(rmax, b.rate[v.g][c]);
             } else if (st == 2) {
                 const long long nc = bg + pg;
                 keyo[nc] = k;
@@ -873,9 +883,7 @@ __device__ __forceinline__ void prune_compact_sorted_body(const Model& m, const 
             omo[nc] = (unsigned short)(om[c] & 0xfffu);
             acc_add(d, (double)val, err);
             mx = fmax(mx, (double)val);
-            int I[N];
-            unpack_key<N>(m, k, I);
-            rmax = fmax(rmax, cfl_rate64<N>(m, I));
+            rmax = fmax(rmax, b.rate[v.g][c]);
         } else {
             Qo[nc] = (T)0;
             omo[nc] = (unsigned short)((om[c] & 0xfffu) | OM_GHOST);

@@ -27,7 +27,7 @@ GBEES_DYN_CONSTANT, GBEES_DYN_LINEAR, GBEES_DYN_LORENZ63, GBEES_DYN_LORENZ63_SHI
 GBEES_LIM_MC, GBEES_LIM_NONE, GBEES_LIM_LW = range(3)
 GBEES_FP64, GBEES_FP32 = 0, 1
 GBEES_LAUNCH_AUTO, GBEES_LAUNCH_PERSISTENT, GBEES_LAUNCH_GRAPH, GBEES_LAUNCH_DIRECT = range(4)
-GBEES_ORDER_KEY, GBEES_ORDER_MORTON, GBEES_ORDER_NONE = range(3)
+GBEES_ORDER_KEY, GBEES_ORDER_MORTON, GBEES_ORDER_NONE, GBEES_ORDER_KEY_MIXED = range(4)
 
 
 class gbees_config(ctypes.Structure):
@@ -98,6 +98,7 @@ _SIGNATURES = {
     "gbees_get_stats": (ctypes.c_int, [_vp, _P(gbees_stats)]),
     "gbees_get_status": (ctypes.c_int, [_vp]),
     "gbees_set_wait_limit": (ctypes.c_int, [_vp, _i64, _i32]),
+    "gbees_set_batch_blocks": (ctypes.c_int, [_vp, _i32]),
     "gbees_profile_control": (ctypes.c_int, [_vp, _i32, _i32]),
     "gbees_profile_read": (ctypes.c_int, [_vp, _P(gbees_profile)]),
     "gbees_last_error": (ctypes.c_char_p, [_vp]),
@@ -182,6 +183,10 @@ def gbees_get_stats(ctx: int, stats: gbees_stats) -> int:
 
 def gbees_set_wait_limit(ctx: int, spins: int, extra_arrivals: int = 0) -> int:
     return int(_f("gbees_set_wait_limit")(_vp(ctx), int(spins), int(extra_arrivals)))
+
+
+def gbees_set_batch_blocks(ctx: int, max_blocks: int) -> int:
+    return int(_f("gbees_set_batch_blocks")(_vp(ctx), int(max_blocks)))
 
 
 def gbees_get_status(ctx: int) -> int:
@@ -409,13 +414,18 @@ class Grid:
     _prof_on = False
 
 
-def propagate_batch(grids: Sequence["Grid"], t_end: Sequence[float], max_steps: int = 0) -> list:
+def propagate_batch(grids: Sequence["Grid"], t_end: Sequence[float], max_steps: int = 0,
+                    max_blocks: int = 0) -> list:
     """Propagate many grids (same dimension, dynamics and precision) in one
     launch on the first grid's stream (max_steps > 0: at most that many steps
-    each); returns their Stats."""
+    each; max_blocks > 0: at most that many thread blocks); returns their
+    Stats."""
     import torch
 
     count = len(grids)
+    rc = gbees_set_batch_blocks(grids[0].ctx, max_blocks)
+    if rc != 0:
+        raise GbeesError(rc, "bad max_blocks")
     nbytes = gbees_batch_workspace_bytes(count)
     if nbytes == 0:
         raise GbeesError(GBEES_EINVAL, "empty batch")

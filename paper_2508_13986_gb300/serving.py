@@ -7,9 +7,12 @@ keeps every admitted grid resident on the device between its propagation
 segments and measurement updates, and advances all grids in service together:
 one round is one batched launch per model family (dimension, dynamics) in which
 every grid takes at most `round_steps` steps towards its next segment target
-(gbees_batch_propagate with a step cap). Between rounds, grids that reached a
-measurement time get their Bayesian update (Eq. 4), finished grids are read
-out and released, and requests that arrived meanwhile join the next round.
+(gbees_batch_propagate with a step cap). The families' launches run at the
+same time, each on its own CUDA stream from its own host thread and capped to
+a share of the GPU's resident blocks in proportion to the family's active
+cells, and the measurement updates that came due (Eq. 4) follow on the same
+stream and thread. Between rounds, finished grids are read out and released,
+and requests that arrived meanwhile join the next round.
 
 Every grid runs the same phases with the same arithmetic whether it is served
 alone or in a mix, so its result does not depend on the mix.
@@ -19,6 +22,7 @@ the plain form that the batched loop is compared with.
 """
 from __future__ import annotations
 
+import concurrent.futures
 import time
 from collections import deque
 from dataclasses import dataclass, field
@@ -63,6 +67,8 @@ class _Active:
     seg: int = 0
     steps: int = 0
     updates: int = 0
+    cells: int = 1                  # active cells after the last round
+    complete: Optional[bool] = False  # set by the round that reached a segment target
     error: Optional[int] = None     # status of a failed call; the request ends with it
 
 
@@ -75,12 +81,24 @@ class Server:
     mode: str = "batched"           # or "single"
     keep_density: bool = False
     realtime: bool = True            # arrivals follow the wall clock
+    concurrent_families: bool = True # the families' rounds overlap on the device
     stats: Dict[str, float] = field(default_factory=dict)
+    family_windows: List[Dict[str, float]] = field(default_factory=list)  # launch intervals of the last run
+    _streams: Dict[Tuple[int, int], object] = field(default_factory=dict)
+
+    def _stream_of(self, family: Tuple[int, int]):
+        import torch
+
+        if self.mode == "single" or not self.concurrent_families or not torch.cuda.is_available():
+            return None
+        if family not in self._streams:
+            self._streams[family] = torch.cuda.Stream(device=self.device)
+        return self._streams[family]
 
     def _admit(self, rid: int, w: Workload, arrival: float, now: float) -> _Active:
         cfg = gbees.make_config(w.n, w.dynamics, w.params, w.h, w.x0, w.thr_rel, w.cfl, w.prune_interval,
                                 self.precision, w.limiter, capacity_for(w))
-        g = gbees.Grid(cfg, self.device)
+        g = gbees.Grid(cfg, self.device, stream=self._stream_of((w.n, w.dynamics)))
         a = _Active(rid, w, arrival, now, g, gbees.gbees_workspace_bytes(cfg), w.segments())
         try:
             g.init_gaussian(w.mean, w.cov)
@@ -117,11 +135,73 @@ class Server:
         a.seg += 1
         return a.seg >= len(a.segments)
 
+    def _pool(self, workers: int) -> concurrent.futures.ThreadPoolExecutor:
+        if getattr(self, "_executor", None) is None or self._executor_workers < workers:
+            self._executor = concurrent.futures.ThreadPoolExecutor(max_workers=workers)
+            self._executor_workers = workers
+        return self._executor
+
+    def _shares(self, families) -> Dict[Tuple[int, int], int]:
+        """Blocks each family's launch may use: all of them for one family,
+        otherwise the resident blocks in proportion to the family's active
+        cells (at least one block per grid where possible)."""
+        import torch
+
+        if len(families) <= 1 or not self.concurrent_families:
+            return {k: 0 for k in families}
+        sms = torch.cuda.get_device_properties(self.device).multi_processor_count if torch.cuda.is_available() else 152
+        total = sms * 4  # resident blocks of the batch kernels (four per SM)
+        work = {k: sum(max(1, m.cells) for m in members) for k, members in families.items()}
+        W = float(sum(work.values()))
+        return {k: max(1, int(total * work[k] / W)) for k in families}
+
+    def _family_round(self, family, members: List[_Active], max_blocks: int, clock):
+        """One round of one family on its stream: the batched launch, then the
+        measurement updates that came due. Returns (failed, reached)."""
+        import torch
+
+        failed: List[_Active] = []
+        reached: List[_Active] = []
+        stream = self._stream_of(family)
+        t_start = clock() if clock else None
+        ev0 = ev1 = None
+        if stream is not None:
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+        targets = [m.segments[m.seg][0] for m in members]
+        try:
+            sts = gbees.propagate_batch([m.grid for m in members], targets, max_steps=self.round_steps,
+                                        max_blocks=max_blocks)
+        except gbees.GbeesError:
+            sts = [m.grid.stats() if m.grid.status == 0 else None for m in members]
+        if ev1 is not None:
+            ev1.record(stream)
+        for m, s, tt in zip(members, sts, targets):
+            if s is None:
+                m.error = m.grid.status
+                failed.append(m)
+                continue
+            m.steps = s.total_steps
+            m.updates += s.cell_updates
+            m.cells = s.n_cells
+            if s.t == tt:
+                try:
+                    m.complete = self._advance_segment(m)
+                except gbees.GbeesError as e:
+                    m.error = e.status
+                    m.complete = None
+                reached.append(m)
+        if ev1 is not None:
+            self._windows.append((family, ev0, ev1, t_start))
+        return failed, reached
+
     def run(self, stream: Sequence[Tuple[float, Workload]]) -> List[Result]:
         import torch
 
         t0 = time.perf_counter()
         clock = (lambda: time.perf_counter() - t0) if self.realtime else None
+        self._windows = []
         pending = deque((rid, arr, w) for rid, (arr, w) in enumerate(sorted(stream, key=lambda x: x[0])))
         active: List[_Active] = []
         results: List[Result] = []
@@ -181,21 +261,17 @@ class Server:
                 families: Dict[Tuple[int, int], List[_Active]] = {}
                 for a in runnable:
                     families.setdefault((a.w.n, a.w.dynamics), []).append(a)
-                for members in families.values():
-                    targets = [m.segments[m.seg][0] for m in members]
-                    try:
-                        sts = gbees.propagate_batch([m.grid for m in members], targets, max_steps=self.round_steps)
-                    except gbees.GbeesError:
-                        sts = [m.grid.stats() if m.grid.status == 0 else None for m in members]
-                    for m, s, tt in zip(members, sts, targets):
-                        if s is None:
-                            m.error = m.grid.status
-                            failed.append(m)
-                            continue
-                        m.steps = s.total_steps
-                        m.updates += s.cell_updates
-                        if s.t == tt:
-                            reached.append(m)
+                shares = self._shares(families)
+                fams = list(families.items())
+                if self.concurrent_families and len(fams) > 1:
+                    pool = self._pool(len(fams))
+                    outs = list(pool.map(lambda kv: self._family_round(kv[0], kv[1], shares[kv[0]], clock),
+                                         fams))
+                else:
+                    outs = [self._family_round(k, m, shares[k], clock) for k, m in fams]
+                for f_failed, f_reached in outs:
+                    failed.extend(f_failed)
+                    reached.extend(f_reached)
             torch.cuda.synchronize(self.device)
             done_now = clock() if clock else virtual_now
             for a in failed:
@@ -203,10 +279,16 @@ class Server:
                 active.remove(a)
                 used -= a.nbytes
             for a in reached:
-                try:
-                    complete = self._advance_segment(a)
-                except gbees.GbeesError as e:
-                    results.append(self._finish(a, done_now, error=gbees.STATUS_NAMES.get(e.status, "error")))
+                if self.mode == "single":
+                    try:
+                        complete = self._advance_segment(a)
+                    except gbees.GbeesError as e:
+                        a.error = e.status
+                        complete = None
+                else:
+                    complete = a.complete
+                if complete is None:
+                    results.append(self._finish(a, done_now, error=gbees.STATUS_NAMES.get(a.error, "error")))
                     active.remove(a)
                     used -= a.nbytes
                     continue
@@ -215,6 +297,7 @@ class Server:
                     active.remove(a)
                     used -= a.nbytes
         elapsed = time.perf_counter() - t0
+        self._collect_windows()
         lat = np.array([r.latency for r in results]) if results else np.zeros(1)
         self.stats = {
             "requests": len(results),
@@ -231,3 +314,14 @@ class Server:
             "latency_max_s": float(lat.max()),
         }
         return sorted(results, key=lambda r: r.rid)
+
+    def _collect_windows(self):
+        """Device-time intervals (ms from the first launch) of every family launch of the run."""
+        self.family_windows = []
+        if not self._windows:
+            return
+        ref = self._windows[0][1]
+        for family, e0, e1, _ in self._windows:
+            e1.synchronize()
+            self.family_windows.append({"family": family, "start_ms": ref.elapsed_time(e0),
+                                        "end_ms": ref.elapsed_time(e1)})

@@ -70,6 +70,23 @@ def test_served_results_match_the_oracle_grid_by_grid():
         assert l1 <= FP64_L1, (w.name, l1)
 
 
+def test_model_families_run_at_the_same_time_on_the_device():
+    """Lorenz '63 and Lorenz '96 requests in service together: each family's
+    round is issued on its own stream from its own host thread with a share of
+    the GPU's blocks, so their launches overlap in device time (CUDA event
+    intervals around each family's launch, on its stream)."""
+    stream = small_stream(12, seed=25, rate=1e6)
+    srv = Server(precision=gbees.GBEES_FP32, realtime=False, round_steps=40)
+    res = srv.run(stream)
+    assert len(res) == len(stream) and srv.stats["failed"] == 0
+    wins = srv.family_windows
+    l63 = [w for w in wins if w["family"][0] == 3]
+    l96 = [w for w in wins if w["family"][0] == 6]
+    assert l63 and l96
+    overlap = max(min(a["end_ms"], b["end_ms"]) - max(a["start_ms"], b["start_ms"]) for a in l63 for b in l96)
+    assert overlap > 0.0, wins
+
+
 def test_admission_respects_the_memory_budget():
     stream = small_stream(8, seed=22)
     srv = Server(precision=gbees.GBEES_FP32, realtime=False)

@@ -18,7 +18,7 @@ class FakeGrid:
 
     created = []
 
-    def __init__(self, cfg, device="cuda:0"):
+    def __init__(self, cfg, device="cuda:0", stream=None):
         self.cfg = cfg
         self.t = 0.0
         self.total = 0
@@ -67,7 +67,7 @@ class FakeGrid:
         pass
 
 
-def fake_batch(grids, targets, max_steps=0):
+def fake_batch(grids, targets, max_steps=0, max_blocks=0):
     out, err = [], None
     for g, t in zip(grids, targets):
         try:
@@ -158,8 +158,8 @@ def test_a_failing_grid_ends_alone_and_the_others_complete(fake_device, monkeypa
     st = stream(count=10, seed=44)
     orig = FakeGrid.__init__
 
-    def init(self, cfg, device="cuda:0"):
-        orig(self, cfg, device)
+    def init(self, cfg, device="cuda:0", stream=None):
+        orig(self, cfg, device, stream)
         if len(FakeGrid.created) == 3:           # the third request runs out of capacity
             self.fail_after = 2
 
@@ -217,11 +217,11 @@ def test_a_grid_that_cannot_be_made_is_reported_and_the_stream_goes_on(fake_devi
     st = stream(count=6, seed=47)
     made = {"n": 0}
 
-    def grid(cfg, device="cuda:0"):
+    def grid(cfg, device="cuda:0", stream=None):
         made["n"] += 1
         if made["n"] == 4:
             raise exc
-        return FakeGrid(cfg, device)
+        return FakeGrid(cfg, device, stream)
 
     monkeypatch.setattr(gbees, "Grid", grid)
     srv = serving.Server(realtime=False, round_steps=4)
