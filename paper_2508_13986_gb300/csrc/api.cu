@@ -404,17 +404,18 @@ void launch_link(gbees_ctx* ctx, int step) {
     cudaLaunchKernel(link_kernel<N, T>(ctx->m.probe_width), dim3(G), dim3(THREADS), args, 0, ctx->stream);
 }
 
-// Blocks of a step kernel f: a resident wave (SMs x blocks per SM), and at
-// least the context's fixed grid (latency-bound kernels with few resident
-// blocks, such as the hashtable probes of the link phase, gain from a second
-// wave that overlaps the first one's tail).
-int resident_grid(gbees_ctx* ctx, const void* f, int sms) {
+// Blocks of a step kernel f: one resident wave (SMs x blocks per SM); with
+// at_least_fixed, at least the context's fixed grid (the hashtable probes of
+// the link phase, latency-bound with few resident blocks, gain from a second
+// wave that overlaps the first one's tail; measured on the 6-D grid).
+int resident_grid(gbees_ctx* ctx, const void* f, int sms, bool at_least_fixed = false) {
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, THREADS, 0) != cudaSuccess || per_sm < 1) {
         cudaGetLastError();
         return ctx->grid;
     }
-    return std::min(GRID_MAX, std::max(ctx->grid, sms * per_sm));
+    const int wave = sms * per_sm;
+    return std::min(GRID_MAX, at_least_fixed ? std::max(ctx->grid, wave) : wave);
 }
 
 void resolve_update_kernels(gbees_ctx* ctx) {
@@ -430,7 +431,7 @@ void resolve_update_kernels(gbees_ctx* ctx) {
         for (int i = 0; i < ctx->kern.npost; ++i) ctx->post_grid[i] = resident_grid(ctx, ctx->kern.post[i], sms);
         with_nt(ctx, [&](auto NN, auto TT) {
             constexpr int N = decltype(NN)::value;
-            ctx->link_grid = resident_grid(ctx, link_kernel<N, decltype(TT)>(ctx->m.probe_width), sms);
+            ctx->link_grid = resident_grid(ctx, link_kernel<N, decltype(TT)>(ctx->m.probe_width), sms, true);
         });
     }
     cudaGetLastError();

@@ -518,81 +518,127 @@ __device__ __forceinline__ T waves_new(const Model& m, const T* Q, const T* U, c
     return S;
 }
 
-// Pass 2, one thread per entry c, all dimensions j: the flux through the lower
-// j-face of c (Eq. 7, the corrections of Algorithm 1 gathered onto the face,
-// the limited HR term), for every face with an active cell on at least one
-// side. The corrections that Algorithm 1 scatters onto face (X, j) add up to
+// The flux pass's view of the step (pointers and constants in the arithmetic type).
+template <int N, typename T>
+struct FaceCtx {
+    const T* Q;
+    const int* link;
+    const T* U;
+    const T* wl;
+    const T* wg;
+    const T* tg;
+    long long cap, nold;
+    int lim;
+    T dt, i2h[N], dth[N];
+};
+
+// The flux through the lower j-face of pool entry X (Eq. 7, the corrections of
+// Algorithm 1 gathered onto the face, the limited HR term), X's value P0. The
+// corrections that Algorithm 1 scatters onto face (X, j) add up to
 //   -u_j(X) dt sum_{d != j} G_d(Y) / (2 h_d),  Y the cell upwind of the face,
-// and sum_{d != j} = tg(Y) - G_j(Y) / (2 h_j). The upper face of an active cell
+// with sum_{d != j} = tg(Y) - G_j(Y) / (2 h_j). Entries added by this step's
+// grow and halo phases (index >= nold) have no pass-1 values; theirs are formed
+// on the spot.
+template <int N, typename T>
+__device__ __forceinline__ T face_flux(const Model& m, const FaceCtx<N, T>& fc, long long X, T P0, int j) {
+    const long long cap = fc.cap;
+    const T u = fc.U[j * cap + X];
+    if (!(gt0(u) || lt0(u))) return (T)0;
+    const int Llo = fc.link[(long long)(2 * j) * cap + X];
+    const bool up = gt0(u);  // the flow crosses the face upwards: the upwind cell is Llo
+    const bool old_x = X < fc.nold;
+    const T PL = (up || !old_x) ? q_or_zero<T>(fc.Q, Llo) : (T)0;
+    const T W = old_x ? fc.wl[j * cap + X] : P0 - PL;
+    // transverse sum of the cell upwind of the face
+    const long long y = up ? (long long)Llo : X;
+    T S;
+    if (y < fc.nold) {
+        S = fmadd(-fc.i2h[j], fc.wg[j * cap + y], fc.tg[y]);
+    } else {
+        S = waves_new<N, T>(m, fc.Q, fc.U, fc.link, y, j);
+    }
+    // Eq. 7 (donor cell) and the corrections of Algorithm 1, gathered
+    T f = u * fmadd(-fc.dt, S, up ? PL : P0);
+    if (fc.lim != LIM_NONE && (gt0(W) || lt0(W))) {
+        T Wup;
+        if (up) {  // jump across the lower face of Llo
+            Wup = Llo < fc.nold ? fc.wl[j * cap + Llo]
+                                : PL - q_or_zero<T>(fc.Q, fc.link[(long long)(2 * j) * cap + Llo]);
+        } else {  // jump across the upper face of X
+            const int Lup = fc.link[(long long)(2 * j + 1) * cap + X];
+            Wup = (Lup >= 0 && Lup < fc.nold) ? fc.wl[j * cap + Lup] : q_or_zero<T>(fc.Q, Lup) - P0;
+        }
+        // the limited high-resolution term 1/2 |u| (1 - dt |u| / h_j) phi W
+        const T au = abs_bits(u);
+        f = fmadd(half_nonneg(au) * fmadd(-fc.dth[j], au, (T)1), limited_wave<T>(fc.lim, W, Wup), f);
+    }
+    return f;
+}
+
+// Pass 2: the flux through every face with an active cell on at least one
+// side, stored as the lower face of the entry above it: all n lower faces of
+// an active cell, and the lower faces of a halo cell whose neighbour below is
+// active. Each warp takes 32 consecutive entries, lists their needed faces
+// (entry, j) in shared memory, dimension by dimension, and evaluates them 32 at
+// a time, so that the lanes of a warp all work although a halo cell needs only
+// the few faces it shares with active cells. The upper face of an active cell
 // is the lower face of its upper neighbour, which is in the pool (active or
 // halo).
 template <int N, int DYN, typename T>
 __device__ __forceinline__ void faces_body(const Model& m, const Bufs& b, const StepView& v) {
     const long long ncell = v.N;
-    const long long nold = v.N_prev;
     const long long cap = m.cap;
-    const T* Q = static_cast<const T*>(b.q[v.pb]);
-    const int* link = b.link[v.g];
     const unsigned short* om = b.om[v.g];
-    const T* U = static_cast<const T*>(b.u[v.g]);
-    const T* wl = static_cast<const T*>(b.wl);
-    const T* wg = static_cast<const T*>(b.wg);
-    const T* tg = static_cast<const T*>(b.tg);
     T* __restrict__ fl = static_cast<T*>(b.fl);  // aliases no input
-    const int lim = m.limiter;
-    const T dt = (T)v.dt;
-    T i2h[N], dth[N];  // 1 / (2 h_j) and dt / h_j in the arithmetic type, converted once
+    FaceCtx<N, T> fc;
+    fc.Q = static_cast<const T*>(b.q[v.pb]);
+    fc.link = b.link[v.g];
+    fc.U = static_cast<const T*>(b.u[v.g]);
+    fc.wl = static_cast<const T*>(b.wl);
+    fc.wg = static_cast<const T*>(b.wg);
+    fc.tg = static_cast<const T*>(b.tg);
+    fc.cap = cap;
+    fc.nold = v.N_prev;
+    fc.lim = m.limiter;
+    fc.dt = (T)v.dt;
 #pragma unroll
-    for (int j = 0; j < N; ++j) {
-        i2h[j] = (T)m.inv_2h[j];
-        dth[j] = (T)v.dth[j];
+    for (int j = 0; j < N; ++j) {  // converted once
+        fc.i2h[j] = (T)m.inv_2h[j];
+        fc.dth[j] = (T)v.dth[j];
     }
+    __shared__ unsigned char s_item[WARPS][32 * N];  // (lane | j << 5) of the warp's needed faces
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
     for (WarpRuns wr(ncell, v.nb, v.bi); wr.next();) {
         const long long c = wr.c;
-        if (c >= ncell) continue;
-        const bool halo_c = is_halo(om, c);
-        const bool old_c = c < nold;
-        int L[2 * N];
-        load_links<N>(link, cap, c, L);
-        const T P0 = Q[c];
+        const long long c0 = c - lane;
+        unsigned need = 0;
+        if (c < ncell) {
+            if (!is_halo(om, c)) {
+                need = (1u << N) - 1u;
+            } else {
 #pragma unroll
-        for (int j = 0; j < N; ++j) {
-            const int Llo = L[2 * j];
-            if (halo_c && (Llo < 0 || is_halo(om, Llo))) continue;  // no active cell on this face
-            const T u = U[j * cap + c];
-            T f = (T)0;
-            if (gt0(u) || lt0(u)) {
-                const bool up = gt0(u);  // the flow crosses the face upwards: the upwind cell is Llo
-                const T W = old_c ? wl[j * cap + c] : P0 - q_or_zero<T>(Q, Llo);
-                // transverse sum of the cell upwind of the face
-                const long long y = up ? (long long)Llo : c;
-                T S;
-                if (y < nold) {
-                    S = fmadd(-i2h[j], wg[j * cap + y], tg[y]);
-                } else {
-                    S = waves_new<N, T>(m, Q, U, link, y, j);
-                }
-                // Eq. 7 (donor cell) and the corrections of Algorithm 1, gathered
-                f = u * fmadd(-dt, S, up ? q_or_zero<T>(Q, Llo) : P0);
-                if (lim != LIM_NONE && (gt0(W) || lt0(W))) {
-                    T Wup;
-                    if (up) {  // jump across the lower face of Llo
-                        if (Llo < nold) {
-                            Wup = wl[j * cap + Llo];
-                        } else {
-                            Wup = q_or_zero<T>(Q, Llo) - q_or_zero<T>(Q, link[(long long)(2 * j) * cap + Llo]);
-                        }
-                    } else {  // jump across the upper face of c
-                        const int Lup = L[2 * j + 1];
-                        Wup = (Lup >= 0 && Lup < nold) ? wl[j * cap + Lup] : q_or_zero<T>(Q, Lup) - P0;
-                    }
-                    // the limited high-resolution term 1/2 |u| (1 - dt |u| / h_j) phi W
-                    const T au = abs_bits(u);
-                    f = fmadd(half_nonneg(au) * fmadd(-dth[j], au, (T)1), limited_wave<T>(lim, W, Wup), f);
+                for (int j = 0; j < N; ++j) {
+                    const int Llo = fc.link[(long long)(2 * j) * cap + c];
+                    if (Llo >= 0 && !is_halo(om, Llo)) need |= 1u << j;
                 }
             }
-            fl[j * cap + c] = f;
         }
+        int count = 0;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            const unsigned bal = __ballot_sync(0xffffffffu, (need >> j) & 1u);
+            if ((need >> j) & 1u) s_item[wid][count + __popc(bal & lt)] = (unsigned char)(lane | (j << 5));
+            count += __popc(bal);
+        }
+        __syncwarp();
+        for (int q = lane; q < count; q += 32) {
+            const int it = s_item[wid][q];
+            const long long X = c0 + (it & 31);
+            const int j = it >> 5;
+            fl[j * cap + X] = face_flux<N, T>(m, fc, X, fc.Q[X], j);
+        }
+        __syncwarp();
     }
 }
 
