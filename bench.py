@@ -46,7 +46,7 @@ TRAFFIC_BYTES_PER_CELL = {
     # k_persistent, third launch of `bench.py --steps 1 --warmup 1 --no-secondary --cpu-budget 0
     # --max-cells 1048576` (segment t = 0.5..0.75: 2118979 cell updates, counted by the oracle):
     # 9.268 MB read + 1.092 MB written
-    "lorenz63_h0.25/f64": {"bytes_per_cell": 10.360832e6 / 2118979, "src": "c00cd41fc877901a"},
+    "lorenz63_h0.25/f64/k_persistent": {"bytes_per_cell": 10.360832e6 / 2118979, "src": "c00cd41fc877901a"},
 }
 # The paper's own throughput on its two cases, in this benchmark's unit (cells
 # per second, total cell computations over the runtime): the fastest GPU row of
@@ -84,6 +84,9 @@ def parse():
                     help="whole runs timed end to end through the C ABI (at most --steps)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the extra keys (the Lorenz '63 workload and the served stream)")
+    ap.add_argument("--block-threads", type=int, default=0,
+                    help="threads per block of the step kernels (0: tuned by timing 128 and 256)")
+    ap.add_argument("--no-tune", dest="tune", action="store_false", help="skip the launch-shape tuning")
     ap.add_argument("--max-cells", type=int, default=0,
                     help="pool capacity of a single-grid workload (0: sized from the workload, see auto_max_cells)")
     ap.add_argument("--launch-mode", choices=["auto", "persistent", "graph", "direct"], default="auto")
@@ -239,7 +242,35 @@ def device_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def time_precision(args, w, precision, dev, rank, world):
+def fp64_peak():
+    """FP64 arithmetic peak of the GPU from its unit counts and clock: SMs x 2
+    FP64 FMA lanes per SM per clock (ncu's sm__sass_thread_inst_executed_op_dfma
+    peak_sustained on GB300: 304 per cycle for 152 SMs) x 2 flops x the
+    maximum SM clock of MEASURED_PEAKS.json (2070 MHz). Returns (TFLOP/s, how)."""
+    import torch
+
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = 2070.0
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = float(json.load(f).get("sm_max_mhz", mhz))
+    except (OSError, ValueError):
+        pass
+    tf = sms * 2 * 2 * mhz * 1e6 / 1e12
+    return tf, f"derived: {sms} SMs x 2 FP64 FMA lanes/clock x 2 flops x {mhz:.0f} MHz"
+
+
+def fp64_flops_per_update(kernel: str, n: int) -> int:
+    """Algorithmic FP64 flops of one cell update in a step kernel (an FMA counts
+    two): the flux pass evaluates the n lower faces of the cell, 11 flops each
+    (the transverse sum, donor cell and corrections: 2 + 2 + 1; the limited
+    high-resolution term: 1 + 2 + 1 + 2); the wave pass 7 per dimension (two
+    jumps, the entering wave 1 + 2, its share of tg 2); the update pass 3 per
+    dimension plus 3 (difference and FMA per face, then the rescale)."""
+    return {"k_faces": 11 * n, "k_waves_list": 7 * n, "k_apply": 3 * n + 3}[kernel]
+
+
+def time_precision(args, w, precision, dev, rank, world, steps=None, warmup=None):
     import torch
 
     from paper_2508_13986_gb300 import gbees
@@ -248,11 +279,25 @@ def time_precision(args, w, precision, dev, rank, world):
     mode = {"auto": gbees.GBEES_LAUNCH_AUTO, "persistent": gbees.GBEES_LAUNCH_PERSISTENT,
             "graph": gbees.GBEES_LAUNCH_GRAPH, "direct": gbees.GBEES_LAUNCH_DIRECT}[args.launch_mode]
     max_cells = args.max_cells or auto_max_cells(w, prec, dev)
+    # launch shape: threads per block of the step kernels, chosen by timing a
+    # short stretch of this workload with each candidate (results do not
+    # depend on it)
+    tuned = {"block_threads": args.block_threads or 256, "tuned": False}
+    if not args.block_threads and args.tune:
+        from paper_2508_13986_gb300.autotune import tune_grid
+
+        t_probe = min(w.t_end, 0.05)
+        best, times = tune_grid(w, prec, t_probe=t_probe, probe_widths=(1,), launch_modes=(mode,),
+                                device=f"cuda:{dev}", max_cells=max_cells, block_threads=(128, 256), repeats=1)
+        tuned = {"block_threads": best.block_threads or 256, "tuned": True, "probe_t_end": t_probe,
+                 "ns_per_cell_update": {str(k.block_threads): round(v * 1e6, 4) for k, v in times.items()}}
     grid = gbees.grid_for_workload(w, precision=prec, max_cells=max_cells, device=f"cuda:{dev}",
-                                   launch_mode=mode)
+                                   launch_mode=mode, block_threads=tuned["block_threads"])
     stream = grid.stream
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=f"cuda:{dev}")
-    for _ in range(args.warmup):
+    steps = args.steps if steps is None else steps
+    warmup = args.warmup if warmup is None else warmup
+    for _ in range(warmup):
         run_workload(grid, w)
     barrier(world)
     torch.cuda.synchronize(dev)
@@ -260,7 +305,7 @@ def time_precision(args, w, precision, dev, rank, world):
     clocks = ClockSampler(dev)
     clocks.start()
     total_ms, total_updates, total_steps, peak = 0.0, 0, 0, 0
-    for _ in range(args.steps):
+    for _ in range(steps):
         flush.zero_()  # L2 flush between timed runs (outside the events)
         torch.cuda.synchronize(dev)
         e0 = torch.cuda.Event(enable_timing=True)
@@ -295,7 +340,7 @@ def time_precision(args, w, precision, dev, rank, world):
     # end to end through the C ABI with host buffers: inputs from host memory,
     # final density and moments read back to host memory, wall clock
     e2e_ms, e2e_updates, h2d, d2h = 0.0, 0, 0, 0
-    e2e_runs = max(1, min(args.steps, args.e2e_runs))
+    e2e_runs = max(1, min(steps, args.e2e_runs))
     for _ in range(e2e_runs):
         flush.zero_()
         torch.cuda.synchronize(dev)
@@ -315,6 +360,7 @@ def time_precision(args, w, precision, dev, rank, world):
 
     peak_gbs, peak_src = load_peaks()
     bpc = bytes_per_update(w.n, precision)
+    args_steps = steps
     # the dominant kernel of the timed region: the persistent step-loop kernel
     # when the launch mode used it (its launches are event-timed inside the
     # library on its stream), otherwise the slowest per-cell step kernel of the
@@ -328,7 +374,7 @@ def time_precision(args, w, precision, dev, rank, world):
     else:
         per_cell = {k: prof["ms"][k] for k in ("grow", "faces", "apply")}
         top = max(per_cell, key=per_cell.get)
-        kernel = {"grow": "k_grow_waves", "faces": "k_faces", "apply": "k_apply"}[top]
+        kernel = {"grow": "k_waves_list", "faces": "k_faces", "apply": "k_apply"}[top]
         timing = "CUDA events around each launch of that kernel in a profiled pass of the same runs"
         launches_k = max(prof["timed"][top], 1)
         units = prof_updates
@@ -336,35 +382,55 @@ def time_precision(args, w, precision, dev, rank, world):
     units_per_launch = units / max(launches_k, 1)
     achieved = bpc * units_per_launch / (avg_us * 1e-6) / 1e9 if avg_us > 0 else None
     traffic = None
-    rec = TRAFFIC_BYTES_PER_CELL.get(f"{w.name}/{precision}")
+    rec = TRAFFIC_BYTES_PER_CELL.get(f"{w.name}/{precision}/{kernel.split(' ')[0]}")
     if rec and rec.get("src") == device_source_hash():
         traffic = rec["bytes_per_cell"] * units_per_launch
+    roof = {
+        "bound": "hbm",
+        "kernel": kernel,
+        "timing": timing,
+        "achieved": achieved,
+        "peak": peak_gbs,
+        "peak_source": peak_src,
+        "unit": "GB/s",
+        "frac": (achieved / peak_gbs) if achieved else None,
+        "traffic": traffic,
+        "algorithmic_bytes_per_cell_update": bpc,
+        "cell_updates_per_launch": units_per_launch,
+        "avg_launch_us": avg_us,
+    }
+    kname = kernel.split(" ")[0]
+    if precision == "f64" and kname in ("k_faces", "k_waves_list", "k_apply"):
+        # FP64 step kernels are bound by the FP64 pipe on this chip (ncu: the
+        # flux pass keeps it about 70 % busy at under 20 % of DRAM bandwidth):
+        # the roofline is the FP64 arithmetic peak; the HBM figures stay beside it
+        tf, how = fp64_peak()
+        fpc = fp64_flops_per_update(kname, w.n)
+        ach = fpc * units_per_launch / (avg_us * 1e-6) / 1e12 if avg_us > 0 else None
+        roof = {"bound": "alu", "kernel": kernel, "timing": timing, "achieved": ach, "peak": tf,
+                "peak_source": how, "unit": "TFLOP/s", "frac": (ach / tf) if ach else None, "traffic": traffic,
+                "algorithmic_fp64_flops_per_cell_update": fpc, "cell_updates_per_launch": units_per_launch,
+                "avg_launch_us": avg_us,
+                "hbm": {"achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
+                        "frac": (achieved / peak_gbs) if achieved else None,
+                        "algorithmic_bytes_per_cell_update": bpc}}
     tot_ms = sum(prof["ms"].values())
     phase_share = {k: (v / tot_ms if tot_ms > 0 else 0.0) for k, v in prof["ms"].items()}
     return {
         "value": upd_sum / (ms_max / 1e3),
-        "ms_per_step": ms_max / args.steps,
-        "updates_per_run": total_updates / args.steps,
-        "time_steps_per_run": total_steps / args.steps,
+        "ms_per_step": ms_max / args_steps,
+        "steps": args_steps,
+        "warmup": warmup,
+        "updates_per_run": total_updates / args_steps,
+        "time_steps_per_run": total_steps / args_steps,
         "time_steps_per_s": steps_sum / (ms_max / 1e3),
         "peak_cells": peak,
         "e2e": {"value": e2e_sum / (e2e_max / 1e3), "unit": METRIC, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_run": e2e_max / e2e_runs, "runs": e2e_runs},
-        "roofline": {
-            "bound": "hbm",
-            "kernel": kernel,
-            "timing": timing,
-            "achieved": achieved,
-            "peak": peak_gbs,
-            "peak_source": peak_src,
-            "unit": "GB/s",
-            "frac": (achieved / peak_gbs) if achieved else None,
-            "traffic": traffic,
-            "algorithmic_bytes_per_cell_update": bpc,
-            "cell_updates_per_launch": units_per_launch,
-            "avg_launch_us": avg_us,
-        },
+        "roofline": roof,
         "profiled_phase_share": phase_share,
+        "profiled_phase_ms": {k: v for k, v in prof["ms"].items()},
+        "launch_shape": tuned,
         "persistent_us_per_step": persist_split,
         "gpu_launches": launches,
         "clocks": clk,
@@ -477,18 +543,15 @@ def time_batch(args, ws, precision, dev, rank, world):
     }
 
 
-def main_serving(args):
+def serving_forms(args, local):
     """The request stream served three ways on one GPU: batched FP32, batched
-    FP64, and the plain FP64 form (one request at a time, gbees_propagate)."""
+    FP64 (continuous batching, model families overlapping on the device), and
+    the plain FP64 form (one request at a time, gbees_propagate)."""
     import torch
 
     from paper_2508_13986_gb300 import gbees, workloads
     from paper_2508_13986_gb300.serving import Server
 
-    rank, world, local = dist_env()
-    if rank != 0:
-        return
-    torch.cuda.set_device(local)
     stream = workloads.serving_stream(count=args.requests, rate=args.rate)
     warm = workloads.serving_stream(count=8, rate=1000.0, seed=7)
     out = {}
@@ -502,6 +565,18 @@ def main_serving(args):
         st = dict(srv.stats)
         st["clocks"] = clocks.stop()
         out[tag] = st
+        torch.cuda.empty_cache()
+    return out
+
+
+def main_serving(args):
+    import torch
+
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    out = serving_forms(args, local)
     main = out["batched_f32"]
     print(json.dumps({
         "metric": METRIC, "value": main["cell_updates_per_s"], "unit": METRIC, "n_gpus": 1, "steps": 1, "warmup": 1,
@@ -624,30 +699,38 @@ def main_ours(args):
         cfg_extra = {"grids": count, "t_end": "per grid, uniform in [0.25, 1.0]" if args.t_end is None
                      else f"per grid, uniform in [0.25, 1.0], capped at {args.t_end}",
                      "grid_sizes": "ragged, 1.7e3-2.7e5 initial cells"}
-        timer = lambda prec: time_batch(args, ws, prec, local, rank, world)  # noqa: E731
+        timer = lambda prec, st=None, wu=None: time_batch(args, ws, prec, local, rank, world)  # noqa: E731
     else:
         w = workloads.config(args.workload)
         if args.t_end is not None:
             w = w.with_(t_end=args.t_end, measurements=[m for m in w.measurements if m.t < args.t_end])
         cfg_extra = {"t_end": w.t_end}
-        timer = lambda prec: time_precision(args, w, prec, local, rank, world)  # noqa: E731
+        timer = lambda prec, st=None, wu=None: time_precision(args, w, prec, local, rank, world, st, wu)  # noqa: E731
     main = timer(args.precision)
     other = None
     if not args.no_secondary:
+        # the other precision beside the headline, on fewer runs (stated in the line)
         other_prec = "f32" if args.precision == "f64" else "f64"
-        other = timer(other_prec)
+        other = timer(other_prec, min(args.steps, 5), min(args.warmup, 3))
     extras = {}
     if not args.no_extras and args.workload == DEFAULT_WORKLOAD and args.t_end is None:
         # the Lorenz '63 workload with measurements (small grid: the persistent
         # kernel) in both precisions, timed the same way
         w2 = workloads.config(SECONDARY_WORKLOAD)
         for prec in ("f64", "f32"):
-            r = time_precision(args, w2, prec, local, rank, world)
+            r = time_precision(args, w2, prec, local, rank, world, min(args.steps, 10), min(args.warmup, 3))
             extras.setdefault(SECONDARY_WORKLOAD, {})[prec] = {
                 "value": r["value"], "unit": METRIC, "ms_per_run": r["ms_per_step"],
                 "time_steps_per_run": r["time_steps_per_run"], "cell_updates_per_run": r["updates_per_run"],
                 "e2e": r["e2e"], "roofline": r["roofline"], "persistent_us_per_step": r["persistent_us_per_step"],
                 "gpu_launches": r["gpu_launches"], "clocks": r["clocks"]}
+        if rank == 0:
+            sv = serving_forms(args, local)
+            extras["serving"] = {"requests": args.requests, "rate_per_s": args.rate,
+                                 "mix": "70 % Lorenz '63, 30 % Lorenz '96 6-D; 0-3 corrections each",
+                                 "forms": {k: {x: v[x] for x in ("cell_updates_per_s", "requests_per_s", "latency_p50_s",
+                                                                 "latency_p99_s", "wall_s", "failed", "clocks")}
+                                           for k, v in sv.items()}}
     if rank == 0:
         cpu = cpu1 = None
         if world == 1 and args.cpu_budget > 0:
@@ -675,6 +758,7 @@ def main_ours(args):
                        "time_steps_per_s": main["time_steps_per_s"],
                        "peak_cells": main["peak_cells"],
                        "e2e_runs": main["e2e"]["runs"], "profiled_runs": 1,
+                       "launch_shape": main.get("launch_shape"),
                        **({"paper_baseline": PAPER_CELLS_PER_S[args.workload][1]}
                           if args.workload in PAPER_CELLS_PER_S else {}),
                        **({"paper_context": PAPER_CONTEXT[args.workload]}
@@ -691,7 +775,9 @@ def main_ours(args):
         if other is not None:
             line["other_precision"] = {
                 "dtype": "f32" if args.precision == "f64" else "f64",
-                "value": other["value"], "ms_per_step": other["ms_per_step"], "e2e": other["e2e"],
+                "value": other["value"], "ms_per_step": other["ms_per_step"],
+                "steps": other.get("steps"), "warmup": other.get("warmup"), "e2e": other["e2e"],
+                "launch_shape": other.get("launch_shape"),
                 "roofline": other["roofline"], "gpu_launches": other["gpu_launches"], "clocks": other["clocks"],
                 "profiled_phase_share": other["profiled_phase_share"],
                 "persistent_us_per_step": other["persistent_us_per_step"]}

@@ -108,6 +108,10 @@ typedef struct {
     double table_factor;    /* hashtable slots per cell of capacity, >= 1.25 (0 = 2.0, Sec. 4.2) */
     int32_t launch_mode;    /* GBEES_LAUNCH_*: how propagate drives the time steps */
     int32_t storage_order;  /* GBEES_ORDER_*: order of the pool after a prune of a large grid */
+    int32_t block_threads;  /* threads per block of the step kernels of the graph and direct launch
+                               modes: 64, 128 or 256 (0 = 256) */
+    int64_t persist_max_entries; /* AUTO runs the persistent kernel while the pool holds at most this
+                                    many entries, the CUDA graph beyond (0 = 2^18) */
 } gbees_config;
 
 /* Storage order of the pool entries after a prune of a grid of more than
@@ -119,8 +123,17 @@ typedef struct {
  *              consecutive too
  *   MORTON     the same split, each part in Morton (Z-curve) order
  *   NONE       the survivors keep their order (active cells first, then halo)
- *   KEY_MIXED  active and halo cells interleaved in lexicographic order */
-enum { GBEES_ORDER_KEY = 0, GBEES_ORDER_MORTON = 1, GBEES_ORDER_NONE = 2, GBEES_ORDER_KEY_MIXED = 3 };
+ *   KEY_MIXED  active and halo cells interleaved in lexicographic order
+ *   ROW_MORTON the KEY split, each part with the rows along the last
+ *              dimension kept whole (in key order) and the rows in Morton
+ *              order of the other indices */
+enum {
+    GBEES_ORDER_KEY = 0,
+    GBEES_ORDER_MORTON = 1,
+    GBEES_ORDER_NONE = 2,
+    GBEES_ORDER_KEY_MIXED = 3,
+    GBEES_ORDER_ROW_MORTON = 4
+};
 
 /* Launch modes of gbees_propagate (all give bit-identical results):
  *   AUTO        persistent kernel while the grid is small, CUDA graph beyond

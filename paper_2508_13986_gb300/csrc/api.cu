@@ -75,12 +75,13 @@ struct gbees_ctx {
     Kernels kern{};
     bool kern_ok = false;
     int persist_grid = 0;
-    long long persist_max_cells = 1ll << 18;
+    long long persist_max_cells = 1ll << 18;  // AUTO: persistent kernel up to this many pool entries
+    int step_threads = THREADS;                // threads per block of the graph/direct step kernels
     int batch_blocks = 0;  // blocks of a batched launch led by this context at most (0: all resident)
     // blocks of the step kernels of the graph and direct paths: as many as the
     // GPU holds resident for each (SMs x blocks per SM by occupancy), so that one
     // wave covers the grid-stride loops: pre[0..npre), link, post[0..npost)
-    int pre_grid[2] = {0, 0}, link_grid = 0, post_grid[3] = {0, 0, 0};
+    int pre_grid[3] = {0, 0, 0}, link_grid = 0, post_grid[3] = {0, 0, 0};
     // device time of every persistent launch (always measured: few launches)
     cudaEvent_t pev[2] = {nullptr, nullptr};
     ~gbees_ctx() {
@@ -146,8 +147,11 @@ bool config_ok(const gbees_config* c, std::string* why) {
     if (c->max_cells < 1 || c->max_cells > 0x7fffffffll) return fail("max_cells must be in 1..2^31-1");
     if (!(c->table_factor == 0.0 || c->table_factor >= 1.25)) return fail("table_factor must be 0 or >= 1.25");
     if (c->launch_mode < GBEES_LAUNCH_AUTO || c->launch_mode > GBEES_LAUNCH_DIRECT) return fail("unknown launch_mode");
-    if (c->storage_order < GBEES_ORDER_KEY || c->storage_order > GBEES_ORDER_KEY_MIXED)
+    if (c->storage_order < GBEES_ORDER_KEY || c->storage_order > GBEES_ORDER_ROW_MORTON)
         return fail("unknown storage_order");
+    if (!(c->block_threads == 0 || c->block_threads == 64 || c->block_threads == 128 || c->block_threads == 256))
+        return fail("block_threads must be 0, 64, 128 or 256");
+    if (c->persist_max_entries < 0) return fail("persist_max_entries must be >= 0");
     return true;
 }
 
@@ -250,6 +254,8 @@ void bind_context(gbees_ctx* ctx, const gbees_config* cfg, const Layout& L, void
     b.wg = (void*)(base + L.wg);
     b.tg = (void*)(base + L.tg);
     b.fl = (void*)(base + L.fl);
+    ctx->step_threads = cfg->block_threads > 0 ? cfg->block_threads : THREADS;
+    ctx->persist_max_cells = cfg->persist_max_entries > 0 ? cfg->persist_max_entries : (1ll << 18);
 }
 
 void set_err(gbees_ctx* ctx, int st, const std::string& msg) {
@@ -401,7 +407,7 @@ template <int N, typename T>
 void launch_link(gbees_ctx* ctx, int step) {
     void* args[] = {&ctx->m, &ctx->b, &step};
     const int G = ctx->link_grid > 0 ? ctx->link_grid : ctx->grid;
-    cudaLaunchKernel(link_kernel<N, T>(ctx->m.probe_width), dim3(G), dim3(THREADS), args, 0, ctx->stream);
+    cudaLaunchKernel(link_kernel<N, T>(ctx->m.probe_width), dim3(G), dim3(ctx->step_threads), args, 0, ctx->stream);
 }
 
 // Blocks of a step kernel f: one resident wave (SMs x blocks per SM); with
@@ -410,12 +416,14 @@ void launch_link(gbees_ctx* ctx, int step) {
 // wave that overlaps the first one's tail; measured on the 6-D grid).
 int resident_grid(gbees_ctx* ctx, const void* f, int sms, bool at_least_fixed = false) {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, THREADS, 0) != cudaSuccess || per_sm < 1) {
+    const int bt = ctx->step_threads;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, bt, 0) != cudaSuccess || per_sm < 1) {
         cudaGetLastError();
-        return ctx->grid;
+        return ctx->grid * (THREADS / bt);
     }
     const int wave = sms * per_sm;
-    return std::min(GRID_MAX, at_least_fixed ? std::max(ctx->grid, wave) : wave);
+    // the fixed grid holds the same threads whatever the block size
+    return std::min(GRID_MAX, at_least_fixed ? std::max(ctx->grid * (THREADS / bt), wave) : wave);
 }
 
 void resolve_update_kernels(gbees_ctx* ctx) {
@@ -441,7 +449,7 @@ void launch_list(gbees_ctx* ctx, void* const* f, const int* grids, int nf) {
     void* args[] = {&ctx->m, &ctx->b};
     for (int i = 0; i < nf; ++i) {
         const int G = grids[i] > 0 ? grids[i] : ctx->grid;
-        cudaLaunchKernel(f[i], dim3(G), dim3(THREADS), args, 0, ctx->stream);
+        cudaLaunchKernel(f[i], dim3(G), dim3(ctx->step_threads), args, 0, ctx->stream);
     }
 }
 
@@ -513,12 +521,12 @@ void launch_readout(gbees_ctx* ctx, int* d_idx, double* d_p) {
 void launch_step(gbees_ctx* ctx) {
     resolve_update_kernels(ctx);
     {
-        Phase ph(ctx, GBEES_PHASE_GROW, 1);
-        launch_list(ctx, ctx->kern.pre, ctx->pre_grid, 1);
+        Phase ph(ctx, GBEES_PHASE_GROW, 2);
+        launch_list(ctx, ctx->kern.pre, ctx->pre_grid, 2);
     }
     {
         Phase ph(ctx, GBEES_PHASE_HALO, 1);
-        launch_list(ctx, ctx->kern.pre + 1, ctx->pre_grid + 1, 1);
+        launch_list(ctx, ctx->kern.pre + 2, ctx->pre_grid + 2, 1);
     }
     {
         Phase ph(ctx, GBEES_PHASE_LINK, 1);
@@ -581,10 +589,11 @@ void graph_nodes(gbees_ctx* ctx, GraphBuilder& gb, cudaGraph_t body, cudaGraphCo
     resolve_update_kernels(ctx);
     cudaGraphNode_t n = nullptr;
     auto grid_or = [&](int g) { return g > 0 ? g : G; };
-    for (int i = 0; i < ctx->kern.npre; ++i) n = gb.add(body, n, ctx->kern.pre[i], grid_or(ctx->pre_grid[i]), THREADS, mb);
-    n = gb.add(body, n, link_kernel<N, T>(ctx->m.probe_width), grid_or(ctx->link_grid), THREADS, link_args);
+    const int bt = ctx->step_threads;
+    for (int i = 0; i < ctx->kern.npre; ++i) n = gb.add(body, n, ctx->kern.pre[i], grid_or(ctx->pre_grid[i]), bt, mb);
+    n = gb.add(body, n, link_kernel<N, T>(ctx->m.probe_width), grid_or(ctx->link_grid), bt, link_args);
     for (int i = 0; i < ctx->kern.npost; ++i)
-        n = gb.add(body, n, ctx->kern.post[i], grid_or(ctx->post_grid[i]), THREADS, mb);
+        n = gb.add(body, n, ctx->kern.post[i], grid_or(ctx->post_grid[i]), bt, mb);
     DevScalars* sc = ctx->b.sc;
     long long maxit = kGraphMaxIter;
     int step_kernels = ctx->kern.npre + 1 + ctx->kern.npost + 1;

@@ -54,6 +54,7 @@ struct alignas(256) DevScalars {
     long long NA_new;     // active cells surviving the current prune
     long long n_halo;     // halo cells appended by the current halo phase
     long long n_act;      // halo cells made active by the current grow (listed in map)
+    long long n_glist;    // cells listed for the current grow (listed form)
     double t;             // time
     double t_target;      // end of the current propagate call
     double dt;            // last step
@@ -192,7 +193,7 @@ constexpr unsigned short OM_GHOST = 0x4000;
 // The kernels of one time step for one model and precision: those before the
 // link phase, those after it, and the persistent step-loop kernel.
 struct Kernels {
-    void* pre[2];
+    void* pre[3];
     int npre;
     void* post[3];
     int npost;
@@ -658,12 +659,12 @@ __device__ __forceinline__ void block_reduce_acc_max(long long (&d)[NDIG], doubl
     __syncthreads();
     if (threadIdx.x < NDIG) {
         long long v = 0;
-        for (int w = 0; w < WARPS; ++w) v += s_acc[w][threadIdx.x];
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += s_acc[w][threadIdx.x];
         if (v) atomicAdd((unsigned long long*)&g_acc[threadIdx.x], (unsigned long long)v);
     }
     if (threadIdx.x == 32 && g_ord) {
         double m = -INFINITY;
-        for (int w = 0; w < WARPS; ++w) m = fmax(m, s_mx[w]);
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, s_mx[w]);
         if (m > -INFINITY) atomicMax(g_ord, ord_key(m));
     }
     __syncthreads();
@@ -676,7 +677,7 @@ __device__ __forceinline__ double block_max(double mx) {
     if ((threadIdx.x & 31) == 0) s_m[threadIdx.x >> 5] = mx;
     __syncthreads();
     double m = -INFINITY;
-    for (int w = 0; w < WARPS; ++w) m = fmax(m, s_m[w]);
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, s_m[w]);
     __syncthreads();
     return m;
 }
@@ -755,7 +756,7 @@ __device__ __forceinline__ void block_partial(Partial* part, long long (&d)[NDIG
         Partial p;
         unsigned long long mm = 0, rr = 0;
         for (int q = 0; q < NDIG; ++q) p.acc[q] = 0;
-        for (int w = 0; w < WARPS; ++w) {
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
             for (int q = 0; q < NDIG; ++q) p.acc[q] += s_acc[w][q];
             mm = max(mm, s_mx[w]);
             rr = max(rr, s_rt[w]);
@@ -810,7 +811,7 @@ __device__ __forceinline__ Combined combine_partials(const Partial* part, int nb
     for (int q = 0; q < NDIG; ++q) c.acc[q] = 0;
     c.maxq_ord = 0;
     c.rate_bits = 0;
-    for (int w = 0; w < WARPS; ++w) {
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
         for (int q = 0; q < NDIG; ++q) c.acc[q] += s_acc[w][q];
         c.maxq_ord = max(c.maxq_ord, s_mo[w]);
         c.rate_bits = max(c.rate_bits, s_rt[w]);
@@ -869,7 +870,7 @@ __device__ __forceinline__ int block_exclusive_scan(int flag, int& total) {
     if (lane == 0) s_w[wid] = __popc(bal);
     __syncthreads();
     int before = 0, tot = 0;
-    for (int w = 0; w < WARPS; ++w) {
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
         int v = s_w[w];
         if (w < wid) before += v;
         tot += v;

@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(THREADS) k_init_count(const Model m, Bufs b, c
     __syncthreads();
     if (threadIdx.x == 0) {
         long long t = 0;
-        for (int w = 0; w < WARPS; ++w) t += s[w];
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s[w];
         b.blk[blockIdx.x] = t;
     }
 }
@@ -229,6 +229,7 @@ __global__ void __launch_bounds__(THREADS) k_halo(const Model m, Bufs b) {
             sc->N = min(sc->N + sc->n_halo, m.cap);
             sc->n_halo = 0;
             sc->n_act = 0;
+            sc->n_glist = 0;
             sc->ticket = 0;
         }
     }
@@ -260,17 +261,23 @@ __device__ __forceinline__ void finish_step(const Model& m, DevScalars* sc, cons
     sc->ticket = 0;
 }
 
-// First phase of a step: grow, and the waves of the entries that existed
-// before it (a cell that grow or halo adds has p = 0, like a missing one, so
-// the waves of the old entries do not change).
+// The first phase of a step of a large grid in two kernels: the waves of the
+// existing entries, listing the cells that grow (no block-wide rounds over the
+// whole pool), then every (listed cell, candidate) pair over the grid.
 template <int N, int DYN, typename T>
-__global__ void __launch_bounds__(THREADS) k_grow_waves(const Model m, Bufs b) {
+__global__ void __launch_bounds__(THREADS) k_waves_list(const Model m, Bufs b) {
     DevScalars* sc = b.sc;
     if (*(volatile int*)&sc->done | *(volatile int*)&sc->error) return;
     const StepView v = view_of(m, sc);
-    const double r = grow_body<N, T>(m, b, v);
-    waves_body<N, DYN, T>(m, b, v, v.N_prev);
-    grow_rates(sc, r);
+    waves_body<N, DYN, T, true>(m, b, v, v.N_prev);
+}
+
+template <int N, typename T>
+__global__ void __launch_bounds__(THREADS) k_grow_list(const Model m, Bufs b) {
+    DevScalars* sc = b.sc;
+    if (*(volatile int*)&sc->done | *(volatile int*)&sc->error) return;
+    const StepView v = view_of(m, sc);
+    grow_rates(sc, grow_list_body<N, T>(m, b, v));
 }
 
 // Flux update, pass 2: the flux through every face that touches an active

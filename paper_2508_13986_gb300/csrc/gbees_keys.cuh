@@ -54,6 +54,19 @@ GBEES_HD unsigned long long morton_code(unsigned long long k, int n, int b) {
     return out;
 }
 
+// Row-Morton code of a packed key of n fields of b bits: the Morton code of
+// the first n - 1 fields, then the last field. Cells that differ only in the
+// last index keep their key order (a row of the grid along the last dimension
+// stays contiguous, so the neighbours of a run of consecutive cells in any
+// dimension are runs too), while the rows themselves follow the Z curve of
+// the other n - 1 indices (rows near one another in those dimensions stay near
+// one another in code order). A bijection of the n*b-bit keys.
+GBEES_HD unsigned long long row_morton_code(unsigned long long k, int n, int b) {
+    if (n <= 1) return k;
+    const unsigned long long last = k & ((1ull << b) - 1);
+    return (morton_code(k >> b, n - 1, b) << b) | last;
+}
+
 // murmur3 64-bit finaliser (a bijection of u64); the table slot of a key is
 // mix64(key) & (slots - 1)
 GBEES_HD unsigned long long mix64(unsigned long long x) {

@@ -108,6 +108,7 @@ __global__ void k_reset(DevScalars* sc, double t0) {
     sc->NA_new = 0;
     sc->n_halo = 0;
     sc->n_act = 0;
+    sc->n_glist = 0;
     sc->t = t0;
     sc->t_target = t0;
     sc->dt = 0.0;
@@ -195,13 +196,16 @@ __global__ void __launch_bounds__(THREADS) k_sort_init(const Model m, Bufs b) {
     const unsigned long long* key = b.key[v.g];
     long long c0, c1;
     block_chunk(v.N, c0, c1);
-    const bool morton = m.sort_order == 1;
-    const bool mixed = m.sort_order == 3;  // halo cells among the active ones
+    const int order = m.sort_order;        // GBEES_ORDER_*
+    const bool mixed = order == 3;          // halo cells among the active ones
     for (long long c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
         const int st = b.map[c];
         b.keep[c] = (unsigned char)st;
         const unsigned long long region = (st == 2 && !mixed) ? (1ull << 63) : 0ull;
-        sb.key[0][c] = st == 0 ? ~0ull : (region | (morton ? morton_code(key[c], m.n, m.key_bits) : key[c]));
+        const unsigned long long code = order == 1   ? morton_code(key[c], m.n, m.key_bits)
+                                        : order == 4 ? row_morton_code(key[c], m.n, m.key_bits)
+                                                     : key[c];
+        sb.key[0][c] = st == 0 ? ~0ull : (region | code);
         sb.val[0][c] = (unsigned int)c;
     }
 }

@@ -206,75 +206,90 @@ __device__ __forceinline__ long long insert_cell(const Model& m, const Bufs& b, 
 //
 // The candidates of a cell (2n faces, 4 C(n,2) edges, those that are not
 // downwind skipped at once) are independent chains of dependent loads and
-// atomics. Cells that qualify cluster in storage order (the cells a grow adds
-// are appended together), so the qualifying cells of all warps of the block
-// are gathered in shared memory and their (cell, candidate) pairs spread over
-// all threads of the block. Returns the largest CFL rate of the halo cells
-// this thread activated (inserted cells get theirs in the link phase).
+// atomics, spread over many threads: grow_body gathers a block's qualifying
+// cells in shared memory (the persistent and batch step loops); for large
+// grids the wave pass lists them (grow_list_mark) and a kernel of its own
+// spreads every (cell, candidate) pair of the list over the grid
+// (grow_list_body).
+struct GrowWork {
+    double rmax = 0.0;  // largest CFL rate of the halo cells this thread activated
+};
+
+// Candidate k of cell cc with downwind directions out.
 template <int N, typename T>
-__device__ __forceinline__ double grow_body(const Model& m, const Bufs& b, const StepView& v) {
-    constexpr int K = 2 * N + 2 * N * (N - 1);  // candidates per cell
+__device__ __forceinline__ void grow_candidate(const Model& m, const Bufs& b, const StepView& v, long long cc,
+                                               unsigned out, int k, GrowWork& gw) {
     DevScalars* sc = b.sc;
-    const long long ncell = v.N_prev;
-    const double pstar = m.thr_rel * v.maxq;
-    const Above<T> above(pstar);
-    const T* Q = static_cast<const T*>(b.q[v.pb]);
-    const unsigned long long* key = b.key[v.g];
+    const long long cap = m.cap;
     const int* link = b.link[v.g];
     unsigned short* om = b.om[v.g];
-    const long long cap = m.cap;
-    __shared__ long long s_cell[THREADS];
-    __shared__ unsigned s_out[THREADS];
-    double rmax = 0.0;
-    auto make_active = [&](long long e) {
+    int d1, d2 = -1;
+    if (k < 2 * N) {
+        d1 = k;
+    } else {
+        const int e = k - 2 * N;
+        int rem = e >> 2, j = 0;
+        while (rem >= N - 1 - j) {
+            rem -= N - 1 - j;
+            ++j;
+        }
+        d1 = 2 * j + (e & 1);
+        d2 = 2 * (j + 1 + rem) + ((e >> 1) & 1);
+    }
+    if (!((out >> d1) & 1u) || (d2 >= 0 && !((out >> d2) & 1u))) return;
+    const int a = link[(long long)d1 * cap + cc];
+    long long e;
+    if (d2 < 0) {
+        e = a;
+    } else if (a >= 0) {
+        e = link[(long long)d2 * cap + a];
+    } else {
+        const int a2 = link[(long long)d2 * cap + cc];
+        e = a2 >= 0 ? link[(long long)d1 * cap + a2] : -1;
+    }
+    if (e >= 0) {  // in the pool: a halo cell becomes active
         if (!(om[e] & OM_GHOST) || !activate(om, e)) return;
         warp_aggregated_add(&sc->NA);
         b.map[warp_aggregated_add(&sc->n_act)] = (int)e;
-        rmax = fmax(rmax, b.rate[v.g][e]);  // fixed when the halo cell was linked
-    };
-    auto insert_active = [&](const int* J) {
-        if (!interior<N>(m, J)) {
-            set_error(sc, ST_EKEYRANGE);
-            return;
-        }
-        if (insert_cell<N, T>(m, b, v, J, 0, &sc->N, 0) >= 0) warp_aggregated_add(&sc->NA);
-    };
-    // candidate k of cell cc with downwind directions out
-    auto candidate = [&](long long cc, unsigned out, int k) {
-        int d1, d2 = -1;
-        if (k < 2 * N) {
-            d1 = k;
-        } else {
-            const int e = k - 2 * N;
-            int rem = e >> 2, j = 0;
-            while (rem >= N - 1 - j) {
-                rem -= N - 1 - j;
-                ++j;
-            }
-            d1 = 2 * j + (e & 1);
-            d2 = 2 * (j + 1 + rem) + ((e >> 1) & 1);
-        }
-        if (!((out >> d1) & 1u) || (d2 >= 0 && !((out >> d2) & 1u))) return;
-        const int a = link[(long long)d1 * cap + cc];
-        long long e;
-        if (d2 < 0) {
-            e = a;
-        } else if (a >= 0) {
-            e = link[(long long)d2 * cap + a];
-        } else {
-            const int a2 = link[(long long)d2 * cap + cc];
-            e = a2 >= 0 ? link[(long long)d1 * cap + a2] : -1;
-        }
-        if (e >= 0) {
-            make_active(e);
-            return;
-        }
-        int J[N];
-        unpack_key<N>(m, key[cc], J);
-        J[d1 >> 1] += (d1 & 1) ? 1 : -1;
-        if (d2 >= 0) J[d2 >> 1] += (d2 & 1) ? 1 : -1;
-        insert_active(J);
-    };
+        gw.rmax = fmax(gw.rmax, b.rate[v.g][e]);  // fixed when the halo cell was linked
+        return;
+    }
+    int J[N];
+    unpack_key<N>(m, b.key[v.g][cc], J);
+    J[d1 >> 1] += (d1 & 1) ? 1 : -1;
+    if (d2 >= 0) J[d2 >> 1] += (d2 & 1) ? 1 : -1;
+    if (!interior<N>(m, J)) {
+        set_error(sc, ST_EKEYRANGE);
+        return;
+    }
+    if (insert_cell<N, T>(m, b, v, J, 0, &sc->N, 0) >= 0) warp_aggregated_add(&sc->NA);
+}
+
+template <int N>
+constexpr int GROW_K = 2 * N + 2 * N * (N - 1);  // candidates per cell
+
+// Whether cell c takes part in this step's grow: significant, active, with
+// outward directions, its downwind set not yet known to be active.
+template <typename T>
+__device__ __forceinline__ bool grows(const unsigned short* om, const T* Q, const Above<T>& above, long long c,
+                                      unsigned& out) {
+    if (!above(Q[c])) return false;
+    const unsigned f = om[c];
+    out = f & 0xfffu;
+    return !(f & (OM_COMPLETE | OM_GHOST)) && out;
+}
+
+// The block-gathered form (all threads of the block must call it).
+template <int N, typename T>
+__device__ __forceinline__ double grow_body(const Model& m, const Bufs& b, const StepView& v) {
+    constexpr int K = GROW_K<N>;
+    const long long ncell = v.N_prev;
+    const Above<T> above(m.thr_rel * v.maxq);
+    const T* Q = static_cast<const T*>(b.q[v.pb]);
+    unsigned short* om = b.om[v.g];
+    __shared__ long long s_cell[THREADS];
+    __shared__ unsigned s_out[THREADS];
+    GrowWork gw;
     // rounds of one run of 32 cells per warp; the block's first warp has the most
     const long long runs = (ncell + 31) / 32;
     const long long stride = (long long)v.nb * (blockDim.x >> 5);
@@ -283,29 +298,62 @@ __device__ __forceinline__ double grow_body(const Model& m, const Bufs& b, const
     for (long long rd = 0; rd < rounds; ++rd) {
         const long long k = v.bi + (long long)v.nb * wid + stride * rd;
         const long long c = k * 32 + (threadIdx.x & 31);
-        unsigned f = 0;
-        bool q = false;
-        if (k < runs && c < ncell && above(Q[c])) {
-            f = om[c];
-            q = !(f & (OM_COMPLETE | OM_GHOST)) && (f & 0xfffu);
-        }
+        unsigned out = 0;
+        const bool q = k < runs && c < ncell && grows<T>(om, Q, above, c, out);
         int nq;
         const int pos = block_exclusive_scan(q, nq);
         if (nq == 0) continue;
         if (q) {
             s_cell[pos] = c;
-            s_out[pos] = f & 0xfffu;
+            s_out[pos] = out;
         }
         __syncthreads();
         const int pairs = nq * K;
         for (int t = threadIdx.x; t < pairs; t += blockDim.x) {
             const int rank = t / K;
-            candidate(s_cell[rank], s_out[rank], t - rank * K);
+            grow_candidate<N, T>(m, b, v, s_cell[rank], s_out[rank], t - rank * K, gw);
         }
         __syncthreads();
-        if (q) om[c] = (unsigned short)(f | OM_COMPLETE);
+        if (q) om[c] = (unsigned short)(om[c] | OM_COMPLETE);
     }
-    return rmax;
+    return gw.rmax;
+}
+
+// The listed form, first half: cell c (of the wave pass's sweep) joins the
+// step's grow list (in the flux scratch, free until the flux pass) when it
+// grows.
+template <typename T>
+__device__ __forceinline__ void grow_list_mark(const Bufs& b, const StepView& v, const Above<T>& above, long long c) {
+    const T* Q = static_cast<const T*>(b.q[v.pb]);
+    unsigned out;
+    if (grows<T>(b.om[v.g], Q, above, c, out)) {
+        int* glist = static_cast<int*>(b.fl);
+        glist[warp_aggregated_add(&b.sc->n_glist)] = (int)c;
+    }
+}
+
+// The listed form, second half: every (listed cell, candidate) pair, over all
+// threads of the grid; the thread of a cell's first candidate marks it
+// complete (only its own flag bit, and nothing else writes that word now).
+template <int N, typename T>
+__device__ __forceinline__ double grow_list_body(const Model& m, const Bufs& b, const StepView& v) {
+    constexpr int K = GROW_K<N>;
+    const int* glist = static_cast<const int*>(b.fl);
+    unsigned short* om = b.om[v.g];
+    const long long nl = *(volatile long long*)&b.sc->n_glist;
+    GrowWork gw;
+    const long long items = nl * K;
+    const long long tid = (long long)v.bi * blockDim.x + threadIdx.x;
+    const long long nth = (long long)v.nb * blockDim.x;
+    for (long long it = tid; it < items; it += nth) {
+        const long long rank = it / K;
+        const int k = (int)(it - rank * K);
+        const long long c = glist[rank];
+        const unsigned out = om[c] & 0xfffu;
+        grow_candidate<N, T>(m, b, v, c, out, k, gw);
+        if (k == 0) om[c] = (unsigned short)(om[c] | OM_COMPLETE);
+    }
+    return gw.rmax;
 }
 
 // ------------------------------------------------------------------ halo
@@ -468,7 +516,7 @@ __device__ __forceinline__ T wave_of(const T* Q, const T* U, long long cap, cons
 // are left out: they have p = 0, and their waves are formed on the spot. Runs
 // beside grow: a cell that grow or halo adds has p = 0 like the missing cell it
 // replaces, so these waves do not change.
-template <int N, int DYN, typename T>
+template <int N, int DYN, typename T, bool LIST_GROW = false>
 __device__ __forceinline__ void waves_body(const Model& m, const Bufs& b, const StepView& v, long long ncell) {
     const T* Q = static_cast<const T*>(b.q[v.pb]);
     const int* link = b.link[v.g];
@@ -482,9 +530,11 @@ __device__ __forceinline__ void waves_body(const Model& m, const Bufs& b, const 
     T i2h[N];  // 1 / (2 h_d) in the arithmetic type, converted once
 #pragma unroll
     for (int d = 0; d < N; ++d) i2h[d] = (T)m.inv_2h[d];
+    const Above<T> above(m.thr_rel * v.maxq);
     for (WarpRuns wr(ncell, v.nb, v.bi); wr.next();) {
         const long long c = wr.c;
         if (c >= ncell) continue;
+        if (LIST_GROW) grow_list_mark<T>(b, v, above, c);
         int L[2 * N];
         load_links<N>(link, cap, c, L);
         const T P0 = Q[c];
@@ -752,7 +802,7 @@ __device__ __forceinline__ long long block_count(int cnt) {
     if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = cnt;
     __syncthreads();
     long long t = 0;
-    for (int w = 0; w < WARPS; ++w) t += s[w];
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s[w];
     __syncthreads();
     return t;
 }
@@ -822,7 +872,7 @@ __device__ __forceinline__ Survivors block_offsets(const Bufs& b, int nb, int bi
     long long t[4] = {0, 0, 0, 0};
 #pragma unroll
     for (int k = 0; k < 4; ++k)
-        for (int w = 0; w < WARPS; ++w) t[k] += s[k][w];
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t[k] += s[k][w];
     __syncthreads();
     Survivors r;
     r.base_a = t[0];

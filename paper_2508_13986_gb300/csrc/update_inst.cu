@@ -30,9 +30,10 @@ static void kernels_of(Kernels* k) {
     k->persist = (void*)k_persistent<N, DYN, Real>;
     k->batch = (void*)k_batch<N, DYN, Real>;
     k->batch_teams = (void*)k_batch_teams<N, DYN, Real>;
-    k->pre[0] = (void*)k_grow_waves<N, DYN, Real>;
-    k->pre[1] = (void*)k_halo<N, Real, 1>;
-    k->npre = 2;
+    k->pre[0] = (void*)k_waves_list<N, DYN, Real>;
+    k->pre[1] = (void*)k_grow_list<N, Real>;
+    k->pre[2] = (void*)k_halo<N, Real, 1>;
+    k->npre = 3;
     k->post[0] = (void*)k_faces<N, DYN, Real>;
     k->post[1] = (void*)k_apply<N, Real>;
     k->npost = 2;

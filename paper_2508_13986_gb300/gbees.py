@@ -27,7 +27,7 @@ GBEES_DYN_CONSTANT, GBEES_DYN_LINEAR, GBEES_DYN_LORENZ63, GBEES_DYN_LORENZ63_SHI
 GBEES_LIM_MC, GBEES_LIM_NONE, GBEES_LIM_LW = range(3)
 GBEES_FP64, GBEES_FP32 = 0, 1
 GBEES_LAUNCH_AUTO, GBEES_LAUNCH_PERSISTENT, GBEES_LAUNCH_GRAPH, GBEES_LAUNCH_DIRECT = range(4)
-GBEES_ORDER_KEY, GBEES_ORDER_MORTON, GBEES_ORDER_NONE, GBEES_ORDER_KEY_MIXED = range(4)
+GBEES_ORDER_KEY, GBEES_ORDER_MORTON, GBEES_ORDER_NONE, GBEES_ORDER_KEY_MIXED, GBEES_ORDER_ROW_MORTON = range(5)
 
 
 class gbees_config(ctypes.Structure):
@@ -47,6 +47,8 @@ class gbees_config(ctypes.Structure):
         ("table_factor", ctypes.c_double),
         ("launch_mode", ctypes.c_int32),
         ("storage_order", ctypes.c_int32),
+        ("block_threads", ctypes.c_int32),
+        ("persist_max_entries", ctypes.c_int64),
     ]
 
 
@@ -269,7 +271,8 @@ def make_config(n: int, dynamics: int, params: Sequence[float], h: Sequence[floa
                 thr_rel: float = 1e-7, cfl: float = 0.9, prune_interval: int = 20, precision: int = GBEES_FP64,
                 limiter: int = GBEES_LIM_MC, max_cells: int = 1 << 20, table_factor: float = 2.0,
                 probe_width: int = 1, launch_mode: int = GBEES_LAUNCH_AUTO,
-                storage_order: int = GBEES_ORDER_KEY) -> gbees_config:
+                storage_order: int = GBEES_ORDER_KEY, block_threads: int = 0,
+                persist_max_entries: int = 0) -> gbees_config:
     c = gbees_config()
     c.n, c.dynamics = int(n), int(dynamics)
     for k, v in enumerate(params):
@@ -282,6 +285,8 @@ def make_config(n: int, dynamics: int, params: Sequence[float], h: Sequence[floa
     c.probe_width, c.max_cells, c.table_factor = int(probe_width), int(max_cells), float(table_factor)
     c.launch_mode = int(launch_mode)
     c.storage_order = int(storage_order)
+    c.block_threads = int(block_threads)
+    c.persist_max_entries = int(persist_max_entries)
     return c
 
 
@@ -444,8 +449,10 @@ def propagate_batch(grids: Sequence["Grid"], t_end: Sequence[float], max_steps: 
 
 def grid_for_workload(w, precision: int = GBEES_FP64, max_cells: int = 1 << 20, device: str = "cuda:0",
                       probe_width: int = 1, table_factor: float = 2.0, launch_mode: int = GBEES_LAUNCH_AUTO,
-                      storage_order: int = GBEES_ORDER_KEY) -> Grid:
+                      storage_order: int = GBEES_ORDER_KEY, block_threads: int = 0,
+                      persist_max_entries: int = 0) -> Grid:
     """A Grid configured for a paper_2508_13986_gb300.workloads.Workload."""
     cfg = make_config(w.n, w.dynamics, w.params, w.h, w.x0, w.thr_rel, w.cfl, w.prune_interval, precision,
-                      w.limiter, max_cells, table_factor, probe_width, launch_mode, storage_order)
+                      w.limiter, max_cells, table_factor, probe_width, launch_mode, storage_order, block_threads,
+                      persist_max_entries)
     return Grid(cfg, device)

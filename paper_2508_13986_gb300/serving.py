@@ -7,12 +7,17 @@ keeps every admitted grid resident on the device between its propagation
 segments and measurement updates, and advances all grids in service together:
 one round is one batched launch per model family (dimension, dynamics) in which
 every grid takes at most `round_steps` steps towards its next segment target
-(gbees_batch_propagate with a step cap). The families' launches run at the
-same time, each on its own CUDA stream from its own host thread and capped to
-a share of the GPU's resident blocks in proportion to the family's active
-cells, and the measurement updates that came due (Eq. 4) follow on the same
-stream and thread. Between rounds, finished grids are read out and released,
-and requests that arrived meanwhile join the next round.
+(gbees_batch_propagate with a step cap), every grid of the family working in
+the same launch; the measurement updates that came due (Eq. 4) follow. By
+default the families' launches follow one another, each with every block the
+GPU holds; with concurrent_families they run at the same time, each on its own
+CUDA stream from its own host thread and capped to a share of the resident
+blocks in proportion to the family's active cells. (Measured on GB300 with the
+bench's stream: the serial rounds are faster, 1.18 against 0.71 G
+cell-updates/s in FP32 and 1.04 against 0.46 in FP64, with lower latency: a
+step of a family's grids is latency-bound and gains from every block.) Between
+rounds, finished grids are read out and released, and requests that arrived
+meanwhile join the next round.
 
 Every grid runs the same phases with the same arithmetic whether it is served
 alone or in a mix, so its result does not depend on the mix.
@@ -81,7 +86,7 @@ class Server:
     mode: str = "batched"           # or "single"
     keep_density: bool = False
     realtime: bool = True            # arrivals follow the wall clock
-    concurrent_families: bool = True # the families' rounds overlap on the device
+    concurrent_families: bool = False  # the families' rounds overlap on the device (see above)
     stats: Dict[str, float] = field(default_factory=dict)
     family_windows: List[Dict[str, float]] = field(default_factory=list)  # launch intervals of the last run
     _streams: Dict[Tuple[int, int], object] = field(default_factory=dict)

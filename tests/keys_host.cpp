@@ -58,6 +58,10 @@ void keys_morton(const uint64_t* keys, size_t count, int n, int b, uint64_t* out
     for (size_t i = 0; i < count; ++i) out[i] = gbees::morton_code(keys[i], n, b);
 }
 
+void keys_row_morton(const uint64_t* keys, size_t count, int n, int b, uint64_t* out) {
+    for (size_t i = 0; i < count; ++i) out[i] = gbees::row_morton_code(keys[i], n, b);
+}
+
 void keys_mix(const uint64_t* x, size_t count, uint64_t* out) {
     for (size_t i = 0; i < count; ++i) out[i] = mix64(x[i]);
 }

@@ -5,7 +5,7 @@ import pytest
 
 from paper_2508_13986_gb300 import gbees
 from paper_2508_13986_gb300 import workloads as W
-from paper_2508_13986_gb300.autotune import Shape, pick_best, tune_grid
+from paper_2508_13986_gb300.autotune import Shape, crossover, pick_best, tune_grid
 
 
 def test_pick_best_takes_the_fastest_minimum_over_repeats():
@@ -21,21 +21,36 @@ def test_pick_best_needs_a_candidate():
         pick_best([], lambda s: 1.0)
 
 
+def test_crossover_separates_persistent_wins_from_graph_wins():
+    # (pool entries, ms per update persistent, ms per update graph)
+    s = [(4000, 1.0, 3.0), (20000, 1.0, 1.5), (30000, 1.0, 1.2), (40000, 1.1, 1.0), (60000, 1.2, 1.1),
+         (90000, 1.0, 1.2), (300000, 2.0, 1.0)]
+    assert crossover(s) == 30000       # one noisy win at 90000 beyond it does not move it
+    s2 = [(4000, 1.0, 3.0), (20000, 1.0, 1.5), (40000, 1.1, 1.0), (60000, 1.0, 1.2), (90000, 1.2, 1.1)]
+    assert crossover(s2) == 20000      # a tie (one sample misplaced either way) goes to the smaller size
+    assert crossover([(10, 2.0, 1.0), (20, 2.0, 1.0)]) == 0
+    assert crossover([(10, 1.0, 2.0), (20, 1.0, 2.0)]) == 20
+    with pytest.raises(ValueError):
+        crossover([])
+
+
 @pytest.mark.gpu
 def test_tuned_shape_gives_the_default_result():
     import __graft_entry__ as ge
 
     ge.build()
     w = W.lorenz63(h=0.5, t_end=0.05, prune_interval=4)
-    best, times = tune_grid(w, t_probe=0.01, probe_widths=(1, 8), max_cells=1 << 16)
+    best, times = tune_grid(w, t_probe=0.01, probe_widths=(1, 8), max_cells=1 << 16, block_threads=(128, 256))
     assert best in times and all(t > 0 for t in times.values())
     out = []
-    for shape in (Shape(), best):
+    for shape in (Shape(), best, Shape(1, gbees.GBEES_LAUNCH_GRAPH, 64), Shape(1, gbees.GBEES_LAUNCH_DIRECT, 128)):
         cfg = gbees.make_config(w.n, w.dynamics, w.params, w.h, w.x0, w.thr_rel, w.cfl, w.prune_interval,
-                                gbees.GBEES_FP64, w.limiter, 1 << 16, 2.0, shape.probe_width, shape.launch_mode)
+                                gbees.GBEES_FP64, w.limiter, 1 << 16, 2.0, shape.probe_width, shape.launch_mode,
+                                block_threads=shape.block_threads)
         g = gbees.Grid(cfg)
         g.init_gaussian(w.mean, w.cov)
         g.propagate(w.t_end)
         out.append(g.read_cells())
         g.close()
-    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    for o in out[1:]:
+        assert np.array_equal(out[0][0], o[0]) and np.array_equal(out[0][1], o[1])

@@ -71,12 +71,14 @@ def test_served_results_match_the_oracle_grid_by_grid():
 
 
 def test_model_families_run_at_the_same_time_on_the_device():
-    """Lorenz '63 and Lorenz '96 requests in service together: each family's
-    round is issued on its own stream from its own host thread with a share of
-    the GPU's blocks, so their launches overlap in device time (CUDA event
-    intervals around each family's launch, on its stream)."""
+    """Lorenz '63 and Lorenz '96 requests in service together with concurrent
+    family rounds: each family's round is issued on its own stream from its own
+    host thread with a share of the GPU's blocks, so their launches overlap in
+    device time (CUDA event intervals around each family's launch, on its
+    stream), and the results are those of the serial rounds, bit for bit."""
     stream = small_stream(12, seed=25, rate=1e6)
-    srv = Server(precision=gbees.GBEES_FP32, realtime=False, round_steps=40)
+    srv = Server(precision=gbees.GBEES_FP32, realtime=False, round_steps=40, concurrent_families=True,
+                 keep_density=True)
     res = srv.run(stream)
     assert len(res) == len(stream) and srv.stats["failed"] == 0
     wins = srv.family_windows
@@ -85,6 +87,9 @@ def test_model_families_run_at_the_same_time_on_the_device():
     assert l63 and l96
     overlap = max(min(a["end_ms"], b["end_ms"]) - max(a["start_ms"], b["start_ms"]) for a in l63 for b in l96)
     assert overlap > 0.0, wins
+    serial = Server(precision=gbees.GBEES_FP32, realtime=False, round_steps=40, keep_density=True).run(stream)
+    for a, b in zip(res, serial):
+        assert a.steps == b.steps and np.array_equal(a.idx, b.idx) and np.array_equal(a.p, b.p)
 
 
 def test_admission_respects_the_memory_budget():

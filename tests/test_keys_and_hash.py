@@ -29,6 +29,7 @@ def lib(tmp_path_factory):
     L.keys_unpack.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
     L.keys_mix.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
     L.keys_morton.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
+    L.keys_row_morton.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
     L.probe_lengths.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int,
                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     L.probe_lengths.restype = ctypes.c_longlong
@@ -128,6 +129,36 @@ def test_morton_code_is_a_bijection_of_the_keys(lib, n):
     assert [int(c) for c in morton(lib, ones, n, b)] == [(1 << (n * b)) - 1, 0]
     if n == 1:
         assert np.array_equal(codes, keys)                      # one field: the key itself
+
+
+def row_morton(lib, keys, n, b):
+    keys = np.ascontiguousarray(keys, dtype=U64)
+    out = np.zeros_like(keys)
+    lib.keys_row_morton(keys.ctypes.data, keys.shape[0], n, b, out.ctypes.data)
+    return out
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 6])
+def test_row_morton_code_keeps_rows_whole_and_orders_them_on_the_z_curve(lib, n):
+    """A bijection of the keys within n*b bits; cells that differ only in the
+    last index are consecutive in code order exactly as in key order; the rows
+    (the other n - 1 indices) are in Morton order."""
+    b = key_bits(n)
+    rng = np.random.default_rng(190 + n)
+    keys = np.unique(rng.integers(0, 1 << (n * b), size=20000, dtype=np.uint64, endpoint=False))
+    codes = row_morton(lib, keys, n, b)
+    assert np.unique(codes).size == keys.size and int(codes.max()) < (1 << (n * b))
+    if n == 1:
+        assert np.array_equal(codes, keys)
+        return
+    mask = np.uint64((1 << b) - 1)
+    assert np.array_equal(codes & mask, keys & mask)                 # the last field is kept
+    rows = keys >> np.uint64(b)
+    assert np.array_equal(codes >> np.uint64(b), morton(lib, rows, n - 1, b))  # rows on the Z curve
+    # a run of one row: consecutive last indices stay consecutive
+    base = int(keys[0]) & ~int(mask)
+    run = np.array([base | i for i in range(5, 12)], dtype=U64)
+    assert np.all(np.diff(row_morton(lib, run, n, b).astype(np.int64)) == 1)
 
 
 def test_morton_order_keeps_face_neighbours_closer_than_key_order(lib):
