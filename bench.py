@@ -170,17 +170,17 @@ class ClockSampler:
 # ------------------------------------------------------------------ runs
 
 def auto_max_cells(w, precision, dev) -> int:
-    """Pool capacity for a single-grid workload: 24 times its initial set
-    (growth measured up to 18x over the 6-D h = 0.25 horizon, with the halo), a
-    power of two, at least 2^24 (coarser grids grow more in relative terms),
-    and halved while the workspace would take more than 80 % of the device
-    memory."""
+    """Pool capacity for a single-grid workload: its pool growth times its
+    initial set (24 by default: the pool of the 6-D h = 0.25 horizon peaks at
+    18x; 48 for the paper's Lorenz '96 case, which peaks at 38x), a power of
+    two, at least 2^24 (coarser grids grow more in relative terms), and halved
+    while the workspace would take more than 80 % of the device memory."""
     import torch
 
     from paper_2508_13986_gb300 import gbees, workloads
 
     cap = 1 << 24
-    while cap < 24 * workloads.initial_cells_estimate(w):
+    while cap < w.pool_growth * workloads.initial_cells_estimate(w):
         cap <<= 1
     total = torch.cuda.get_device_properties(dev).total_memory
     while cap > (1 << 24):
@@ -543,7 +543,7 @@ def time_batch(args, ws, precision, dev, rank, world):
     }
 
 
-def serving_forms(args, local):
+def serving_forms(args, local, block_threads=0):
     """The request stream served three ways on one GPU: batched FP32, batched
     FP64 (continuous batching, model families overlapping on the device), and
     the plain FP64 form (one request at a time, gbees_propagate)."""
@@ -557,10 +557,11 @@ def serving_forms(args, local):
     out = {}
     for tag, prec, mode in (("batched_f32", gbees.GBEES_FP32, "batched"), ("batched_f64", gbees.GBEES_FP64, "batched"),
                             ("single_f64", gbees.GBEES_FP64, "single")):
-        Server(precision=prec, device=f"cuda:{local}", mode=mode, realtime=False).run(warm)
+        Server(precision=prec, device=f"cuda:{local}", mode=mode, realtime=False,
+               block_threads=block_threads).run(warm)
         clocks = ClockSampler(local)
         clocks.start()
-        srv = Server(precision=prec, device=f"cuda:{local}", mode=mode, realtime=True)
+        srv = Server(precision=prec, device=f"cuda:{local}", mode=mode, realtime=True, block_threads=block_threads)
         srv.run(stream)
         st = dict(srv.stats)
         st["clocks"] = clocks.stop()
@@ -725,8 +726,9 @@ def main_ours(args):
                 "e2e": r["e2e"], "roofline": r["roofline"], "persistent_us_per_step": r["persistent_us_per_step"],
                 "gpu_launches": r["gpu_launches"], "clocks": r["clocks"]}
         if rank == 0:
-            sv = serving_forms(args, local)
-            extras["serving"] = {"requests": args.requests, "rate_per_s": args.rate,
+            bt = (main.get("launch_shape") or {}).get("block_threads", 0)
+            sv = serving_forms(args, local, bt)
+            extras["serving"] = {"requests": args.requests, "rate_per_s": args.rate, "block_threads": bt,
                                  "mix": "70 % Lorenz '63, 30 % Lorenz '96 6-D; 0-3 corrections each",
                                  "forms": {k: {x: v[x] for x in ("cell_updates_per_s", "requests_per_s", "latency_p50_s",
                                                                  "latency_p99_s", "wall_s", "failed", "clocks")}

@@ -507,7 +507,11 @@ __device__ __forceinline__ T wave_of(const T* Q, const T* U, long long cap, cons
     const T ul = U[d * cap + y];
     const T uh = up >= 0 ? U[d * cap + up] : (T)0;
     wlo = Py - Pm;
-    return fmadd(neg_part(uh), Pp - Py, pos_part(ul) * wlo);
+    // one product in the usual case (flow through the cell, or out of it on one
+    // side only); a cell that both faces flow into takes the second term too
+    const bool in_lo = gt0(ul), in_hi = lt0(uh);
+    const T G = (in_lo ? ul : (in_hi ? uh : (T)0)) * (in_lo ? wlo : Pp - Py);
+    return (in_lo && in_hi) ? fmadd(uh, Pp - Py, G) : G;
 }
 
 // Pass 1, one thread per entry c of [0, ncell) (active and halo), all

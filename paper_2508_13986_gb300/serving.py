@@ -87,6 +87,7 @@ class Server:
     keep_density: bool = False
     realtime: bool = True            # arrivals follow the wall clock
     concurrent_families: bool = False  # the families' rounds overlap on the device (see above)
+    block_threads: int = 0           # launch shape of the grids' step kernels (0: the library's default)
     stats: Dict[str, float] = field(default_factory=dict)
     family_windows: List[Dict[str, float]] = field(default_factory=list)  # launch intervals of the last run
     _streams: Dict[Tuple[int, int], object] = field(default_factory=dict)
@@ -102,7 +103,7 @@ class Server:
 
     def _admit(self, rid: int, w: Workload, arrival: float, now: float) -> _Active:
         cfg = gbees.make_config(w.n, w.dynamics, w.params, w.h, w.x0, w.thr_rel, w.cfl, w.prune_interval,
-                                self.precision, w.limiter, capacity_for(w))
+                                self.precision, w.limiter, capacity_for(w), block_threads=self.block_threads)
         g = gbees.Grid(cfg, self.device, stream=self._stream_of((w.n, w.dynamics)))
         a = _Active(rid, w, arrival, now, g, gbees.gbees_workspace_bytes(cfg), w.segments())
         try:
