@@ -220,6 +220,13 @@ int gbees_batch_propagate(gbees_ctx* const* ctxs, int32_t count, const double* t
  * queue form. max_blocks >= 0. */
 int gbees_set_batch_blocks(gbees_ctx* ctx, int32_t max_blocks);
 
+/* Blocks of the persistent step-loop kernel of ctx, at most (0, the default:
+ * one per SM). A grid of 10^4 cells has a few cells per block at one block per
+ * SM; fewer blocks make each grid barrier cheaper (fewer arrivals) at the cost
+ * of more cells per block. The result does not depend on it (sums are exact).
+ * max_blocks >= 0. */
+int gbees_set_persist_blocks(gbees_ctx* ctx, int32_t max_blocks);
+
 /* Bayesian measurement update (Eq. 4) with the Gaussian likelihood
  * exp(-1/2 (y - x_H)^T R^{-1} (y - x_H)) of m measured components
  * x_H = (x[H_idx[0]], ..., x[H_idx[m-1]]) at the cell centres, followed by a

@@ -78,6 +78,7 @@ struct gbees_ctx {
     long long persist_max_cells = 1ll << 18;  // AUTO: persistent kernel up to this many pool entries
     int step_threads = THREADS;                // threads per block of the graph/direct step kernels
     int batch_blocks = 0;  // blocks of a batched launch led by this context at most (0: all resident)
+    int persist_blocks = 0;  // blocks of the persistent kernel at most (0: one per SM)
     // blocks of the step kernels of the graph and direct paths: as many as the
     // GPU holds resident for each (SMs x blocks per SM by occupancy), so that one
     // wave covers the grid-stride loops: pre[0..npre), link, post[0..npost)
@@ -795,6 +796,12 @@ int gbees_set_batch_blocks(gbees_ctx* ctx, int32_t max_blocks) {
     return GBEES_OK;
 }
 
+int gbees_set_persist_blocks(gbees_ctx* ctx, int32_t max_blocks) {
+    if (!ctx || max_blocks < 0) return GBEES_EINVAL;
+    ctx->persist_blocks = max_blocks;
+    return GBEES_OK;
+}
+
 int gbees_set_wait_limit(gbees_ctx* ctx, int64_t spins, int32_t extra_arrivals) {
     if (!ctx || spins < 1 || extra_arrivals < 0 || extra_arrivals > GRID_MAX) return GBEES_EINVAL;
     ctx->m.spin_limit = spins;
@@ -979,7 +986,8 @@ int gbees_propagate(gbees_ctx* ctx, double t_end, gbees_stats* stats) {
             long long max_pool = limit;
             void* args[] = {&ctx->m, &ctx->b, &max_steps, &max_pool};
             cudaEventRecord(ctx->pev[0], s);
-            if (!cuda_ok(ctx, cudaLaunchCooperativeKernel(ctx->kern.persist, dim3(ctx->persist_grid), dim3(THREADS), args, 0, s),
+            const int pg = ctx->persist_blocks > 0 ? std::min(ctx->persist_blocks, ctx->persist_grid) : ctx->persist_grid;
+            if (!cuda_ok(ctx, cudaLaunchCooperativeKernel(ctx->kern.persist, dim3(pg), dim3(THREADS), args, 0, s),
                          "propagate"))
                 return ctx->status;
             cudaEventRecord(ctx->pev[1], s);

@@ -77,8 +77,9 @@ struct alignas(256) DevScalars {
     unsigned long long tmp_ord;  // scratch maximum (init)
     long long loop_iter;  // iterations of the device-side step loop in the current graph launch
     long long graph_kernels;  // kernels executed by graph launches (counted on the device)
-    unsigned int bar_count;   // grid barrier of the persistent kernel: arrivals
-    unsigned int bar_gen;     // and generation
+    // grid barrier of the persistent kernel: arrivals in the low 32 bits,
+    // generation in the high 32 bits
+    unsigned long long bar_word;
     // SM cycles spent by block 0 of the persistent kernel per phase (grow,
     // halo, link, faces, apply, prune, step scalars) and the steps they cover
     long long phase_cycles[8];
@@ -825,26 +826,40 @@ __device__ __forceinline__ Combined combine_partials(const Partial* part, int nb
 // spin_limit polls (BARRIER_SPIN_LIMIT by default: about two seconds), sets
 // ST_ETIMEOUT, and returns false; callers then leave.
 constexpr long long BARRIER_SPIN_LIMIT = 1ll << 26;
+
+__device__ __forceinline__ unsigned long long atom_add_acq_rel_gpu(unsigned long long* p, unsigned long long v) {
+    unsigned long long old;
+    asm volatile("atom.add.acq_rel.gpu.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+    return old;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_gpu(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
 // Barrier of the nb blocks that share the grid whose scalars are sc (the whole
 // launch, or a team of a batched launch); every block of the team must be
 // resident (cooperative launch). Bounded: gives up with ST_ETIMEOUT.
 __device__ __forceinline__ bool grid_barrier(DevScalars* sc, int nb, long long spin_limit = BARRIER_SPIN_LIMIT) {
     __shared__ int s_ok;
-    unsigned int* bar = &sc->bar_count;
+    unsigned long long* word = &sc->bar_word;
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned int* vgen = &sc->bar_gen;
-        const unsigned int gen = *vgen;
-        __threadfence();
-        const unsigned int arrived = atomicAdd(bar, 1u);
+        // one release-acquire add per block: it publishes the block's writes
+        // and counts the arrival; the last to arrive clears the count and opens
+        // the next generation with a second add on the same word (a count of
+        // nb plus 2^32 - nb carries into the generation), so the waiters'
+        // acquire loads see every block's writes once the generation moves
+        const unsigned long long old = atom_add_acq_rel_gpu(word, 1ull);
+        const unsigned int gen = (unsigned int)(old >> 32);
         int ok = 1;
-        if (arrived == (unsigned int)nb - 1u) {
-            *(volatile unsigned int*)bar = 0u;
-            __threadfence();
-            atomicAdd(&sc->bar_gen, 1u);
+        if ((unsigned int)old == (unsigned int)nb - 1u) {
+            atom_add_acq_rel_gpu(word, (1ull << 32) - (unsigned long long)(unsigned int)nb);
         } else {
             long long spins = 0;
-            while (*vgen == gen) {
+            while ((unsigned int)(ld_acquire_gpu(word) >> 32) == gen) {
                 if (*(volatile int*)&sc->error) { ok = 0; break; }
                 if (++spins > spin_limit) {
                     set_error(sc, ST_ETIMEOUT);
@@ -854,7 +869,6 @@ __device__ __forceinline__ bool grid_barrier(DevScalars* sc, int nb, long long s
                 __nanosleep(32);
             }
         }
-        __threadfence();
         s_ok = ok && !*(volatile int*)&sc->error;
     }
     __syncthreads();

@@ -101,6 +101,7 @@ _SIGNATURES = {
     "gbees_get_status": (ctypes.c_int, [_vp]),
     "gbees_set_wait_limit": (ctypes.c_int, [_vp, _i64, _i32]),
     "gbees_set_batch_blocks": (ctypes.c_int, [_vp, _i32]),
+    "gbees_set_persist_blocks": (ctypes.c_int, [_vp, _i32]),
     "gbees_profile_control": (ctypes.c_int, [_vp, _i32, _i32]),
     "gbees_profile_read": (ctypes.c_int, [_vp, _P(gbees_profile)]),
     "gbees_last_error": (ctypes.c_char_p, [_vp]),
@@ -189,6 +190,10 @@ def gbees_set_wait_limit(ctx: int, spins: int, extra_arrivals: int = 0) -> int:
 
 def gbees_set_batch_blocks(ctx: int, max_blocks: int) -> int:
     return int(_f("gbees_set_batch_blocks")(_vp(ctx), int(max_blocks)))
+
+
+def gbees_set_persist_blocks(ctx: int, max_blocks: int) -> int:
+    return int(_f("gbees_set_persist_blocks")(_vp(ctx), int(max_blocks)))
 
 
 def gbees_get_status(ctx: int) -> int:
