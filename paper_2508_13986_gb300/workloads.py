@@ -227,12 +227,17 @@ def capacity_for(w: Workload) -> int:
     return int(min(1 << 24, max(1 << 15, math.ceil(want / 4096.0) * 4096)))
 
 
-def paper_e1(thr_rel: float = 1e-7, prune_interval: int = 20) -> Workload:
+def paper_e1(thr_rel: float = 1e-3, prune_interval: int = 20) -> Workload:
     """The paper's Lorenz '63 validation case (Sec. 5.1.1): the shifted form with
     (sigma, b, r) = (4, 1, 48), initial Gaussian at (-11.5, -10, 9.5) with unit
     standard deviations, h = 0.5 (half the standard deviation, Table 2), CFL
-    1.0, a measurement y = x3 = -8 with sigma_y = 1 at t = 1, end at t = 2. The
-    paper does not state its threshold: thr_rel is this library's reading."""
+    1.0, a measurement y = x3 = -8 with sigma_y = 1 at t = 1, end at t = 2.
+
+    The paper does not state its threshold. A relative threshold of 1e-3 of the
+    largest value gives the burden Table 2 prints for this case (about 24k cells
+    at most, about 960 steps, about 6.5e6 cell computations): 972 steps and
+    7.2e6 cell updates straight to the end, 1.8e4 active cells at most. Finer
+    thresholds grow all three (1e-7: 1303 steps, 3.3e7 updates, 5.4e4 cells)."""
     meas = [Measurement(1.0, np.array([-8.0]), np.array([[1.0]]), np.array([2], dtype=np.int32))]
     return Workload(name="paper_e1", n=3, dynamics=DYN_LORENZ63_SHIFTED, params=(4.0, 1.0, 48.0),
                     h=(0.5, 0.5, 0.5), mean=(-11.5, -10.0, 9.5), cov=np.eye(3), thr_rel=thr_rel, cfl=1.0,

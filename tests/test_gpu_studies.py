@@ -66,10 +66,8 @@ def test_paper_e1_full_run_matches_the_oracle_and_is_plausible_against_table_2()
     """The paper's own Lorenz '63 case through the library, FP64, read every
     0.05: the oracle's steps, cell updates and active cells at every read
     (tests/golden/paper_e1_counts.txt, written by the oracle alone), and
-    steps, largest grid and cell updates within small factors of Table 2.
-    Table 2 cannot be matched: the paper does not state its threshold (this
-    run uses 1e-7 of the maximum), and its grid counts may exclude cells this
-    method keeps."""
+    steps, largest grid and cell updates within small factors of Table 2 (the
+    relative threshold 1e-3 is the reading that reproduces it)."""
     import __graft_entry__ as ge
     from paper_2508_13986_gb300 import gbees
     from paper_2508_13986_gb300 import workloads as W
@@ -93,9 +91,9 @@ def test_paper_e1_full_run_matches_the_oracle_and_is_plausible_against_table_2()
     steps = sum(r[1] for r in rows)
     updates = sum(r[2] for r in rows)
     peak = max(r[3] for r in rows)
-    assert 0.5 <= steps / ref["integration_steps"] <= 2.0, steps
-    assert 0.5 <= peak / ref["max_grid_size"] <= 4.0, peak
-    assert 0.5 <= updates / ref["cell_computations"] <= 8.0, updates
+    assert 0.8 <= steps / ref["integration_steps"] <= 1.25, steps
+    assert 0.5 <= peak / ref["max_grid_size"] <= 2.0, peak
+    assert 0.5 <= updates / ref["cell_computations"] <= 2.0, updates
 
 
 @pytest.mark.gpu
