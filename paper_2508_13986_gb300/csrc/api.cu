@@ -987,6 +987,9 @@ int gbees_propagate(gbees_ctx* ctx, double t_end, gbees_stats* stats) {
             void* args[] = {&ctx->m, &ctx->b, &max_steps, &max_pool};
             cudaEventRecord(ctx->pev[0], s);
             const int pg = ctx->persist_blocks > 0 ? std::min(ctx->persist_blocks, ctx->persist_grid) : ctx->persist_grid;
+            // the kernel's barriers count arrivals from zero
+            if (!cuda_ok(ctx, cudaMemsetAsync(&ctx->b.sc->bar_seq, 0, sizeof(unsigned long long), s), "propagate"))
+                return ctx->status;
             if (!cuda_ok(ctx, cudaLaunchCooperativeKernel(ctx->kern.persist, dim3(pg), dim3(THREADS), args, 0, s),
                          "propagate"))
                 return ctx->status;

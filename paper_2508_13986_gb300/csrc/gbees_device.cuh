@@ -77,9 +77,12 @@ struct alignas(256) DevScalars {
     unsigned long long tmp_ord;  // scratch maximum (init)
     long long loop_iter;  // iterations of the device-side step loop in the current graph launch
     long long graph_kernels;  // kernels executed by graph launches (counted on the device)
-    // grid barrier of the persistent kernel: arrivals in the low 32 bits,
+    // grid barrier of a team of a batched launch: arrivals in the low 32 bits,
     // generation in the high 32 bits
     unsigned long long bar_word;
+    // grid barrier of the persistent kernel: arrivals since the launch began
+    // (cleared by the host before every persistent launch)
+    unsigned long long bar_seq;
     // SM cycles spent by block 0 of the persistent kernel per phase (grow,
     // halo, link, faces, apply, prune, step scalars) and the steps they cover
     long long phase_cycles[8];
@@ -753,18 +756,20 @@ __device__ __forceinline__ void block_partial(Partial* part, long long (&d)[NDIG
         s_rt[wid] = rk;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        Partial p;
-        unsigned long long mm = 0, rr = 0;
-        for (int q = 0; q < NDIG; ++q) p.acc[q] = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-            for (int q = 0; q < NDIG; ++q) p.acc[q] += s_acc[w][q];
-            mm = max(mm, s_mx[w]);
-            rr = max(rr, s_rt[w]);
-        }
-        p.maxq_ord = mm;
-        p.rate_bits = rr;
-        part[bi] = p;
+    // one thread per digit and per maximum folds the warps' values
+    const int q = threadIdx.x, nw = (int)(blockDim.x >> 5);
+    if (q < NDIG) {
+        long long a = 0;
+        for (int w = 0; w < nw; ++w) a += s_acc[w][q];
+        part[bi].acc[q] = a;
+    } else if (q == NDIG) {
+        unsigned long long mm = 0;
+        for (int w = 0; w < nw; ++w) mm = max(mm, s_mx[w]);
+        part[bi].maxq_ord = mm;
+    } else if (q == NDIG + 1) {
+        unsigned long long rr = 0;
+        for (int w = 0; w < nw; ++w) rr = max(rr, s_rt[w]);
+        part[bi].rate_bits = rr;
     }
     __syncthreads();
 }
@@ -808,15 +813,29 @@ __device__ __forceinline__ Combined combine_partials(const Partial* part, int nb
         s_rt[wid] = rt;
     }
     __syncthreads();
-    Combined c;
-    for (int q = 0; q < NDIG; ++q) c.acc[q] = 0;
-    c.maxq_ord = 0;
-    c.rate_bits = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-        for (int q = 0; q < NDIG; ++q) c.acc[q] += s_acc[w][q];
-        c.maxq_ord = max(c.maxq_ord, s_mo[w]);
-        c.rate_bits = max(c.rate_bits, s_rt[w]);
+    // one thread per digit and per maximum folds the warps' values; every
+    // thread then reads the results
+    __shared__ unsigned long long s_fin[NDIG + 2];
+    const int q = threadIdx.x, nw = (int)(blockDim.x >> 5);
+    if (q < NDIG) {
+        long long a = 0;
+        for (int w = 0; w < nw; ++w) a += s_acc[w][q];
+        s_fin[q] = (unsigned long long)a;
+    } else if (q == NDIG) {
+        unsigned long long mm = 0;
+        for (int w = 0; w < nw; ++w) mm = max(mm, s_mo[w]);
+        s_fin[q] = mm;
+    } else if (q == NDIG + 1) {
+        unsigned long long rr = 0;
+        for (int w = 0; w < nw; ++w) rr = max(rr, s_rt[w]);
+        s_fin[q] = rr;
     }
+    __syncthreads();
+    Combined c;
+#pragma unroll
+    for (int k = 0; k < NDIG; ++k) c.acc[k] = (long long)s_fin[k];
+    c.maxq_ord = s_fin[NDIG];
+    c.rate_bits = s_fin[NDIG + 1];
     __syncthreads();
     return c;
 }
@@ -860,6 +879,39 @@ __device__ __forceinline__ bool grid_barrier(DevScalars* sc, int nb, long long s
         } else {
             long long spins = 0;
             while ((unsigned int)(ld_acquire_gpu(word) >> 32) == gen) {
+                if (*(volatile int*)&sc->error) { ok = 0; break; }
+                if (++spins > spin_limit) {
+                    set_error(sc, ST_ETIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        s_ok = ok && !*(volatile int*)&sc->error;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Barrier k (1, 2, ...) of a launch whose nb blocks all take part in every
+// barrier, on a counter that was zero when the launch began: the barrier is
+// complete once k * nb arrivals are counted. One release-acquire add per block
+// and no reset, so the last arrival releases the waiters directly. Bounded like
+// grid_barrier.
+__device__ __forceinline__ bool grid_barrier_seq(DevScalars* sc, int nb, unsigned long long& k,
+                                                 long long spin_limit = BARRIER_SPIN_LIMIT) {
+    __shared__ int s_ok;
+    unsigned long long* cnt = &sc->bar_seq;
+    __syncthreads();
+    k += 1;
+    if (threadIdx.x == 0) {
+        const unsigned long long target = k * (unsigned long long)(unsigned int)nb;
+        const unsigned long long old = atom_add_acq_rel_gpu(cnt, 1ull);
+        int ok = 1;
+        if (old + 1ull < target) {
+            long long spins = 0;
+            while (ld_acquire_gpu(cnt) < target) {
                 if (*(volatile int*)&sc->error) { ok = 0; break; }
                 if (++spins > spin_limit) {
                     set_error(sc, ST_ETIMEOUT);

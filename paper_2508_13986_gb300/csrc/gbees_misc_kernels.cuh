@@ -132,6 +132,7 @@ __global__ void k_reset(DevScalars* sc, double t0) {
     sc->loop_iter = 0;
     sc->graph_kernels = 0;
     sc->bar_word = 0;
+    sc->bar_seq = 0;
     for (int q = 0; q < 8; ++q) sc->phase_cycles[q] = 0;
     sc->phase_steps = 0;
 }

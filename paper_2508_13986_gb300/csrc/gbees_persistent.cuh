@@ -15,7 +15,8 @@
 // from the same per-block partials, so the scalars need no extra barrier;
 // block 0 of the grid writes them back.
 //
-// Barriers per step: grow + waves | halo | link | faces | apply; a prune adds
+// Barriers per step: grow + waves | halo | link | faces | apply (halo and link
+// are skipped in a step whose grow added and activated nothing); a prune adds
 // mark | scatter | status | compact | relink.
 #pragma once
 
@@ -47,17 +48,21 @@ __device__ __forceinline__ void normalisation(const Model& m, const Combined& c,
 // max_pool: the loop also stops after a step that leaves more pool entries
 // than that (the persistent kernel hands a grown grid to the graph path; every
 // block sees the same count, so all leave together).
+// seq: the nb blocks are the whole launch and sc->bar_seq was zero when it
+// began (the persistent kernel), so the barriers count arrivals without reset.
 template <int N, int DYN, typename T>
 __device__ __forceinline__ void step_loop(const Model& m, const Bufs& b, long long max_steps, int nb, int bi,
-                                          long long max_pool = 0x7fffffffffffffffll) {
+                                          long long max_pool = 0x7fffffffffffffffll, bool seq = false) {
     __shared__ StepShared ss;
     DevScalars* sc = b.sc;
     // The result is the same for every thread of the block: a warp that read
     // the error flag after another warp of the block had already raised it in
     // the next phase must not return while the others go on (their block
     // barriers would then pair with the wrong ones).
+    unsigned long long n_bar = 0;
     auto barrier = [&]() -> bool {
         if (nb == 1) return __syncthreads_and(!*(volatile int*)&sc->error) != 0;
+        if (seq) return grid_barrier_seq(sc, nb + m.bar_extra, n_bar, m.spin_limit);
         return grid_barrier(sc, nb + m.bar_extra, m.spin_limit);
     };
     StepView v = view_of(m, sc);
@@ -95,25 +100,32 @@ __device__ __forceinline__ void step_loop(const Model& m, const Bufs& b, long lo
         // stays put until the link phase)
         const long long n_ins = min(*(volatile long long*)&sc->N, m.cap);
         const long long n_active = *(volatile long long*)&sc->NA;
-        halo_body<N, T>(m, b, v, v.N_prev, n_ins, *(volatile long long*)&sc->n_act);
-        if (!barrier()) return;
-        mark(1);
-        v.N = min(n_ins + *(volatile long long*)&sc->n_halo, m.cap);
-        // link the new entries; CFL rates of the new active cells
-        {
-            const double r = fmax(rg, link_body<N, T>(m, b, v.N_prev, v.N, v.g, nb, bi));
-            long long zero[NDIG] = {0, 0, 0, 0, 0, 0};
-            block_partial(b.part, zero, -INFINITY, r, bi);
-        }
-        if (bi == 0 && threadIdx.x == 0) sc->N = v.N;  // read again only after the next grow
-        if (!barrier()) return;
-        mark(2);
-        // everyone has read the halo and activation counts: reset them
-        if (bi == 0 && threadIdx.x == 0) {
-            sc->n_halo = 0;
-            sc->n_act = 0;
-        }
-        {
+        const long long n_act = *(volatile long long*)&sc->n_act;
+        if (n_ins == v.N_prev && n_act == 0) {
+            // the grow added and activated nothing (every block reads the same
+            // counts): no halo to make, no entry to link, no new CFL rate
+            v.N = n_ins;
+            mark(1);
+            mark(2);
+        } else {
+            halo_body<N, T>(m, b, v, v.N_prev, n_ins, n_act);
+            if (!barrier()) return;
+            mark(1);
+            v.N = min(n_ins + *(volatile long long*)&sc->n_halo, m.cap);
+            // link the new entries; CFL rates of the new active cells
+            {
+                const double r = fmax(rg, link_body<N, T>(m, b, v.N_prev, v.N, v.g, nb, bi));
+                long long zero[NDIG] = {0, 0, 0, 0, 0, 0};
+                block_partial(b.part, zero, -INFINITY, r, bi);
+            }
+            if (bi == 0 && threadIdx.x == 0) sc->N = v.N;  // read again only after the next grow
+            if (!barrier()) return;
+            mark(2);
+            // everyone has read the halo and activation counts: reset them
+            if (bi == 0 && threadIdx.x == 0) {
+                sc->n_halo = 0;
+                sc->n_act = 0;
+            }
             Combined cr = combine_partials(b.part, nb);
             maxrate = max(maxrate, cr.rate_bits);
         }
@@ -248,7 +260,7 @@ __device__ __forceinline__ void step_loop(const Model& m, const Bufs& b, long lo
 template <int N, int DYN, typename T>
 __global__ void __launch_bounds__(THREADS, 1) k_persistent(const Model m, Bufs b, long long max_steps,
                                                            long long max_pool) {
-    step_loop<N, DYN, T>(m, b, max_steps, gridDim.x, blockIdx.x, max_pool);
+    step_loop<N, DYN, T>(m, b, max_steps, gridDim.x, blockIdx.x, max_pool, true);
 }
 
 // Resident blocks per SM of the batch kernels: the register cap (64) spills a

@@ -572,6 +572,14 @@ __device__ __forceinline__ T waves_new(const Model& m, const T* Q, const T* U, c
     return S;
 }
 
+// 0 - x as IEEE subtraction gives it, without FP64 arithmetic for doubles:
+// the sign flips, except that both zeros give +0.
+__device__ __forceinline__ double zero_minus(double x) {
+    const long long b = __double_as_longlong(x);
+    return __longlong_as_double((b << 1) == 0 ? 0ll : (b ^ (long long)0x8000000000000000ull));
+}
+__device__ __forceinline__ float zero_minus(float x) { return 0.0f - x; }
+
 // The flux pass's view of the step (pointers and constants in the arithmetic type).
 template <int N, typename T>
 struct FaceCtx {
@@ -620,7 +628,8 @@ __device__ __forceinline__ T face_flux(const Model& m, const FaceCtx<N, T>& fc, 
                                 : PL - q_or_zero<T>(fc.Q, fc.link[(long long)(2 * j) * cap + Llo]);
         } else {  // jump across the upper face of X
             const int Lup = fc.link[(long long)(2 * j + 1) * cap + X];
-            Wup = (Lup >= 0 && Lup < fc.nold) ? fc.wl[j * cap + Lup] : q_or_zero<T>(fc.Q, Lup) - P0;
+            Wup = (Lup >= 0 && Lup < fc.nold) ? fc.wl[j * cap + Lup]
+                  : (Lup >= 0 ? fc.Q[Lup] - P0 : zero_minus(P0));
         }
         // the limited high-resolution term 1/2 |u| (1 - dt |u| / h_j) phi W
         const T au = abs_bits(u);
@@ -629,13 +638,44 @@ __device__ __forceinline__ T face_flux(const Model& m, const FaceCtx<N, T>& fc, 
     return f;
 }
 
+// face_flux for the faces whose values all come from pass 1: X and the cell
+// upwind of the face were in the pool before this step's grow, and so was the
+// upper neighbour whose jump the limiter reads. The same operations on the
+// same values as face_flux gives those faces; returns false, with nothing
+// evaluated, for any other face (new entries are few, and their waves are
+// formed on the spot by face_flux later, with all lanes of a warp).
+template <int N, typename T>
+__device__ __forceinline__ bool face_flux_old(const FaceCtx<N, T>& fc, long long X, T P0, int j, T& f) {
+    const long long cap = fc.cap;
+    const T u = fc.U[j * cap + X];
+    if (!(gt0(u) || lt0(u))) {
+        f = (T)0;
+        return true;
+    }
+    const int Llo = fc.link[(long long)(2 * j) * cap + X];
+    const bool up = gt0(u);
+    const int Lup = up ? -1 : fc.link[(long long)(2 * j + 1) * cap + X];
+    const long long y = up ? (long long)Llo : X;
+    if (X >= fc.nold || y >= fc.nold || Lup >= fc.nold) return false;
+    const T PL = up ? q_or_zero<T>(fc.Q, Llo) : (T)0;
+    const T W = fc.wl[j * cap + X];
+    const T S = fmadd(-fc.i2h[j], fc.wg[j * cap + y], fc.tg[y]);
+    f = u * fmadd(-fc.dt, S, up ? PL : P0);
+    if (fc.lim != LIM_NONE && (gt0(W) || lt0(W))) {
+        const T Wup = up ? fc.wl[j * cap + Llo] : (Lup >= 0 ? fc.wl[j * cap + Lup] : zero_minus(P0));
+        const T au = abs_bits(u);
+        f = fmadd(half_nonneg(au) * fmadd(-fc.dth[j], au, (T)1), limited_wave<T>(fc.lim, W, Wup), f);
+    }
+    return true;
+}
+
 // Pass 2: the flux through every face with an active cell on at least one
 // side, stored as the lower face of the entry above it: all n lower faces of
 // an active cell, and the lower faces of a halo cell whose neighbour below is
-// active. Each warp takes 32 consecutive entries, lists their needed faces
-// (entry, j) in shared memory, dimension by dimension, and evaluates them 32 at
-// a time, so that the lanes of a warp all work although a halo cell needs only
-// the few faces it shares with active cells. The upper face of an active cell
+// active. Each warp takes runs of 32 consecutive entries, queues their needed
+// faces (entry, j) in shared memory, dimension by dimension, and evaluates
+// them 32 at a time, so that the lanes of a warp all work although a halo cell
+// needs only the few faces it shares with active cells. The upper face of an active cell
 // is the lower face of its upper neighbour, which is in the pool (active or
 // halo).
 template <int N, int DYN, typename T>
@@ -660,12 +700,61 @@ __device__ __forceinline__ void faces_body(const Model& m, const Bufs& b, const 
         fc.i2h[j] = (T)m.inv_2h[j];
         fc.dth[j] = (T)v.dth[j];
     }
-    __shared__ unsigned char s_item[WARPS][32 * N];  // (lane | j << 5) of the warp's needed faces
+    // The warp's needed faces wait in a queue in shared memory (entry, j) and
+    // are evaluated 32 at a time once that many are queued, whatever runs
+    // they come from; the rest at the end.
+    constexpr int QCAP = 32 * N + 32;
+    __shared__ int s_qx[WARPS][QCAP];
+    __shared__ unsigned char s_qj[WARPS][QCAP];
+    // FP64 (the pipe bounds it): faces that touch a new entry wait in a second
+    // queue, so that face_flux's longer path runs with all lanes too
+    constexpr bool DEFER = sizeof(T) == 8;
+    __shared__ int s_lx[WARPS][DEFER ? 64 : 1];
+    __shared__ unsigned char s_lj[WARPS][DEFER ? 64 : 1];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
+    int n_q = 0, n_later = 0;  // the same in every lane
+    auto later_flush = [&](int k) {  // the top k deferred faces, one per lane
+        n_later -= k;
+        if (lane < k) {
+            const long long X = s_lx[wid][n_later + lane];
+            const int jj = s_lj[wid][n_later + lane];
+            fl[jj * cap + X] = face_flux<N, T>(m, fc, X, fc.Q[X], jj);
+        }
+        __syncwarp();
+    };
+    auto eval = [&](int k) {  // the top k queued faces, one per lane
+        n_q -= k;
+        bool later = false;
+        long long X = 0;
+        int jj = 0;
+        if (lane < k) {
+            X = s_qx[wid][n_q + lane];
+            jj = s_qj[wid][n_q + lane];
+            if constexpr (DEFER) {
+                T f;
+                if (face_flux_old<N, T>(fc, X, fc.Q[X], jj, f)) fl[jj * cap + X] = f;
+                else later = true;
+            } else {
+                fl[jj * cap + X] = face_flux<N, T>(m, fc, X, fc.Q[X], jj);
+            }
+        }
+        if constexpr (DEFER) {
+            const unsigned bal = __ballot_sync(0xffffffffu, later);
+            if (later) {
+                const int at = n_later + __popc(bal & lt);
+                s_lx[wid][at] = (int)X;
+                s_lj[wid][at] = (unsigned char)jj;
+            }
+            n_later += __popc(bal);
+        }
+        __syncwarp();
+        if constexpr (DEFER) {
+            if (n_later >= 32) later_flush(32);
+        }
+    };
     for (WarpRuns wr(ncell, v.nb, v.bi); wr.next();) {
         const long long c = wr.c;
-        const long long c0 = c - lane;
         unsigned need = 0;
         if (c < ncell) {
             if (!is_halo(om, c)) {
@@ -678,21 +767,22 @@ __device__ __forceinline__ void faces_body(const Model& m, const Bufs& b, const 
                 }
             }
         }
-        int count = 0;
 #pragma unroll
         for (int j = 0; j < N; ++j) {
             const unsigned bal = __ballot_sync(0xffffffffu, (need >> j) & 1u);
-            if ((need >> j) & 1u) s_item[wid][count + __popc(bal & lt)] = (unsigned char)(lane | (j << 5));
-            count += __popc(bal);
+            if ((need >> j) & 1u) {
+                const int at = n_q + __popc(bal & lt);
+                s_qx[wid][at] = (int)c;
+                s_qj[wid][at] = (unsigned char)j;
+            }
+            n_q += __popc(bal);
         }
         __syncwarp();
-        for (int q = lane; q < count; q += 32) {
-            const int it = s_item[wid][q];
-            const long long X = c0 + (it & 31);
-            const int j = it >> 5;
-            fl[j * cap + X] = face_flux<N, T>(m, fc, X, fc.Q[X], j);
-        }
-        __syncwarp();
+        while (n_q >= 32) eval(32);
+    }
+    if (n_q > 0) eval(n_q);
+    if constexpr (DEFER) {
+        if (n_later > 0) later_flush(n_later);
     }
 }
 
