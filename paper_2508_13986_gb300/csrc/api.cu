@@ -225,9 +225,12 @@ void bind_context(gbees_ctx* ctx, const gbees_config* cfg, const Layout& L, void
     }
     m.thr_rel = cfg->thr_rel;
     m.cfl = cfg->cfl;
+    m.h_pow2 = 0;
     for (int j = 0; j < cfg->n; ++j) {
         m.inv_h[j] = 1.0 / cfg->h[j];
         m.inv_2h[j] = 1.0 / (2.0 * cfg->h[j]);
+        int ex = 0;
+        if (std::frexp(cfg->h[j], &ex) == 0.5 && std::isnormal(m.inv_h[j])) m.h_pow2 |= 1 << j;
         m.hf[j] = (float)cfg->h[j];
         m.x0f[j] = (float)cfg->x0[j];
     }

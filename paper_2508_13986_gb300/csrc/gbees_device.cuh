@@ -83,6 +83,12 @@ struct alignas(256) DevScalars {
     // grid barrier of the persistent kernel: arrivals since the launch began
     // (cleared by the host before every persistent launch)
     unsigned long long bar_seq;
+    // the step loop's running reductions, in global atomics: the largest CFL
+    // rate of the current prune epoch (two epochs by parity), and the exact
+    // sum and maximum of the apply phase (two steps by parity)
+    unsigned long long loop_rate[2];
+    long long loop_acc[2][NDIG];
+    unsigned long long loop_maxq[2];
     // SM cycles spent by block 0 of the persistent kernel per phase (grow,
     // halo, link, faces, apply, prune, step scalars) and the steps they cover
     long long phase_cycles[8];
@@ -120,6 +126,7 @@ struct Model {
     double prod_h;
     double inv_h[MAXN];    // 1 / h_j
     double inv_2h[MAXN];   // 1 / (2 h_j)
+    int h_pow2;            // bit j: h_j is a power of two
     // float copies for the FP32 update (no double-to-float conversion per use)
     float af[48];
     float hf[MAXN];
@@ -400,12 +407,19 @@ __device__ __forceinline__ double face_velocity64(const Model& m, const int* I, 
     return drift<double, N>(m, m.dyn, y, j);
 }
 
+// x / h_j as the IEEE division rounds it. For a width that is a power of two
+// the reciprocal is exact, so the product rounds the same real number: the
+// same result for one FP64 multiplication instead of a division sequence.
+__device__ __forceinline__ double div_h(const Model& m, double x, int j) {
+    return ((m.h_pow2 >> j) & 1) ? __dmul_rn(x, m.inv_h[j]) : __ddiv_rn(x, m.h[j]);
+}
+
 // FP64 CFL rate sum_j |f_j(x_{i-e_j/2})| / h_j (Eq. 8 with |f|).
 template <int N>
 __device__ __forceinline__ double cfl_rate64(const Model& m, const int* I) {
     double r = 0.0;
 #pragma unroll
-    for (int j = 0; j < N; ++j) r = __dadd_rn(r, __ddiv_rn(fabs(face_velocity64<N>(m, I, j)), m.h[j]));
+    for (int j = 0; j < N; ++j) r = __dadd_rn(r, div_h(m, fabs(face_velocity64<N>(m, I, j)), j));
     return r;
 }
 
@@ -775,6 +789,58 @@ __device__ __forceinline__ void block_partial(Partial* part, long long (&d)[NDIG
 }
 __device__ __forceinline__ void block_partial(Partial* part, long long (&d)[NDIG], double mx, double rate) {
     block_partial(part, d, mx, rate, blockIdx.x);
+}
+
+// The block's digits, maximum value and maximum rate folded into global
+// accumulators with atomics (acc may be null: rate only). Integer sums and
+// maxima: the totals do not depend on the order of the blocks.
+__device__ __forceinline__ void block_atomics(long long* acc, unsigned long long* maxq, unsigned long long* rate,
+                                              long long (&d)[NDIG], double mx, double r) {
+    __shared__ long long s_acc[WARPS][NDIG];
+    __shared__ unsigned long long s_mx[WARPS], s_rt[WARPS];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned long long mk = mx > -INFINITY ? ord_key(mx) : 0ull;
+    unsigned long long rk = r > 0.0 ? (unsigned long long)__double_as_longlong(r) : 0ull;
+    if (acc) {
+#pragma unroll
+        for (int q = 0; q < NDIG; ++q) {
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) d[q] += __shfl_down_sync(0xffffffffu, d[q], off);
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        mk = max(mk, __shfl_down_sync(0xffffffffu, mk, off));
+        rk = max(rk, __shfl_down_sync(0xffffffffu, rk, off));
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < NDIG; ++q) s_acc[wid][q] = d[q];
+        s_mx[wid] = mk;
+        s_rt[wid] = rk;
+    }
+    __syncthreads();
+    const int q = threadIdx.x, nw = (int)(blockDim.x >> 5);
+    if (q < NDIG) {
+        if (acc) {
+            long long a = 0;
+            for (int w = 0; w < nw; ++w) a += s_acc[w][q];
+            if (a) atomicAdd((unsigned long long*)&acc[q], (unsigned long long)a);
+        }
+    } else if (q == NDIG) {
+        if (maxq) {
+            unsigned long long mm = 0;
+            for (int w = 0; w < nw; ++w) mm = max(mm, s_mx[w]);
+            if (mm) atomicMax(maxq, mm);
+        }
+    } else if (q == NDIG + 1) {
+        if (rate) {
+            unsigned long long rr = 0;
+            for (int w = 0; w < nw; ++w) rr = max(rr, s_rt[w]);
+            if (rr) atomicMax(rate, rr);
+        }
+    }
+    __syncthreads();
 }
 
 // Combine the partials of blocks [0, nblk) in every thread of the calling

@@ -133,6 +133,11 @@ __global__ void k_reset(DevScalars* sc, double t0) {
     sc->graph_kernels = 0;
     sc->bar_word = 0;
     sc->bar_seq = 0;
+    for (int e = 0; e < 2; ++e) {
+        sc->loop_rate[e] = 0;
+        sc->loop_maxq[e] = 0;
+        for (int q = 0; q < NDIG; ++q) sc->loop_acc[e][q] = 0;
+    }
     for (int q = 0; q < 8; ++q) sc->phase_cycles[q] = 0;
     sc->phase_steps = 0;
 }

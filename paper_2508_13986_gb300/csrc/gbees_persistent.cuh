@@ -76,6 +76,16 @@ __device__ __forceinline__ void step_loop(const Model& m, const Bufs& b, long lo
     double w = *(volatile double*)&sc->w;
     double last_dt = *(volatile double*)&sc->dt;
     long long nsteps = 0, nupd = 0;
+    // the running reductions start from the state (before the first barrier,
+    // which orders these writes before every use)
+    int ep = 0;  // parity of the prune epoch in loop_rate
+    if (bi == 0 && threadIdx.x == 0 && !done) {
+        sc->loop_rate[0] = maxrate;
+        for (int e = 0; e < 2; ++e) {
+            sc->loop_maxq[e] = 0;
+            for (int q = 0; q < NDIG; ++q) sc->loop_acc[e][q] = 0;
+        }
+    }
     // every block has read the state before anyone changes it
     if (done || *(volatile int*)&sc->error || !barrier()) return;
     // phase timing by block 0 (cycles between the barriers it passes)
@@ -96,6 +106,12 @@ __device__ __forceinline__ void step_loop(const Model& m, const Bufs& b, long lo
         waves_body<N, DYN, T>(m, b, v, v.N_prev);
         if (!barrier()) return;
         mark(0);
+        // every block read the other apply slot in the previous step: clear it
+        // for the next one
+        if (bi == 0 && threadIdx.x == 0) {
+            sc->loop_maxq[(it + 1) & 1] = 0;
+            for (int q = 0; q < NDIG; ++q) sc->loop_acc[(it + 1) & 1][q] = 0;
+        }
         // halo cells around the newly active cells (appended after sc->N, which
         // stays put until the link phase)
         const long long n_ins = min(*(volatile long long*)&sc->N, m.cap);
@@ -116,7 +132,7 @@ __device__ __forceinline__ void step_loop(const Model& m, const Bufs& b, long lo
             {
                 const double r = fmax(rg, link_body<N, T>(m, b, v.N_prev, v.N, v.g, nb, bi));
                 long long zero[NDIG] = {0, 0, 0, 0, 0, 0};
-                block_partial(b.part, zero, -INFINITY, r, bi);
+                block_atomics(nullptr, nullptr, &sc->loop_rate[ep], zero, -INFINITY, r);
             }
             if (bi == 0 && threadIdx.x == 0) sc->N = v.N;  // read again only after the next grow
             if (!barrier()) return;
@@ -126,8 +142,8 @@ __device__ __forceinline__ void step_loop(const Model& m, const Bufs& b, long lo
                 sc->n_halo = 0;
                 sc->n_act = 0;
             }
-            Combined cr = combine_partials(b.part, nb);
-            maxrate = max(maxrate, cr.rate_bits);
+            // the epoch's largest rate, every block's included (thread 0 uses it)
+            if (threadIdx.x == 0) maxrate = max(maxrate, *(volatile unsigned long long*)&sc->loop_rate[ep]);
         }
         if (threadIdx.x == 0) {
             const StepTime st0 = step_time(m, __longlong_as_double((long long)maxrate), t, tt, ss.dth, ss.ch);
@@ -161,12 +177,18 @@ __device__ __forceinline__ void step_loop(const Model& m, const Bufs& b, long lo
         mark(3);
         apply_body<N, T>(m, b, v, d, mx, err);
         if (err) set_error(sc, ST_EDEGENERATE);
-        block_partial(b.part, d, mx, 0.0, bi);
+        block_atomics(sc->loop_acc[it & 1], &sc->loop_maxq[it & 1], nullptr, d, mx, 0.0);
         if (!barrier()) return;
         mark(4);
         {
-            Combined cs = combine_partials(b.part, nb);
-            if (threadIdx.x == 0) normalisation(m, cs, ss);
+            if (threadIdx.x == 0) {
+                Combined cs;
+#pragma unroll
+                for (int q = 0; q < NDIG; ++q) cs.acc[q] = *(volatile long long*)&sc->loop_acc[it & 1][q];
+                cs.maxq_ord = *(volatile unsigned long long*)&sc->loop_maxq[it & 1];
+                cs.rate_bits = 0;
+                normalisation(m, cs, ss);
+            }
             __syncthreads();
             w = ss.w;
             v.scale = ss.scale;
@@ -225,6 +247,9 @@ __device__ __forceinline__ void step_loop(const Model& m, const Bufs& b, long lo
                 return;
             }
             maxrate = cp.rate_bits;
+            // a new epoch of the running rate starts from the survivors' largest
+            ep ^= 1;
+            if (bi == 0 && threadIdx.x == 0) sc->loop_rate[ep] = maxrate;
             mark(5);
             v.N = total;
             v.N_prev = total;

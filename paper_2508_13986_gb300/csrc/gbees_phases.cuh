@@ -371,9 +371,11 @@ __device__ __forceinline__ void halo_body(const Model& m, const Bufs& b, const S
     const long long cap = m.cap;
     const long long ni = hi - lo;
     const long long items = (ni + nact) * 2 * N;
-    const long long tid = (long long)v.bi * blockDim.x + threadIdx.x;
-    const long long nth = (long long)v.nb * blockDim.x;
-    for (long long it = tid; it < items; it += nth) {
+    // runs of 32 items, one per warp, the warps of consecutive runs on
+    // different SMs: a few hundred items of a small grid spread over the GPU
+    for (WarpRuns wr(items, v.nb, v.bi); wr.next();) {
+        const long long it = wr.c;
+        if (it >= items) continue;
         const long long q = it / (2 * N);
         const int d = (int)(it - q * 2 * N);
         long long x;
@@ -401,10 +403,12 @@ __device__ __forceinline__ double link_masks(const Model& m, const Bufs& b, long
     const unsigned long long* key = b.key[g];
     T* U = static_cast<T*>(b.u[g]);
     const long long cap = m.cap;
-    const long long tid = (long long)bi * blockDim.x + threadIdx.x;
-    const long long nth = (long long)nb * blockDim.x;
     double rmax = 0.0;
-    for (long long c = lo + tid; c < hi; c += nth) {
+    // runs of 32 entries, one per warp, consecutive runs on different SMs (the
+    // FP64 drift evaluations of a few hundred new entries spread over the GPU)
+    for (WarpRuns wr(hi - lo, nb, bi); wr.next();) {
+        const long long c = lo + wr.c;
+        if (c >= hi) continue;
         int I[N];
         unpack_key<N>(m, key[c], I);
         const unsigned short f = b.om[g][c];
@@ -419,7 +423,7 @@ __device__ __forceinline__ double link_masks(const Model& m, const Bufs& b, long
             if (face_velocity64<N>(m, J, j) > 0.0) msk |= 1u << (2 * j + 1);
             if (ul < 0.0) msk |= 1u << (2 * j);
             U[j * cap + c] = (T)ul;
-            r = __dadd_rn(r, __ddiv_rn(fabs(ul), m.h[j]));
+            r = __dadd_rn(r, div_h(m, fabs(ul), j));
         }
         b.om[g][c] = (unsigned short)(f | msk);
         b.rate[g][c] = r;
@@ -438,10 +442,10 @@ __device__ __forceinline__ double link_body(const Model& m, const Bufs& b, long 
     const unsigned long long* key = b.key[g];
     int* link = b.link[g];
     const long long cap = m.cap;
-    const long long tid = (long long)bi * blockDim.x + threadIdx.x;
-    const long long nth = (long long)nb * blockDim.x;
     const long long work = (hi - lo) * 2 * N;
-    for (long long wi = tid; wi < work; wi += nth) {
+    for (WarpRuns wr(work, nb, bi); wr.next();) {
+        const long long wi = wr.c;
+        if (wi >= work) continue;
         const long long c = lo + wi / (2 * N);
         const int dir = (int)(wi % (2 * N));
         const int j = dir >> 1, s = dir & 1;
@@ -449,9 +453,9 @@ __device__ __forceinline__ double link_body(const Model& m, const Bufs& b, long 
         unpack_key<N>(m, key[c], I);
         I[j] += s ? 1 : -1;
         unsigned long long k;
-        int nb = pack_key<N>(m, I, k) ? table_find(m, b.table, k) : -1;
-        link[(long long)dir * cap + c] = nb;
-        if (nb >= 0) link[(long long)(2 * j + (1 - s)) * cap + nb] = (int)c;
+        const int nbr = pack_key<N>(m, I, k) ? table_find(m, b.table, k) : -1;
+        link[(long long)dir * cap + c] = nbr;
+        if (nbr >= 0) link[(long long)(2 * j + (1 - s)) * cap + nbr] = (int)c;
     }
     return link_masks<N, T>(m, b, lo, hi, g, nb, bi);
 }
@@ -475,10 +479,10 @@ __device__ __forceinline__ double link_body_tile(const Model& m, const Bufs& b, 
         unpack_key<N>(m, key[c], I);
         I[j] += s ? 1 : -1;
         unsigned long long k;
-        int nb = pack_key<N>(m, I, k) ? table_find_tile<W>(m, b.table, k, tile) : -1;
+        const int nbr = pack_key<N>(m, I, k) ? table_find_tile<W>(m, b.table, k, tile) : -1;
         if (tile.thread_rank() == 0) {
-            link[(long long)dir * cap + c] = nb;
-            if (nb >= 0) link[(long long)(2 * j + (1 - s)) * cap + nb] = (int)c;
+            link[(long long)dir * cap + c] = nbr;
+            if (nbr >= 0) link[(long long)(2 * j + (1 - s)) * cap + nbr] = (int)c;
         }
     }
     return link_masks<N, T>(m, b, lo, hi, g, nb, bi);
