@@ -172,7 +172,7 @@ __device__ __forceinline__ void step_loop(const Model& m, const Bufs& b, long lo
         long long d[NDIG] = {0, 0, 0, 0, 0, 0};
         double mx = -INFINITY;
         int err = 0;
-        faces_body<N, DYN, T>(m, b, v);
+        faces_body<N, DYN, T, true>(m, b, v);
         if (!barrier()) return;
         mark(3);
         apply_body<N, T>(m, b, v, d, mx, err);

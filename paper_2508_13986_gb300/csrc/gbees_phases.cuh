@@ -682,7 +682,10 @@ __device__ __forceinline__ bool face_flux_old(const FaceCtx<N, T>& fc, long long
 // needs only the few faces it shares with active cells. The upper face of an active cell
 // is the lower face of its upper neighbour, which is in the pool (active or
 // halo).
-template <int N, int DYN, typename T>
+// LATENCY: the step loop of a small grid, bound by dependent loads, not by the
+// FP64 pipe: faces that touch a new entry are evaluated where they stand (a
+// second queue would add a flush to the critical path of every warp).
+template <int N, int DYN, typename T, bool LATENCY = false>
 __device__ __forceinline__ void faces_body(const Model& m, const Bufs& b, const StepView& v) {
     const long long ncell = v.N;
     const long long cap = m.cap;
@@ -712,7 +715,7 @@ __device__ __forceinline__ void faces_body(const Model& m, const Bufs& b, const 
     __shared__ unsigned char s_qj[WARPS][QCAP];
     // FP64 (the pipe bounds it): faces that touch a new entry wait in a second
     // queue, so that face_flux's longer path runs with all lanes too
-    constexpr bool DEFER = sizeof(T) == 8;
+    constexpr bool DEFER = sizeof(T) == 8 && !LATENCY;
     __shared__ int s_lx[WARPS][DEFER ? 64 : 1];
     __shared__ unsigned char s_lj[WARPS][DEFER ? 64 : 1];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
