@@ -47,6 +47,14 @@ TRAFFIC_BYTES_PER_CELL = {
     # --max-cells 1048576` (segment t = 0.5..0.75: 2118979 cell updates, counted by the oracle):
     # 9.268 MB read + 1.092 MB written
     "lorenz63_h0.25/f64/k_persistent": {"bytes_per_cell": 10.360832e6 / 2118979, "src": "c00cd41fc877901a"},
+    # k_faces, all 539 launches of the profiled run of `bench.py --precision f64|f32 --steps 1 --warmup 0
+    # --no-secondary --no-extras --cpu-budget 0 --e2e-runs 1 --no-tune --block-threads 256`
+    # (17,611,960,218 cell updates in FP64, 17,611,960,553 in FP32):
+    # FP64 10769.858 GB read + 1139.416 GB written; FP32 6631.578 GB read + 612.886 GB written
+    "lorenz96_6d/f64/k_faces": {"bytes_per_cell": (10769858390784 + 1139416195840) / 17611960218,
+                                "src": "c449dd11aa64e840"},
+    "lorenz96_6d/f32/k_faces": {"bytes_per_cell": (6631577890304 + 612885722880) / 17611960553,
+                                "src": "c449dd11aa64e840"},
 }
 # The paper's own throughput on its two cases, in this benchmark's unit (cells
 # per second, total cell computations over the runtime): the fastest GPU row of
@@ -398,7 +406,7 @@ def time_precision(args, w, precision, dev, rank, world, steps=None, warmup=None
     kname = kernel.split(" ")[0]
     if precision == "f64" and kname in ("k_faces", "k_waves_list", "k_apply"):
         # FP64 step kernels are bound by the FP64 pipe on this chip (ncu: the
-        # flux pass keeps it about 70 % busy at under 20 % of DRAM bandwidth):
+        # flux pass keeps it 64 % busy at 29 % of DRAM bandwidth):
         # the roofline is the FP64 arithmetic peak; the HBM figures stay beside it
         tf, how = fp64_peak()
         fpc = fp64_flops_per_update(kname, w.n)
