@@ -175,7 +175,7 @@ __device__ __forceinline__ void step_loop(const Model& m, const Bufs& b, long lo
         faces_body<N, DYN, T, true>(m, b, v);
         if (!barrier()) return;
         mark(3);
-        apply_body<N, T>(m, b, v, d, mx, err);
+        apply_body<N, T, true>(m, b, v, d, mx, err);
         if (err) set_error(sc, ST_EDEGENERATE);
         block_atomics(sc->loop_acc[it & 1], &sc->loop_maxq[it & 1], nullptr, d, mx, 0.0);
         if (!barrier()) return;

@@ -497,6 +497,14 @@ __device__ __forceinline__ T q_or_zero(const T* Q, int i) {
 
 __device__ __forceinline__ bool is_halo(const unsigned short* om, long long i) { return (om[i] & OM_GHOST) != 0; }
 
+// 0 - x as IEEE subtraction gives it, without FP64 arithmetic for doubles:
+// the sign flips, except that both zeros give +0.
+__device__ __forceinline__ double zero_minus(double x) {
+    const long long b = __double_as_longlong(x);
+    return __longlong_as_double((b << 1) == 0 ? 0ll : (b ^ (long long)0x8000000000000000ull));
+}
+__device__ __forceinline__ float zero_minus(float x) { return 0.0f - x; }
+
 // The entering wave of entry y in dimension d,
 //   G_d(y) = max(u_lo, 0) (P_y - P_{y-e_d}) + min(u_hi, 0) (P_{y+e_d} - P_y),
 // u_lo, u_hi the velocities at its lower and upper d-face (the upper one is the
@@ -516,6 +524,22 @@ __device__ __forceinline__ T wave_of(const T* Q, const T* U, long long cap, cons
     const bool in_lo = gt0(ul), in_hi = lt0(uh);
     const T G = (in_lo ? ul : (in_hi ? uh : (T)0)) * (in_lo ? wlo : Pp - Py);
     return (in_lo && in_hi) ? fmadd(uh, Pp - Py, G) : G;
+}
+
+// wave_of for a halo entry, whose value is +0: the same results (0 - P_m and
+// P_p - 0 are exact) without the two subtractions.
+template <int N, typename T>
+__device__ __forceinline__ T wave_of_halo(const T* Q, const T* U, long long cap, const int* L, long long y, int d,
+                                          T& wlo) {
+    const int dn = L[2 * d], up = L[2 * d + 1];
+    const T Pm = q_or_zero<T>(Q, dn);
+    const T Pp = q_or_zero<T>(Q, up);
+    const T ul = U[d * cap + y];
+    const T uh = up >= 0 ? U[d * cap + up] : (T)0;
+    wlo = zero_minus(Pm);
+    const bool in_lo = gt0(ul), in_hi = lt0(uh);
+    const T G = (in_lo ? ul : (in_hi ? uh : (T)0)) * (in_lo ? wlo : Pp);
+    return (in_lo && in_hi) ? fmadd(uh, Pp, G) : G;
 }
 
 // Pass 1, one thread per entry c of [0, ncell) (active and halo), all
@@ -547,13 +571,26 @@ __device__ __forceinline__ void waves_body(const Model& m, const Bufs& b, const 
         load_links<N>(link, cap, c, L);
         const T P0 = Q[c];
         T t = (T)0;
+        // a warp of halo entries (the pool keeps them together after a
+        // prune) takes the form without the subtractions
+        if (__all_sync(__activemask(), is_halo(b.om[v.g], c))) {
 #pragma unroll
-        for (int d = 0; d < N; ++d) {
-            T wlo;
-            const T G = wave_of<N, T>(Q, U, cap, L, c, P0, d, wlo);
-            wl[d * cap + c] = wlo;
-            wg[d * cap + c] = G;
-            t = fmadd(G, i2h[d], t);
+            for (int d = 0; d < N; ++d) {
+                T wlo;
+                const T G = wave_of_halo<N, T>(Q, U, cap, L, c, d, wlo);
+                wl[d * cap + c] = wlo;
+                wg[d * cap + c] = G;
+                t = fmadd(G, i2h[d], t);
+            }
+        } else {
+#pragma unroll
+            for (int d = 0; d < N; ++d) {
+                T wlo;
+                const T G = wave_of<N, T>(Q, U, cap, L, c, P0, d, wlo);
+                wl[d * cap + c] = wlo;
+                wg[d * cap + c] = G;
+                t = fmadd(G, i2h[d], t);
+            }
         }
         tg[c] = t;
     }
@@ -575,14 +612,6 @@ __device__ __forceinline__ T waves_new(const Model& m, const T* Q, const T* U, c
     }
     return S;
 }
-
-// 0 - x as IEEE subtraction gives it, without FP64 arithmetic for doubles:
-// the sign flips, except that both zeros give +0.
-__device__ __forceinline__ double zero_minus(double x) {
-    const long long b = __double_as_longlong(x);
-    return __longlong_as_double((b << 1) == 0 ? 0ll : (b ^ (long long)0x8000000000000000ull));
-}
-__device__ __forceinline__ float zero_minus(float x) { return 0.0f - x; }
 
 // The flux pass's view of the step (pointers and constants in the arithmetic type).
 template <int N, typename T>
@@ -795,8 +824,11 @@ __device__ __forceinline__ void faces_body(const Model& m, const Bufs& b, const 
 
 // Pass 3: the conservative update of the active cells with the previous
 // normalisation applied (halo cells stay 0); adds this thread's new values to
-// its digits and maximum.
-template <int N, typename T>
+// its digits and maximum. Large FP64 grids (not LATENCY): each warp queues the
+// active cells of its runs in shared memory and updates them 32 at a time, so
+// the FP64 lanes all work where halo and active entries mix (after growth);
+// FP32 and small grids are bound by load latency and update in place.
+template <int N, typename T, bool LATENCY = false>
 __device__ __forceinline__ void apply_body(const Model& m, const Bufs& b, const StepView& v, long long (&dacc)[NDIG],
                                            double& mx, int& err) {
     const long long ncell = v.N;
@@ -811,13 +843,7 @@ __device__ __forceinline__ void apply_body(const Model& m, const Bufs& b, const 
 #pragma unroll
     for (int k = 0; k < N; ++k) dth[k] = (T)v.dth[k];
     T tmax = -INFINITY;
-    for (WarpRuns wr(ncell, v.nb, v.bi); wr.next();) {
-        const long long c = wr.c;
-        if (c >= ncell) continue;
-        if (is_halo(om, c)) {
-            Qn[c] = (T)0;
-            continue;
-        }
+    auto update = [&](long long c) {
         int L[2 * N];
         load_links<N>(link, cap, c, L);
         T upd = (T)0;
@@ -831,6 +857,40 @@ __device__ __forceinline__ void apply_body(const Model& m, const Bufs& b, const 
         Qn[c] = qn;
         acc_add(dacc, qn, err);
         tmax = vmax(tmax, qn);
+    };
+    if constexpr (LATENCY || sizeof(T) == 4) {
+        for (WarpRuns wr(ncell, v.nb, v.bi); wr.next();) {
+            const long long c = wr.c;
+            if (c >= ncell) continue;
+            if (is_halo(om, c)) {
+                Qn[c] = (T)0;
+                continue;
+            }
+            update(c);
+        }
+    } else {
+        __shared__ int s_ac[WARPS][64];
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        const unsigned lt = (1u << lane) - 1u;
+        int n_a = 0;  // the same in every lane
+        for (WarpRuns wr(ncell, v.nb, v.bi); wr.next();) {
+            const long long c = wr.c;
+            bool act = false;
+            if (c < ncell) {
+                if (is_halo(om, c)) Qn[c] = (T)0;
+                else act = true;
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, act);
+            if (act) s_ac[wid][n_a + __popc(bal & lt)] = (int)c;
+            n_a += __popc(bal);
+            __syncwarp();
+            if (n_a >= 32) {
+                n_a -= 32;
+                update(s_ac[wid][n_a + lane]);
+                __syncwarp();
+            }
+        }
+        if (lane < n_a) update(s_ac[wid][lane]);
     }
     if (tmax > -INFINITY) mx = fmax(mx, (double)tmax);
 }
