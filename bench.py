@@ -45,17 +45,17 @@ SECONDARY_WORKLOAD = "lorenz63_h0.25"
 TRAFFIC_BYTES_PER_CELL = {
     # k_persistent, third launch of `bench.py --workload lorenz63_h0.25 --steps 1 --warmup 1
     # --no-secondary --no-extras --cpu-budget 0 --max-cells 1048576 --no-tune --block-threads 256`
-    # (segment t = 0.5..0.75: 2118979 cell updates, counted by the oracle): 6.530 MB read + 0.752 MB
+    # (segment t = 0.5..0.75: 2118979 cell updates, counted by the oracle): 6.497 MB read + 0.789 MB
     # written (the grid stays in L2)
-    "lorenz63_h0.25/f64/k_persistent": {"bytes_per_cell": (6529792 + 752384) / 2118979, "src": "c449dd11aa64e840"},
+    "lorenz63_h0.25/f64/k_persistent": {"bytes_per_cell": (6496512 + 789248) / 2118979, "src": "76f5b5c1d67733cc"},
     # k_faces, all 539 launches of the profiled run of `bench.py --precision f64|f32 --steps 1 --warmup 0
     # --no-secondary --no-extras --cpu-budget 0 --e2e-runs 1 --no-tune --block-threads 256`
     # (17,611,960,218 cell updates in FP64, 17,611,960,553 in FP32):
-    # FP64 10769.858 GB read + 1139.416 GB written; FP32 6631.578 GB read + 612.886 GB written
-    "lorenz96_6d_h0.25/f64/k_faces": {"bytes_per_cell": (10769858390784 + 1139416195840) / 17611960218,
-                                      "src": "c449dd11aa64e840"},
-    "lorenz96_6d_h0.25/f32/k_faces": {"bytes_per_cell": (6631577890304 + 612885722880) / 17611960553,
-                                      "src": "c449dd11aa64e840"},
+    # FP64 10796.660 GB read + 1139.416 GB written; FP32 6672.539 GB read + 612.942 GB written
+    "lorenz96_6d_h0.25/f64/k_faces": {"bytes_per_cell": (10796659815168 + 1139416118016) / 17611960218,
+                                      "src": "76f5b5c1d67733cc"},
+    "lorenz96_6d_h0.25/f32/k_faces": {"bytes_per_cell": (6672539490560 + 612941847040) / 17611960553,
+                                      "src": "76f5b5c1d67733cc"},
 }
 # The paper's own throughput on its two cases, in this benchmark's unit (cells
 # per second, total cell computations over the runtime): the fastest GPU row of
