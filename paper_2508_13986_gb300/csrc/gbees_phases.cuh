@@ -509,8 +509,10 @@ __device__ __forceinline__ float zero_minus(float x) { return 0.0f - x; }
 //   G_d(y) = max(u_lo, 0) (P_y - P_{y-e_d}) + min(u_hi, 0) (P_{y+e_d} - P_y),
 // u_lo, u_hi the velocities at its lower and upper d-face (the upper one is the
 // lower one of the neighbour above; a missing neighbour above of a halo cell
-// leaves both P at 0), with the jump across the lower face in wlo.
-template <int N, typename T>
+// leaves both P at 0), with the jump across the lower face in wlo. VOTE: the
+// warp's lanes run this together (the wave pass), so terms that no lane needs
+// are skipped by a warp vote.
+template <int N, typename T, bool VOTE = false>
 __device__ __forceinline__ T wave_of(const T* Q, const T* U, long long cap, const int* L, long long y, T Py, int d,
                                      T& wlo) {
     const int dn = L[2 * d], up = L[2 * d + 1];
@@ -520,10 +522,20 @@ __device__ __forceinline__ T wave_of(const T* Q, const T* U, long long cap, cons
     const T uh = up >= 0 ? U[d * cap + up] : (T)0;
     wlo = Py - Pm;
     // one product in the usual case (flow through the cell, or out of it on one
-    // side only); a cell that both faces flow into takes the second term too
+    // side only); a cell that both faces flow into takes the second term too.
+    // The flow direction varies slowly: when no lane of the warp takes flow in
+    // through the upper face, the upper jump and the second term are skipped.
     const bool in_lo = gt0(ul), in_hi = lt0(uh);
-    const T G = (in_lo ? ul : (in_hi ? uh : (T)0)) * (in_lo ? wlo : Pp - Py);
-    return (in_lo && in_hi) ? fmadd(uh, Pp - Py, G) : G;
+    if constexpr (VOTE) {
+        const unsigned act = __activemask();
+        if (!__any_sync(act, in_hi)) return (in_lo ? ul : (T)0) * wlo;
+        const T G = (in_lo ? ul : (in_hi ? uh : (T)0)) * (in_lo ? wlo : Pp - Py);
+        if (!__any_sync(act, in_lo && in_hi)) return G;
+        return (in_lo && in_hi) ? fmadd(uh, Pp - Py, G) : G;
+    } else {
+        const T G = (in_lo ? ul : (in_hi ? uh : (T)0)) * (in_lo ? wlo : Pp - Py);
+        return (in_lo && in_hi) ? fmadd(uh, Pp - Py, G) : G;
+    }
 }
 
 // wave_of for a halo entry, whose value is +0: the same results (0 - P_m and
@@ -539,6 +551,7 @@ __device__ __forceinline__ T wave_of_halo(const T* Q, const T* U, long long cap,
     wlo = zero_minus(Pm);
     const bool in_lo = gt0(ul), in_hi = lt0(uh);
     const T G = (in_lo ? ul : (in_hi ? uh : (T)0)) * (in_lo ? wlo : Pp);
+    if (!__any_sync(__activemask(), in_lo && in_hi)) return G;
     return (in_lo && in_hi) ? fmadd(uh, Pp, G) : G;
 }
 
@@ -586,7 +599,7 @@ __device__ __forceinline__ void waves_body(const Model& m, const Bufs& b, const 
 #pragma unroll
             for (int d = 0; d < N; ++d) {
                 T wlo;
-                const T G = wave_of<N, T>(Q, U, cap, L, c, P0, d, wlo);
+                const T G = wave_of<N, T, true>(Q, U, cap, L, c, P0, d, wlo);
                 wl[d * cap + c] = wlo;
                 wg[d * cap + c] = G;
                 t = fmadd(G, i2h[d], t);
