@@ -45,17 +45,17 @@ SECONDARY_WORKLOAD = "lorenz63_h0.25"
 TRAFFIC_BYTES_PER_CELL = {
     # k_persistent, third launch of `bench.py --workload lorenz63_h0.25 --steps 1 --warmup 1
     # --no-secondary --no-extras --cpu-budget 0 --max-cells 1048576 --no-tune --block-threads 256`
-    # (segment t = 0.5..0.75: 2118979 cell updates, counted by the oracle): 6.497 MB read + 0.789 MB
+    # (segment t = 0.5..0.75: 2118979 cell updates, counted by the oracle): 6.493 MB read + 0.803 MB
     # written (the grid stays in L2)
-    "lorenz63_h0.25/f64/k_persistent": {"bytes_per_cell": (6496512 + 789248) / 2118979, "src": "76f5b5c1d67733cc"},
+    "lorenz63_h0.25/f64/k_persistent": {"bytes_per_cell": (6493184 + 802816) / 2118979, "src": "5c6420cf21eedbce"},
     # k_faces, all 539 launches of the profiled run of `bench.py --precision f64|f32 --steps 1 --warmup 0
     # --no-secondary --no-extras --cpu-budget 0 --e2e-runs 1 --no-tune --block-threads 256`
     # (17,611,960,218 cell updates in FP64, 17,611,960,553 in FP32):
-    # FP64 10796.660 GB read + 1139.416 GB written; FP32 6672.539 GB read + 612.942 GB written
-    "lorenz96_6d_h0.25/f64/k_faces": {"bytes_per_cell": (10796659815168 + 1139416118016) / 17611960218,
-                                      "src": "76f5b5c1d67733cc"},
-    "lorenz96_6d_h0.25/f32/k_faces": {"bytes_per_cell": (6672539490560 + 612941847040) / 17611960553,
-                                      "src": "76f5b5c1d67733cc"},
+    # FP64 10743.123 GB read + 1139.365 GB written; FP32 6651.750 GB read + 612.772 GB written
+    "lorenz96_6d_h0.25/f64/k_faces": {"bytes_per_cell": (10743122864128 + 1139365122560) / 17611960218,
+                                      "src": "5c6420cf21eedbce"},
+    "lorenz96_6d_h0.25/f32/k_faces": {"bytes_per_cell": (6651749612288 + 612772230144) / 17611960553,
+                                      "src": "5c6420cf21eedbce"},
 }
 # The paper's own throughput on its two cases, in this benchmark's unit (cells
 # per second, total cell computations over the runtime): the fastest GPU row of
