@@ -26,3 +26,25 @@ def test_reference_arm_prints_one_contract_line():
     assert d["cpu_baseline"]["value"] == d["value"]
     e = d["e2e"]
     assert e["value"] == d["value"] and e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+
+
+def test_traffic_records_name_real_workloads_and_the_current_sources():
+    """Every DRAM-traffic record of the bench is keyed by a workload's own name
+    (the name the bench looks up), a precision and a step kernel, and carries
+    the hash of the device sources it was measured on, which the bench compares
+    before it reports roofline.traffic (a record of other sources reads as
+    null)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2508_13986_gb300 import workloads as W
+
+    names = {W.config(n).name for n in ("lorenz63_h0.5", "lorenz63_h0.25", "lorenz96_6d", "lorenz96_6d_h0.5",
+                                         "paper_e1", "paper_e2")}
+    kernels = {"k_faces", "k_waves_list", "k_apply", "k_persistent"}
+    assert bench.TRAFFIC_BYTES_PER_CELL
+    for key, rec in bench.TRAFFIC_BYTES_PER_CELL.items():
+        wname, prec, kern = key.split("/")
+        assert wname in names and prec in ("f64", "f32") and kern in kernels, key
+        assert rec["bytes_per_cell"] > 0 and len(rec["src"]) == 16, key
+    h = bench.device_source_hash()
+    assert len(h) == 16 and all(c in "0123456789abcdef" for c in h)
