@@ -54,3 +54,29 @@ def test_tuned_shape_gives_the_default_result():
         g.close()
     for o in out[1:]:
         assert np.array_equal(out[0][0], o[0]) and np.array_equal(out[0][1], o[1])
+
+
+@pytest.mark.gpu
+def test_persistent_block_count_gives_the_same_result():
+    """gbees_set_persist_blocks: the persistent step loop on 152, 76 and 19
+    blocks (grid barriers over fewer arrivals, more cells per block) ends with
+    the same cells and bit-identical densities, the same steps and updates;
+    a negative count is refused."""
+    import __graft_entry__ as ge
+
+    ge.build()
+    w = W.lorenz63(h=0.5, t_end=0.1, prune_interval=5)
+    out = []
+    for blocks in (0, 76, 19):
+        g = gbees.grid_for_workload(w, max_cells=1 << 16, launch_mode=gbees.GBEES_LAUNCH_PERSISTENT)
+        assert gbees.gbees_set_persist_blocks(g.ctx, blocks) == gbees.GBEES_OK
+        g.init_gaussian(w.mean, w.cov)
+        st = g.propagate(w.t_end)
+        idx, p = g.read_cells()
+        out.append((st.steps, st.cell_updates, idx, p))
+        if blocks == 19:
+            assert gbees.gbees_set_persist_blocks(g.ctx, -1) == gbees.GBEES_EINVAL
+        g.close()
+    for o in out[1:]:
+        assert o[0] == out[0][0] and o[1] == out[0][1]
+        assert np.array_equal(o[2], out[0][2]) and np.array_equal(o[3], out[0][3])
