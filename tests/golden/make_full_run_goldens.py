@@ -14,7 +14,8 @@ cell count, a SHA-256 of the sorted index array (int32, row-major), the mean
 and covariance, and the indices and densities of 10^4 cells drawn uniformly
 (seed 2508) from the sorted set. Every file also records the steps, the cell
 updates and the time reached. Calls only the oracle (on all cores) and the
-input generators; the 6-D parts take tens of minutes.
+input generators; each 6-D part takes hours on an 8-core host (about 2.7 h for
+c3_20 and 3 h for c3h05 with the two running side by side), c2 under a minute.
 
     python tests/golden/make_full_run_goldens.py [c2] [c3_20] [c3h05]
 """
