@@ -73,3 +73,27 @@ def test_the_truth_integrator_is_fourth_order_and_converged_at_its_step():
     e1 = np.abs(W.truth_trajectory(rhs, x0, [0.5], dt=0.01)[0] - ref[1]).max()
     e2 = np.abs(W.truth_trajectory(rhs, x0, [0.5], dt=0.005)[0] - ref[1]).max()
     assert 12.0 < e1 / e2 < 20.0
+
+
+def test_paper_e1_reading_reproduces_the_table_2_burden():
+    """The threshold reading of the paper's Lorenz '63 case (1e-3 of the
+    maximum): the oracle's own run of it (tests/golden/paper_e1_counts.txt,
+    written by the oracle alone, read every 0.05) lies within small factors of
+    the burden Table 2 prints (tests/golden/table2_lorenz63_burden.txt)."""
+    import os
+
+    here = os.path.join(os.path.dirname(__file__), "golden")
+    ref = {}
+    for line in open(os.path.join(here, "table2_lorenz63_burden.txt")):
+        if line.strip() and not line.startswith("#"):
+            k, v = line.split()
+            ref[k] = float(v)
+    rows = [line.split() for line in open(os.path.join(here, "paper_e1_counts.txt"))
+            if line.strip() and not line.startswith("#")]
+    steps = sum(int(r[1]) for r in rows)
+    updates = sum(int(r[2]) for r in rows)
+    peak = max(int(r[3]) for r in rows)
+    assert W.paper_e1().thr_rel == 1e-3 and len(rows) == 40
+    assert 0.8 <= steps / ref["integration_steps"] <= 1.25, steps
+    assert 0.5 <= peak / ref["max_grid_size"] <= 2.0, peak
+    assert 0.5 <= updates / ref["cell_computations"] <= 2.0, updates
